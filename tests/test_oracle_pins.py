@@ -1,0 +1,470 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a closed form, a textbook
+identity, a special case the paper prints, brute force on a tiny input, or a finite difference.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import binning, composite, projection, render, sh, slicing
+
+F64 = torch.float64
+
+
+def _random_L(rng, n, scale=0.1):
+    """Well-conditioned random Cholesky factors (cond(Sigma) ~ 1e2), so FP64 identities hold to 1e-10."""
+    L = np.tril(rng.normal(0.0, scale, size=(n, 7, 7)))
+    for i in range(7):
+        L[:, i, i] = np.exp(rng.uniform(np.log(0.2), np.log(0.6), size=n))
+    return L
+
+
+def _pack(L):
+    rows, cols = np.tril_indices(7)
+    return L[:, rows, cols]
+
+
+def _mvn_logpdf(x, mu, S):
+    """log N(x; mu, S) written from the density, via a Cholesky-free solve and slogdet."""
+    k = x.shape[-1]
+    diff = (x - mu)
+    sol = torch.linalg.solve(S, diff.unsqueeze(-1)).squeeze(-1)
+    _, logdet = torch.linalg.slogdet(S)
+    return -0.5 * (diff * sol).sum(-1) - 0.5 * logdet - 0.5 * k * math.log(2 * math.pi)
+
+
+# ----------------------------------------------------------------------------------------------
+# Slicing: Eq. cond_mean / cond_cov / temp_mod / dir_mod (Sec. 4.2, Algorithm 1 steps 3-6)
+# ----------------------------------------------------------------------------------------------
+
+def test_unpack_matches_packed_layout():
+    rng = np.random.default_rng(1)
+    L = _random_L(rng, 5)
+    got = slicing.unpack_L(torch.tensor(_pack(L))).numpy()
+    np.testing.assert_array_equal(got, L)
+    # element (i, j) lives at i(i+1)/2 + j
+    L28 = torch.arange(28, dtype=F64).reshape(1, 28)
+    U = slicing.unpack_L(L28)[0]
+    for i in range(7):
+        for j in range(i + 1):
+            assert U[i, j] == i * (i + 1) // 2 + j
+
+
+def test_density_factorisation_pins_conditioning():
+    """N7((x_p, t, d)) / N3(x_p; mu_cond, Sigma_cond) is constant in x_p and equals N4((t, d))."""
+    rng = np.random.default_rng(2)
+    n = 16
+    L = torch.tensor(_random_L(rng, n))
+    mean7 = torch.tensor(rng.normal(size=(n, 7)))
+    t = 0.37
+    d = np.array([0.2, -0.5, 0.84])
+    Sigma = slicing.covariance(L)
+    mu_c, S_c = slicing.condition(mean7, Sigma, t, d)
+    td = torch.tensor(np.concatenate([[t], d]))
+    log_marg = _mvn_logpdf(td.expand(n, 4), mean7[:, 3:], Sigma[:, 3:, 3:])
+    for _ in range(4):
+        xp = torch.tensor(rng.normal(size=(n, 3)))
+        x7 = torch.cat([xp, td.expand(n, 4)], 1)
+        ratio = _mvn_logpdf(x7, mean7, Sigma) - _mvn_logpdf(xp, mu_c, S_c)
+        np.testing.assert_allclose(ratio.numpy(), log_marg.numpy(), rtol=0, atol=1e-10)
+
+
+def test_block_diagonal_static_case_is_plain_3dgs():
+    """Block-diagonal L with t = mu_t, d = mu_d: mu_cond = mu_p, Sigma_cond = L_pp L_pp^T, f = 1."""
+    rng = np.random.default_rng(3)
+    n = 8
+    L = _random_L(rng, n)
+    L[:, 3:, :3] = 0.0  # no p <-> (t, d) coupling
+    L[:, 4:, 3] = 0.0  # no t <-> d coupling
+    mean7 = rng.normal(size=(n, 7))
+    for i in range(n):
+        mu_t, mu_d = mean7[i, 3], mean7[i, 4:]
+        Ls = torch.tensor(L[i:i + 1])
+        Sigma = slicing.covariance(Ls)
+        m = torch.tensor(mean7[i:i + 1])
+        mu_c, S_c = slicing.condition(m, Sigma, mu_t, mu_d)
+        np.testing.assert_allclose(mu_c.numpy()[0], mean7[i, :3], rtol=0, atol=1e-14)
+        Lpp = L[i, :3, :3]
+        np.testing.assert_allclose(S_c.numpy()[0], Lpp @ Lpp.T, rtol=0, atol=1e-14)
+        ft, fd = slicing.modulation(m, Sigma, mu_t, mu_d, 0.7, 0.9)
+        assert ft.item() == 1.0 and fd.item() == 1.0
+        # away from mu_t the geometry is unchanged and only the opacity drops
+        mu_c2, S_c2 = slicing.condition(m, Sigma, mu_t + 0.3, mu_d)
+        np.testing.assert_allclose(mu_c2.numpy()[0], mean7[i, :3], atol=1e-14)
+        np.testing.assert_allclose(S_c2.numpy()[0], Lpp @ Lpp.T, atol=1e-14)
+        ft2, _ = slicing.modulation(m, Sigma, mu_t + 0.3, mu_d, 0.7, 0.9)
+        assert ft2.item() < 1.0
+
+
+def _sigma_from_blocks(rng, zero_pt=False, zero_pd=False, zero_td=False):
+    A = rng.normal(size=(7, 7))
+    S = A @ A.T + 7 * np.eye(7)
+    if zero_pt:
+        S[:3, 3] = S[3, :3] = 0.0
+    if zero_pd:
+        S[:3, 4:] = S[4:, :3] = 0.0
+    if zero_td:
+        S[3, 4:] = S[4:, 3] = 0.0
+    return S
+
+
+def test_reduces_to_6dgs_conditioning():
+    """Sigma_pt = Sigma_td = 0 and t = mu_t: the 6DGS formulas of Sec. 3 (direction only)."""
+    rng = np.random.default_rng(4)
+    S = _sigma_from_blocks(rng, zero_pt=True, zero_td=True)
+    L = np.linalg.cholesky(S)
+    mean7 = rng.normal(size=7)
+    d = np.array([0.3, 0.1, -0.9])
+    mu_c, S_c = slicing.condition(torch.tensor(mean7[None]), slicing.covariance(torch.tensor(L[None])),
+                                  mean7[3], d)
+    Spd, Sd = S[:3, 4:], S[4:, 4:]
+    want_mu = mean7[:3] + Spd @ np.linalg.solve(Sd, d - mean7[4:])
+    want_S = S[:3, :3] - Spd @ np.linalg.solve(Sd, Spd.T)
+    np.testing.assert_allclose(mu_c.numpy()[0], want_mu, atol=1e-12)
+    np.testing.assert_allclose(S_c.numpy()[0], want_S, atol=1e-12)
+
+
+def test_reduces_to_scalar_time_conditioning():
+    """Sigma_pd = Sigma_td = 0 and d = mu_d: the scalar Schur complement in time."""
+    rng = np.random.default_rng(5)
+    S = _sigma_from_blocks(rng, zero_pd=True, zero_td=True)
+    L = np.linalg.cholesky(S)
+    mean7 = rng.normal(size=7)
+    t = mean7[3] + 0.8
+    mu_c, S_c = slicing.condition(torch.tensor(mean7[None]), slicing.covariance(torch.tensor(L[None])),
+                                  t, mean7[4:])
+    Spt, St = S[:3, 3], S[3, 3]
+    np.testing.assert_allclose(mu_c.numpy()[0], mean7[:3] + Spt * (t - mean7[3]) / St, atol=1e-12)
+    np.testing.assert_allclose(S_c.numpy()[0], S[:3, :3] - np.outer(Spt, Spt) / St, atol=1e-12)
+
+
+def test_conditional_covariance_spd_and_schur_determinant():
+    rng = np.random.default_rng(6)
+    n = 64
+    L = torch.tensor(_random_L(rng, n))
+    Sigma = slicing.covariance(L)
+    mean7 = torch.tensor(rng.normal(size=(n, 7)))
+    _, S_c = slicing.condition(mean7, Sigma, 0.5, [0.0, 0.0, 1.0])
+    assert torch.all(torch.linalg.eigvalsh(S_c) > 0)
+    det_ratio = torch.linalg.det(Sigma) / torch.linalg.det(Sigma[:, 3:, 3:])
+    np.testing.assert_allclose(torch.linalg.det(S_c).numpy(), det_ratio.numpy(), rtol=1e-9)
+    # precision-matrix identity: Sigma_cond = ((Sigma^-1)_pp)^-1
+    prec = torch.linalg.inv(Sigma)
+    np.testing.assert_allclose(S_c.numpy(), torch.linalg.inv(prec[:, :3, :3]).numpy(), rtol=1e-8,
+                               atol=1e-12)
+
+
+def test_modulation_is_scaled_marginal_density_ratio():
+    """With lambda = 1, f_temp and f_dir are the marginal densities of t and d over their peaks."""
+    rng = np.random.default_rng(7)
+    n = 16
+    L = torch.tensor(_random_L(rng, n))
+    Sigma = slicing.covariance(L)
+    mean7 = torch.tensor(rng.normal(size=(n, 7)))
+    t, d = 0.25, np.array([0.6, 0.0, 0.8])
+    ft, fd = slicing.modulation(mean7, Sigma, t, d, 1.0, 1.0)
+    tt = torch.full((n, 1), t, dtype=F64)
+    lt = _mvn_logpdf(tt, mean7[:, 3:4], Sigma[:, 3:4, 3:4]) - _mvn_logpdf(mean7[:, 3:4], mean7[:, 3:4],
+                                                                          Sigma[:, 3:4, 3:4])
+    dd = torch.tensor(d).expand(n, 3)
+    ld = _mvn_logpdf(dd, mean7[:, 4:], Sigma[:, 4:, 4:]) - _mvn_logpdf(mean7[:, 4:], mean7[:, 4:],
+                                                                      Sigma[:, 4:, 4:])
+    np.testing.assert_allclose(torch.log(ft).numpy(), lt.numpy(), atol=1e-10)
+    np.testing.assert_allclose(torch.log(fd).numpy(), ld.numpy(), atol=1e-10)
+    # lambda scales the exponent
+    ft2, fd2 = slicing.modulation(mean7, Sigma, t, d, 0.05, 0.3)
+    np.testing.assert_allclose(torch.log(ft2).numpy(), 0.05 * lt.numpy(), atol=1e-10)
+    np.testing.assert_allclose(torch.log(fd2).numpy(), 0.3 * ld.numpy(), atol=1e-10)
+    sl = slicing.slice_gaussians(mean7, torch.tensor(_pack(L.numpy())), torch.full((n,), 0.8, dtype=F64),
+                                 t, d, 0.05, 0.3)
+    a = sl["alpha_cond"].numpy()
+    assert np.all(a >= 0) and np.all(a <= 0.8)
+
+
+# ----------------------------------------------------------------------------------------------
+# SH colour (Sec. 3 colour model, kept by Sec. 4.1)
+# ----------------------------------------------------------------------------------------------
+
+def test_sh_matches_textbook_cartesian_table(golden_dir):
+    rng = np.random.default_rng(8)
+    v = rng.normal(size=(32, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    Y = sh.basis(torch.tensor(v)).numpy()
+    rows = [ln.split(None, 3) for ln in open(os.path.join(golden_dir, "real_sh_cartesian.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 16
+    for l, m, sign, expr in rows:
+        l, m, sign = int(l), int(m), int(sign)
+        ns = dict(x=v[:, 0], y=v[:, 1], z=v[:, 2], pi=math.pi, sqrt=np.sqrt)
+        want = sign * eval(expr, {"__builtins__": {}}, ns)
+        np.testing.assert_allclose(Y[:, l * l + l + m], want, rtol=1e-13, atol=1e-13)
+
+
+def test_sh_orthonormal_by_quadrature():
+    """Gauss-Legendre in z times a uniform grid in phi integrates degree <= 6 polynomials exactly."""
+    zs, wz = np.polynomial.legendre.leggauss(8)
+    phis = np.arange(16) * 2 * np.pi / 16
+    Z, P = np.meshgrid(zs, phis, indexing="ij")
+    W = np.repeat(wz, 16) * (2 * np.pi / 16)
+    s = np.sqrt(1 - Z ** 2)
+    dirs = np.stack([s * np.cos(P), s * np.sin(P), Z], -1).reshape(-1, 3)
+    Y = sh.basis(torch.tensor(dirs)).numpy()
+    gram = (Y * W[:, None]).T @ Y
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-13)
+
+
+def test_sh_colour_dc_only_is_view_independent():
+    rng = np.random.default_rng(9)
+    coeffs = np.zeros((1, 16, 3))
+    coeffs[0, 0] = [0.3, -0.2, 0.9]
+    v = rng.normal(size=(10, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    c = sh.colour(torch.tensor(coeffs).expand(10, 16, 3), torch.tensor(v)).numpy()
+    want = np.maximum(0.0, 0.5 / math.sqrt(math.pi) * np.array([0.3, -0.2, 0.9]) + 0.5)
+    np.testing.assert_allclose(c, np.tile(want, (10, 1)), atol=1e-15)
+
+
+# ----------------------------------------------------------------------------------------------
+# Projection
+# ----------------------------------------------------------------------------------------------
+
+def test_ewa_covariance_matches_numerical_jacobian():
+    """Sigma_2D - 0.3 I = dpi/dp Sigma_cam dpi/dp^T with dpi/dp by central differences of pi."""
+    rng = np.random.default_rng(10)
+    cam = synth.config_cameras(1, count=1, width=128, height=96)[0]  # a rotated camera
+    n = 12
+    mu = torch.tensor(rng.uniform(-0.3, 0.3, size=(n, 3)))
+    A = rng.normal(size=(n, 3, 3)) * 0.1
+    S = torch.tensor(A @ A.transpose(0, 2, 1) + 0.01 * np.eye(3))
+    pr = projection.project(mu, S, cam)
+    R = cam.viewmat[:3, :3]
+    tv = cam.viewmat[:3, 3]
+
+    def pi(p):
+        return np.array([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy])
+
+    for i in range(n):
+        p = R @ mu[i].numpy() + tv
+        h = 1e-6
+        Jn = np.stack([(pi(p + h * e) - pi(p - h * e)) / (2 * h) for e in np.eye(3)], 1)
+        want = Jn @ (R @ S[i].numpy() @ R.T) @ Jn.T + 0.3 * np.eye(2)
+        a, b, c = pr["cov2d"][i].numpy()
+        np.testing.assert_allclose([[a, b], [b, c]], want, rtol=1e-7)
+        np.testing.assert_allclose(pr["mean2d"][i].numpy(), pi(p), rtol=1e-14)
+        q = pr["conic"][i].numpy()
+        np.testing.assert_allclose(np.array([[q[0], q[1]], [q[1], q[2]]]) @ want, np.eye(2), atol=1e-9)
+        lam = np.linalg.eigvalsh(want).max()
+        np.testing.assert_allclose(pr["extent"][i].item(), 3 * np.sqrt(lam), rtol=1e-8)
+
+
+def test_tile_rect_matches_brute_force_intersection():
+    rng = np.random.default_rng(11)
+    W, H = 100, 70
+    tx, ty = 7, 5
+    u = torch.tensor(rng.uniform(-40, 140, size=300))
+    v = torch.tensor(rng.uniform(-40, 110, size=300))
+    r = torch.tensor(rng.integers(0, 40, size=300).astype(np.float64))
+    u[:20] = torch.tensor(rng.integers(0, 7, size=20) * 16.0) + r[:20]  # edges exactly on tile borders
+    rect = projection.tile_rect(u, v, r, tx, ty).numpy()
+    for i in range(300):
+        want = np.zeros((ty, tx), bool)
+        for j in range(ty):
+            for k in range(tx):
+                # closed square [u-r, u+r] meets the half-open box [16k, 16k+16)
+                want[j, k] = (16 * k <= u[i] + r[i]) and (u[i] - r[i] < 16 * k + 16) and \
+                             (16 * j <= v[i] + r[i]) and (v[i] - r[i] < 16 * j + 16)
+        got = np.zeros((ty, tx), bool)
+        got[rect[i, 1]:rect[i, 3], rect[i, 0]:rect[i, 2]] = True
+        assert np.array_equal(got, want), i
+
+
+# ----------------------------------------------------------------------------------------------
+# Binning and compositing
+# ----------------------------------------------------------------------------------------------
+
+def test_binning_matches_python_sort_of_tuples():
+    rec = synth.random_projected(300, 100, 70, seed=12)
+    keys, vals = binning.sort_keys(rec["depth"], rec["rect"], 7)
+    tuples = []
+    for g in range(300):
+        rx0, ry0, rx1, ry1 = rec["rect"][g]
+        for y in range(ry0, ry1):
+            for x in range(rx0, rx1):
+                tuples.append((y * 7 + x, float(rec["depth"][g]), g))
+    tuples.sort()
+    assert [int(k >> np.uint64(32)) for k in keys] == [t[0] for t in tuples]
+    assert [int(v) for v in vals] == [t[2] for t in tuples]
+    assert np.all(np.diff(keys.astype(np.float64)) >= 0)
+    ranges = binning.tile_ranges(keys, 35)
+    counts = np.bincount([t[0] for t in tuples], minlength=35)
+    np.testing.assert_array_equal(ranges[:, 1] - ranges[:, 0], counts)
+    lists = binning.tile_lists(rec["depth"], rec["rect"], 7, 35)
+    for tile in range(35):
+        np.testing.assert_array_equal(lists[tile], vals[ranges[tile, 0]:ranges[tile, 1]])
+
+
+def test_single_gaussian_closed_form():
+    """One Gaussian on the optical axis with an axis-aligned Sigma_cond: every pixel is
+    alpha_i c + (1 - alpha_i) bg with Sigma_2D = diag(fx^2 sx^2 / z^2, fy^2 sy^2 / z^2) + 0.3 I."""
+    sx, sy, sz = 0.05, 0.08, 0.03
+    L = np.zeros((1, 7, 7))
+    np.fill_diagonal(L[0], [sx, sy, sz, 0.2, 0.3, 0.3, 0.3])
+    mean7 = np.array([[0.0, 0.0, 0.0, 0.5, 0.0, 0.0, 1.0]], dtype=np.float32)
+    coeffs = np.zeros((1, 16, 3), np.float32)
+    coeffs[0, 0] = [0.4, 0.1, -0.3]
+    scene = synth.Scene(mean7, _pack(L).astype(np.float32), np.array([0.7], np.float32), coeffs,
+                        0.05, 0.05, (0.2, 0.3, 0.4))
+    cam = synth.make_camera((0.0, 0.0, -3.0), 64, 48, 60.0, 0.5, bg=(0.2, 0.3, 0.4))
+    out = render.render(scene, cam)
+    L32 = _pack(L).astype(np.float32).astype(np.float64)
+    sx2, sy2 = L32[0, 0] ** 2, L32[0, 2] ** 2
+    z = 3.0
+    a = cam.fx ** 2 * sx2 / z ** 2 + 0.3
+    c = cam.fy ** 2 * sy2 / z ** 2 + 0.3
+    col = np.maximum(0.0, 0.5 / math.sqrt(math.pi) * coeffs[0, 0].astype(np.float64) + 0.5)
+    alpha0 = float(np.float32(0.7))
+    ys, xs = np.mgrid[0:48, 0:64]
+    dx, dy = xs + 0.5 - 32.0, ys + 0.5 - 24.0
+    al = np.minimum(0.99, alpha0 * np.exp(-0.5 * (dx * dx / a + dy * dy / c)))
+    al = np.where(al >= 1 / 255, al, 0.0)
+    r = math.ceil(3 * math.sqrt(max(a, c)))
+    inside = (np.floor((32 - r) / 16) * 16 <= xs) & (xs < (np.floor((32 + r) / 16) + 1) * 16) & \
+             (np.floor((24 - r) / 16) * 16 <= ys) & (ys < (np.floor((24 + r) / 16) + 1) * 16)
+    al = np.where(inside, al, 0.0)
+    want = al[..., None] * col + (1 - al[..., None]) * np.array(cam.bg)
+    np.testing.assert_allclose(out["image"].numpy(), want, atol=1e-12)
+
+
+def test_colour_is_evaluated_toward_the_gaussian_from_the_camera():
+    """SH colour at dir = (mu_cond - camera centre) / |.|, checked with the textbook l = 1 terms."""
+    rng = np.random.default_rng(18)
+    n = 6
+    L = np.zeros((n, 7, 7))
+    for i in range(n):
+        np.fill_diagonal(L[i], [0.05, 0.05, 0.05, 0.2, 0.3, 0.3, 0.3])
+    mean7 = np.zeros((n, 7), np.float32)
+    mean7[:, :3] = rng.uniform(-0.6, 0.6, size=(n, 3))
+    mean7[:, 3] = 0.5
+    mean7[:, 6] = 1.0
+    coeffs = np.zeros((n, 16, 3), np.float32)
+    coeffs[:, 0] = 0.3
+    coeffs[:, 1:4] = rng.normal(0, 0.2, size=(n, 3, 3))
+    scene = synth.Scene(mean7, _pack(L).astype(np.float32), np.full(n, 0.5, np.float32), coeffs,
+                        0.05, 0.05)
+    cam = synth.make_camera((0.4, -0.2, -3.0), 64, 64, 60.0, 0.5)
+    g = render.render(scene, cam)["g"]
+    c1 = math.sqrt(3 / (4 * math.pi))
+    for i in range(n):
+        v = mean7[i, :3].astype(np.float64) - np.array([0.4, -0.2, -3.0])
+        x, y, z = v / np.linalg.norm(v)
+        want = 0.5 / math.sqrt(math.pi) * coeffs[i, 0] + c1 * (-y * coeffs[i, 1] + z * coeffs[i, 2]
+                                                                 - x * coeffs[i, 3]) + 0.5
+        np.testing.assert_allclose(g["rgb"][i].numpy(), np.maximum(want, 0), atol=1e-7)
+
+
+def test_compositing_invariants():
+    rec = synth.random_projected(200, 64, 64, seed=13)
+    out = render.render_projected(rec, 64, 64, (0.0, 0.0, 0.0))
+    # weights + final transmittance = 1: with white Gaussians on black, image = 1 - T_final
+    white = dict(rec, rgb=np.ones_like(rec["rgb"]))
+    o2 = render.render_projected(white, 64, 64, (0.0, 0.0, 0.0))
+    np.testing.assert_allclose(o2["image"].numpy(), np.repeat(1 - o2["final_T"].numpy()[..., None], 3, -1),
+                               atol=1e-12)
+    # every colour equal to the background: the image is that colour
+    grey = dict(rec, rgb=np.full_like(rec["rgb"], 0.25))
+    o3 = render.render_projected(grey, 64, 64, (0.25, 0.25, 0.25))
+    np.testing.assert_allclose(o3["image"].numpy(), 0.25, atol=1e-12)
+    assert np.all(out["final_T"].numpy() >= 1e-4 * 0.0) and np.all(out["final_T"].numpy() <= 1.0)
+
+
+def test_transmittance_monotone_and_stop_rule():
+    rec = synth.random_projected(400, 32, 32, seed=14, max_half_tiles=2)
+    rec["opacity"] = np.full_like(rec["opacity"], 0.95)
+    lists = binning.tile_lists(rec["depth"], rec["rect"], 2, 4)
+    f = lambda k: np.asarray(rec[k], np.float32).astype(np.float64)
+    for (px, py) in [(3.5, 4.5), (20.5, 9.5), (30.5, 30.5)]:
+        tile = int(py // 16) * 2 + int(px // 16)
+        T = 1.0
+        g = lists[tile]
+        col, Tf, last = composite.composite_pixel_loop(px, py, g, f("mean2d"), f("conic"), f("opacity"),
+                                                       f("rgb"), (0, 0, 0))
+        # replay: T never increases and never drops below 1e-4
+        for gi in g[:last]:
+            dx, dy = px - f("mean2d")[gi][0], py - f("mean2d")[gi][1]
+            a, b, c = f("conic")[gi]
+            al = min(0.99, f("opacity")[gi] * math.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy))
+            if al >= 1 / 255:
+                assert T * (1 - al) <= T
+                T *= 1 - al
+        assert abs(T - Tf) < 1e-15 and Tf >= 1e-4
+
+
+def test_vectorised_compositing_equals_per_pixel_loop():
+    rec = synth.random_projected(150, 48, 32, seed=15)
+    out = render.render_projected(rec, 48, 32, (0.1, 0.2, 0.3))
+    lists = binning.tile_lists(rec["depth"], rec["rect"], 3, 6)
+    f = lambda k: np.asarray(rec[k], np.float32).astype(np.float64)
+    for y in range(0, 32, 3):
+        for x in range(0, 48, 5):
+            tile = (y // 16) * 3 + x // 16
+            col, T, last = composite.composite_pixel_loop(x + 0.5, y + 0.5, lists[tile], f("mean2d"),
+                                                          f("conic"), f("opacity"), f("rgb"), (0.1, 0.2, 0.3))
+            np.testing.assert_allclose(out["image"][y, x].numpy(), col, atol=1e-13)
+            assert out["n_contrib"][y, x].item() == last
+            assert abs(out["final_T"][y, x].item() - T) < 1e-13
+
+
+# ----------------------------------------------------------------------------------------------
+# Gradients: autograd through the oracle forward vs central finite differences (FP64)
+# ----------------------------------------------------------------------------------------------
+
+def _decisions(scene, cam):
+    out = render.render(scene, cam)
+    g = out["g"]
+    return (g["visible"].numpy().copy(), g["rect"].numpy().copy(), out["n_contrib"].numpy().copy()), out
+
+
+def test_oracle_gradient_matches_central_differences():
+    scene = synth.make_scene(64, seed=16, box=0.6)
+    cam = synth.make_camera((0.0, 0.0, -3.0), 32, 32, 60.0, 0.5, bg=(0.3, 0.3, 0.3))
+    rng = np.random.default_rng(17)
+    dL = rng.normal(size=(32, 32, 3))
+    grads = render.vjp(scene, cam, dL)
+    base_dec, _ = _decisions(scene, cam)
+    checked = skipped = 0
+    names = ["mean7", "L28", "opacity", "sh"]
+    for _ in range(40):
+        name = names[rng.integers(0, 4)]
+        arr = getattr(scene, name)
+        flat_idx = int(rng.integers(0, arr.size))
+        # choose a visible Gaussian's parameter
+        g = flat_idx // (arr.size // scene.n)
+        if not base_dec[0][g]:
+            continue
+        vals = []
+        decs = []
+        for sgn in (+1, -1):
+            a64 = {k: getattr(scene, k).astype(np.float64) for k in names}
+            x0 = a64[name].reshape(-1)[flat_idx]
+            h = 1e-6 * max(1.0, abs(x0))
+            a64[name].reshape(-1)[flat_idx] = x0 + sgn * h
+            sc = synth.Scene(a64["mean7"], a64["L28"], a64["opacity"], a64["sh"], scene.lambda_t,
+                             scene.lambda_d, scene.bg)
+            dec, out = _decisions(sc, cam)
+            decs.append(dec)
+            vals.append(float((out["image"].numpy() * dL).sum()))
+        if not all(np.array_equal(a, b) for d in decs for a, b in zip(d, base_dec)):
+            skipped += 1
+            continue
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = grads[name].reshape(-1)[flat_idx]
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-7, (name, flat_idx, fd, an)
+        checked += 1
+    assert checked >= 20 and skipped <= 5
