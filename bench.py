@@ -1,0 +1,388 @@
+"""Benchmark of the 7DGS render path on GB300: Mpix/s and FPS of the 800x800 / 300k-Gaussian
+forward render, plus fwd+bwd it/s, through libsdgs's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full forward render of one camera view (conditional slicing + projection + SH,
+tile binning with the depth/tile radix sort, compositing) of the 300k-Gaussian object-scale scene
+at 800x800; the camera cycles over the scene's 100 orbit cameras, each at its own time t.  Rank 0
+prints one JSON line.  With N > 1 (torchrun), every rank renders its own cameras (replicas: the
+render path needs no collective) and the value is the images of all ranks over the slowest rank's
+time.  `--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "Mpix/s & FPS at 800×800/300k Gaussians; fwd+bwd it/s; p50/p99 serving latency"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# Source-level FP32 work of one (pixel, Gaussian) evaluation in the compositing loop: offsets (2),
+# exponent (8), opacity clamp (2), tests (2), transmittance (2), weight (1), colour FMAs (6) = 23
+# FLOP (an FMA counts 2) plus one exp2 on the MUFU pipe.
+FLOP_PER_EVAL = 23
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    except (OSError, KeyError, ValueError):
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 FLOP x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------------
+
+def oracle_frame_estimate(scene, cam, tiles_sample: int, seed: int, gauss_frac: float = 1.0) -> dict:
+    """Time the oracle on one view: the per-Gaussian stage plus `tiles_sample` random tiles of
+    compositing, extrapolated to the full frame.  With gauss_frac < 1 both run on that fraction of
+    the Gaussians and their times are scaled by 1 / gauss_frac (both are linear in N)."""
+    from oracle import composite
+    from oracle import render as orender
+    m = scene.n if gauss_frac >= 1.0 else max(1, int(scene.n * gauss_frac))
+    sc = scene if m == scene.n else scene.subset(np.arange(m))
+    scale = scene.n / m
+    t0 = time.perf_counter()
+    g = orender.gaussians(orender.params_from_scene(sc), cam, scene.lambda_t, scene.lambda_d)
+    t_g = (time.perf_counter() - t0) * scale
+    rng = np.random.default_rng(seed)
+    ntiles = cam.tiles_x * cam.tiles_y
+    tiles = rng.choice(ntiles, size=tiles_sample, replace=False)
+    bg = torch.as_tensor(cam.bg, dtype=torch.float64)
+    t1 = time.perf_counter()
+    rect, depth = g["rect"], g["depth"]
+    for tile in tiles:
+        tx, ty = int(tile % cam.tiles_x), int(tile // cam.tiles_x)
+        inside = (rect[:, 0] <= tx) & (tx < rect[:, 2]) & (rect[:, 1] <= ty) & (ty < rect[:, 3])
+        ids = torch.nonzero(inside).reshape(-1)
+        order = np.lexsort((ids.numpy(), depth[ids].numpy()))
+        cand = ids[torch.as_tensor(order, dtype=torch.int64)]
+        pix, _ = orender.pixel_centres(cam, int(tile))
+        composite.composite_tile(pix, cand, g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], bg)
+    t_t = (time.perf_counter() - t1) * scale
+    frame_s = t_g + t_t * ntiles / tiles_sample
+    return dict(frame_s=frame_s, t_gauss=t_g, t_tiles=t_t, tiles=tiles_sample, gauss_frac=m / scene.n)
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    scene = synth.config_scene(1)
+    cams = synth.config_cameras(1)
+    cores = torch.get_num_threads()
+    times = []
+    total = args.warmup + args.steps
+    budget_s = 150.0  # keep the whole reference run within a few minutes
+    frac = 1.0
+    for i in range(total):
+        t0 = time.perf_counter()
+        est = oracle_frame_estimate(scene, cams[i % len(cams)], tiles_sample=2, seed=i, gauss_frac=frac)
+        step_s = time.perf_counter() - t0
+        if i == 0 and step_s * total > budget_s:
+            frac = max(0.02, budget_s / (step_s * total))
+        if i >= args.warmup:
+            times.append(est["frame_s"])
+    frame_s = float(np.mean(times))
+    mpix = 800 * 800 / frame_s / 1e6
+    sample = ("per step: the oracle's per-Gaussian stage plus compositing of 2 random 16x16 tiles of one "
+              "800x800 view, extrapolated to the 2500-tile frame; run on %.0f%% of the 300k Gaussians "
+              "with times scaled by N/m" % (100 * frac))
+    line = {"impl": "reference", "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "fps": 1.0 / frame_s,
+            "config": {"workload": "config 1: 300k 7D Gaussians, 800x800, 100 orbit cameras",
+                       "n_gaussians": 300000, "width": 800, "height": 800},
+            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------------------------
+
+def launches_per_frame(n: int, width: int, height: int) -> int:
+    """Kernels libsdgs launches for one render: slice_project; depth keys; 4 depth radix passes
+    (upsweep, 3 scan kernels, downsweep); tile counts; 3-kernel scan; duplicate; the tile radix
+    passes; tile ranges; the rasteriser."""
+    tiles = ((width + 15) // 16) * ((height + 15) // 16)
+    bits = max(0, math.ceil(math.log2(tiles))) if tiles > 1 else 0
+    tile_passes = (bits + 7) // 8
+    return 1 + 1 + 4 * 5 + 1 + 3 + 1 + tile_passes * 5 + 1 + 1
+
+
+def cpu_baseline(scene, cam) -> dict:
+    est = oracle_frame_estimate(scene, cam, tiles_sample=4, seed=0)
+    return {"value": 800 * 800 / est["frame_s"] / 1e6, "unit": "Mpix/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": ("the oracle's per-Gaussian stage for all 300k Gaussians (%.1f s) plus compositing of 4 "
+                       "random 16x16 tiles (%.1f s) of camera 0, extrapolated to the 2500-tile frame"
+                       % (est["t_gauss"], est["t_tiles"]))}
+
+
+def run_ours(args, rank: int, world: int):
+    from paper_2503_07946_gb300 import render as prender
+    from paper_2503_07946_gb300 import sdgs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    sdgs.lib()  # fails loudly if the CUDA library is missing
+    peaks = load_peaks()
+    scene = synth.config_scene(1)
+    cams = synth.config_cameras(1)
+    W, H = 800, 800
+    t_scene = prender.scene_to_device(scene)
+    st = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
+    steps, warm = args.steps, args.warmup
+    order = [(rank * 37 + i) % len(cams) for i in range(steps + warm)]
+    views = [sdgs.view_struct(cams[i]) for i in order]
+
+    # size the instance lists once from the frames this run renders
+    sizing = prender.Renderer(scene.n, W, H, capacity=4096)
+    kmax = 0
+    for v in views[: min(len(views), 100)]:
+        sdgs.slice_project(st, v, sizing.proj)
+        kmax = max(kmax, sizing.bin(v))
+    del sizing
+    r = prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    n_eval = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(v, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        sdgs.slice_project(st, v, r.proj, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        sdgs.bin_sort(r.proj, v, r.bins, sync=False, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        sdgs.render_fwd(r.proj, r.bins, v, r.image, r.final_T, r.n_contrib, n_eval, stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for i in range(warm):
+        step(views[i])
+        flush.zero_()
+    torch.cuda.synchronize()
+    n_eval.zero_()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t_wall = time.perf_counter()
+        for i in range(steps):
+            step(views[warm + i], evs[i])
+            flush.zero_()  # outside the step's events: every step starts with a cold L2
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    phase = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
+    step_ms = phase.sum(1)
+    ms = float(step_ms.mean())
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    evals = int(n_eval.item())
+    k_inst = int(r.bins.num_instances.item())
+    visible = int(((r.proj.rect[:, 2] > r.proj.rect[:, 0]) & (r.proj.rect[:, 3] > r.proj.rect[:, 1])).sum())
+
+    # ---- end to end: the public API with the image read back to pinned host memory ----
+    host_img = torch.empty(H, W, 3, dtype=torch.float32, pin_memory=True)
+    view_bytes = ctypes_sizeof_view()
+    for i in range(warm):
+        r.forward(st, views[i])
+        host_img.copy_(r.image, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        r.forward(st, views[warm + i])  # synchronises once to read the instance count
+        host_img.copy_(r.image, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / steps
+
+    # ---- fwd + bwd (L2 loss against a target from perturbed parameters, camera 0) ----
+    fb = fwd_bwd_its(scene, cams[0], steps, warm, dev)
+
+    pix = W * H
+    value = world * pix / (ms * 1e-3) / 1e6
+    raster_ms = float(phase[:, 2].mean())
+    achieved_tflops = (evals / steps) * FLOP_PER_EVAL / (raster_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    sm_for_peak = peaks["sm_max_mhz"]
+    peak_tflops = fp32_peak_tflops(sm_for_peak)
+    slice_gbs = (scene.n * 148 + visible * (192 + 60)) / (float(phase[:, 0].mean()) * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": steps, "warmup": warm,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "fps": world * 1000.0 / ms,
+        "config": {"workload": "config 1: 300k 7D Gaussians, 800x800, 100 orbit cameras (random frame each), "
+                               "white background, lambda_t = lambda_d = 0.05",
+                   "n_gaussians": scene.n, "width": W, "height": H, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MiB write) between steps, outside the per-step CUDA events"},
+        "phases_ms": {"slice_project": float(phase[:, 0].mean()), "bin_sort": float(phase[:, 1].mean()),
+                      "render_fwd": raster_ms},
+        "workload_stats": {"instances": k_inst, "visible": visible, "evaluations_per_frame": evals // steps},
+        "fwd_bwd_it_s": fb,
+        "e2e": {"value": world * pix / e2e_s / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
+                "d2h_bytes_per_step": pix * 3 * 4 + 8},
+        "gpu_launches": steps * launches_per_frame(scene.n, W, H),
+        "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
+                     "traffic": None,
+                     "note": "FP32 FMA peak 152 SM x 128 lanes x 2 x %.0f MHz (max clock); %d FLOP per "
+                             "evaluated (pixel, Gaussian) pair" % (sm_for_peak, FLOP_PER_EVAL)},
+        "slice_project_hbm": {"achieved": slice_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": slice_gbs / peaks["hbm_gbs"], "peak_source": peaks["source"]},
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cams[order[0]])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def ctypes_sizeof_view() -> int:
+    import ctypes
+
+    from paper_2503_07946_gb300 import sdgs
+    return ctypes.sizeof(sdgs.View)
+
+
+def fwd_bwd_its(scene, cam, steps: int, warm: int, dev) -> dict:
+    from paper_2503_07946_gb300 import render as prender
+    from paper_2503_07946_gb300 import sdgs
+    target_scene = synth.perturb_scene(scene)
+    view = sdgs.view_struct(cam)
+    r = prender.Renderer(scene.n, cam.width, cam.height)
+    tt = prender.scene_to_device(target_scene)
+    with torch.no_grad():
+        target = r.forward(sdgs.scene_struct(tt, scene.lambda_t, scene.lambda_d), view).clone()
+    params = {k: v.clone().requires_grad_(True) for k, v in prender.scene_to_device(scene).items()}
+
+    def it():
+        img = prender.render_image(params["mean7"], params["L28"], params["opacity"], params["sh"], view,
+                                   scene.lambda_t, scene.lambda_d, r)
+        loss = ((img - target) ** 2).mean()
+        loss.backward()
+        for p in params.values():
+            p.grad = None
+        return loss
+
+    for _ in range(max(warm, 1)):
+        it()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        it()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": 1000.0 / ms, "unit": "it/s", "ms_per_it": ms,
+            "workload": "config 3: 300k Gaussians, 800x800, camera 0, L2 loss vs a perturbed-parameter target"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

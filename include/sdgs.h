@@ -1,0 +1,200 @@
+/*
+ * sdgs.h -- C ABI of libsdgs, a GB300 (sm_103a) renderer for 7D Gaussian Splatting.
+ *
+ * The render path of 7DGS without adaptive refinement:
+ *   sdgs_slice_project  conditional slicing of each 7D Gaussian at (t, d) (Sec. 4.2, Eqs.
+ *                       cond_mean / cond_cov, temp_mod / dir_mod; Algorithm 1 steps 3-6) fused
+ *                       with the 3DGS perspective (EWA) projection and SH colour (Sec. 4.3).
+ *   sdgs_bin_sort       tile binning: one instance per (tile, Gaussian) ordered by
+ *                       (tile, depth, Gaussian id) -- the 3DGS tile sort the paper's rasteriser
+ *                       uses (Sec. 4.3) -- and per-tile [start, end) ranges.
+ *   sdgs_render_fwd     front-to-back alpha compositing per pixel (Sec. 4.3, "depth-aware,
+ *                       opacity-blended").
+ *   sdgs_render_bwd     adjoint of the three steps above, for the joint optimisation of all 7D
+ *                       parameters (Sec. 4.3; Sec. 1 contributions).
+ *   sdgs_server_*       a continuous-batching render server over resident scenes.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named "device" are CUDA device memory owned by the caller; the library never
+ *     frees them.  Pointers named "host" are ordinary host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call only enqueues work on
+ *     it and returns, unless it says it synchronises.
+ *   - Return value: SDGS_OK or an SDGS_ERR_* code.  On error nothing was enqueued, and
+ *     sdgs_last_error() returns a message (thread-local, valid until the next call on the thread).
+ *     Errors never trap the device.
+ *   - Images are row-major height x width, colour channels innermost (HWC), float32.
+ *   - Tiles are 16 x 16 pixels; tiles_x = ceil(width / 16), tiles_y = ceil(height / 16), and
+ *     tile_id = ty * tiles_x + tx.
+ */
+#ifndef SDGS_H_
+#define SDGS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum sdgs_status {
+  SDGS_OK = 0,
+  SDGS_ERR_INVALID_ARG = 1, /* a pointer is NULL, a size is out of range, sh_degree != 3 ... */
+  SDGS_ERR_WORKSPACE = 2,   /* workspace missing or smaller than sdgs_bin_workspace_size() */
+  SDGS_ERR_OVERFLOW = 3,    /* more (tile, Gaussian) instances than the bins' capacity */
+  SDGS_ERR_CUDA = 4,        /* a CUDA runtime call failed; the message names it */
+  SDGS_ERR_TIMEOUT = 5,     /* a bounded wait ran out (server) */
+  SDGS_ERR_BUSY = 6,        /* server queue full */
+  SDGS_ERR_OOM_BUDGET = 7,  /* a request does not fit the server's memory budget */
+  SDGS_ERR_NOT_FOUND = 8    /* unknown scene or request id */
+};
+
+#define SDGS_TILE 16
+#define SDGS_SH_COEFFS 16
+
+/* A scene of n 7D Gaussians (Sec. 4.1).  All arrays are float32 device memory, C-contiguous.
+ *   mean7   [n][7]      mu = (mu_p.x, mu_p.y, mu_p.z, mu_t, mu_d.x, mu_d.y, mu_d.z)
+ *   L28     [n][28]     Cholesky factor L of Sigma = L L^T, lower triangle packed row-major:
+ *                       L[i][j] (j <= i) at index i*(i+1)/2 + j.  Positive diagonal is the
+ *                       caller's responsibility (Sec. 4.1).
+ *   opacity [n]         base opacity alpha (already activated, in [0, 1])
+ *   sh      [n][16][3]  real SH coefficients of degree 3, index l*l + l + m, RGB innermost
+ *   lambda_t, lambda_d  the positive modulation sensitivities of Eqs. temp_mod / dir_mod
+ *                       (one scalar each per scene). */
+typedef struct sdgs_scene {
+  const float* mean7;
+  const float* L28;
+  const float* opacity;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree; /* must be 3 */
+  float lambda_t;
+  float lambda_d;
+} sdgs_scene;
+
+/* One render request: camera, query time t and conditioning view direction d (Sec. 4.2).
+ *   viewmat     world->camera 4x4 row-major, OpenCV axes (+x right, +y down, +z forward)
+ *   fx fy cx cy pinhole intrinsics in pixels; pixel (i, j) has its centre at (i + 0.5, j + 0.5)
+ *   near_plane  Gaussians whose conditional mean has camera depth < near_plane are culled
+ *   t, d[3]     the observed time and unit view direction the 7D Gaussians are conditioned on
+ *   bg[3]       background colour added with the final transmittance */
+typedef struct sdgs_view {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_plane;
+  float t;
+  float d[3];
+  float bg[3];
+} sdgs_view;
+
+/* Per-Gaussian screen-space record written by sdgs_slice_project (device, caller-allocated,
+ * n entries each).  A culled Gaussian has rect = {0, 0, 0, 0}; its other fields are unspecified.
+ *   mean2d        [n][2]  projected conditional mean (u, v) in pixels
+ *   conic_opacity [n][4]  (a, b, c, alpha_cond): inverse 2D covariance [[a, b], [b, c]] and the
+ *                         conditional opacity alpha * f_temp * f_dir
+ *   rgb           [n][3]  SH colour max(0, sum beta Y(dir) + 0.5), dir = unit(mu_cond - camera centre)
+ *   depth         [n]     camera-space z of mu_cond
+ *   rect          [n][4]  uint16 tile rectangle [rx0, rx1) x [ry0, ry1) stored (rx0, ry0, rx1, ry1)
+ *   radius        [n]     int32 3-sigma screen radius in pixels (0 when culled) */
+typedef struct sdgs_projected {
+  float* mean2d;
+  float* conic_opacity;
+  float* rgb;
+  float* depth;
+  uint16_t* rect;
+  int32_t* radius;
+  int64_t n;
+} sdgs_projected;
+
+/* Output of sdgs_bin_sort (device, caller-allocated).
+ *   tile_keys  [capacity] uint32 tile id of each sorted instance
+ *   point_list [capacity] uint32 Gaussian id of each sorted instance; instances are ordered by
+ *              (tile id, float32 depth, Gaussian id)
+ *   ranges     [tiles_x * tiles_y][2] uint32 [start, end) of each tile in the sorted lists
+ *   num_instances  device int64: total instance count K written by the call (may exceed capacity,
+ *              in which case only the first `capacity` instances in (depth, id) emission order
+ *              are kept and SDGS_ERR_OVERFLOW is reported when the call synchronises)
+ *   capacity   number of entries allocated in tile_keys / point_list (< 2^31) */
+typedef struct sdgs_bins {
+  uint32_t* tile_keys;
+  uint32_t* point_list;
+  uint32_t* ranges;
+  int64_t* num_instances;
+  int64_t capacity;
+} sdgs_bins;
+
+/* Gradients accumulated by sdgs_render_bwd (device, caller-allocated and zeroed; the call adds).
+ *   dmean7 [n][7], dL28 [n][28], dopacity [n], dsh [n][16][3] */
+typedef struct sdgs_grads {
+  float* dmean7;
+  float* dL28;
+  float* dopacity;
+  float* dsh;
+} sdgs_grads;
+
+/* Library version string, e.g. "sdgs 0.1.0 sm_103a". */
+const char* sdgs_version(void);
+
+/* Message of the last error on this thread ("" if none). */
+const char* sdgs_last_error(void);
+
+/* Conditional slicing + modulation + culling + EWA projection + SH colour, one pass per Gaussian.
+ * Reads the scene (n * 144 bytes of geometry, plus 192 bytes of SH for Gaussians that survive
+ * culling) and writes the projected record.  Culled when alpha_cond < 1/255, depth < near_plane,
+ * the 2D covariance is not positive definite, or the tile rectangle is empty.
+ * Errors: SDGS_ERR_INVALID_ARG (NULL pointer, n < 0, sh_degree != 3, width/height <= 0 or
+ * > 65535 * 16, fx/fy <= 0), SDGS_ERR_CUDA (launch failure). */
+int sdgs_slice_project(const sdgs_scene* scene, const sdgs_view* view, const sdgs_projected* out,
+                       void* stream);
+
+/* Bytes of device workspace sdgs_bin_sort needs for n Gaussians, `capacity` instances and a
+ * width x height image.  Writes *bytes (host).  Errors: SDGS_ERR_INVALID_ARG. */
+int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
+                            size_t* bytes);
+
+/* Tile binning.  Sorts Gaussians by float32 depth (stable, so equal depths keep ascending id),
+ * emits one instance per tile of each visible Gaussian's rectangle in that order, stably sorts the
+ * instances by tile id, and writes the per-tile ranges: the result is the stable sort of the
+ * 64-bit keys tile_id << 32 | bits(depth).  `workspace` is device memory of at least
+ * sdgs_bin_workspace_size() bytes, 256-byte aligned.
+ * If num_instances_host is not NULL the call synchronises the stream, stores K there and returns
+ * SDGS_ERR_OVERFLOW when K > capacity; otherwise it never synchronises (K stays on the device and
+ * an overflow only truncates the lists).
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_OVERFLOW, SDGS_ERR_CUDA. */
+int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                  size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                  void* stream);
+
+/* Front-to-back compositing of each 16x16 tile's sorted instances.
+ * Per pixel: alpha_i = min(0.99, alpha_cond exp(-1/2 (a dx^2 + c dy^2) - b dx dy)), skipped when
+ * below 1/255; the pixel stops before the Gaussian that would take its transmittance below 1e-4.
+ * Writes image [height][width][3] = sum c_i alpha_i T_i + T_final bg, final_T [height][width] and
+ * n_contrib [height][width] (1 + position in the tile list of the last Gaussian blended, 0 if
+ * none).  All outputs are device float32 / uint32.  If n_evaluated (device uint64) is not NULL,
+ * the number of (pixel, Gaussian) pairs evaluated is ADDED to it (the compositing work).
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_CUDA. */
+int sdgs_render_fwd(const sdgs_projected* proj, const sdgs_bins* bins, const sdgs_view* view,
+                    float* image, float* final_T, uint32_t* n_contrib, uint64_t* n_evaluated,
+                    void* stream);
+
+/* Bytes of device workspace sdgs_render_bwd needs for n Gaussians (per-Gaussian screen-space
+ * gradients).  Writes *bytes (host). */
+int sdgs_bwd_workspace_size(int64_t n, size_t* bytes);
+
+/* Adjoint of sdgs_render_fwd, sdgs_slice_project (projection, SH, conditioning, modulation and
+ * Sigma = L L^T).  Inputs are the forward's scene, view, projected record, bins, final_T and
+ * n_contrib, and dL_dimage [height][width][3] (device).  Gradients are ADDED to `grads`.  The
+ * culling decisions, radius and tile rectangles are held fixed (they have no derivative); where
+ * the 0.99 opacity clamp or the colour clamp at 0 is active the corresponding derivative is 0.
+ * `workspace` needs sdgs_bwd_workspace_size() bytes.
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_CUDA. */
+int sdgs_render_bwd(const sdgs_scene* scene, const sdgs_view* view, const sdgs_projected* proj,
+                    const sdgs_bins* bins, const float* final_T, const uint32_t* n_contrib,
+                    const float* dL_dimage, void* workspace, size_t workspace_bytes,
+                    const sdgs_grads* grads, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDGS_H_ */

@@ -1,0 +1,208 @@
+// C-ABI entry points of libsdgs: argument validation, error reporting and dispatch to the
+// kernel launchers.  Declarations and contracts are in include/sdgs.h.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <cmath>
+
+#include "common.cuh"
+
+namespace sdgs {
+
+static thread_local char g_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_error, sizeof(g_error), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SDGS_OK;
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return SDGS_ERR_CUDA;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static int check_scene(const sdgs_scene* s) {
+  if (s == nullptr) { set_error("scene is NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (s->n < 0 || s->n >= (int64_t(1) << 31)) {
+    set_error("scene n = %lld out of range [0, 2^31)", (long long)s->n);
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (s->sh_degree != 3) { set_error("sh_degree must be 3 (got %d)", s->sh_degree); return SDGS_ERR_INVALID_ARG; }
+  if (!(s->lambda_t >= 0.f) || !(s->lambda_d >= 0.f) || !std::isfinite(s->lambda_t) ||
+      !std::isfinite(s->lambda_d)) {
+    set_error("lambda_t / lambda_d must be finite and >= 0");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (s->n > 0) {
+    if (!s->mean7 || !s->L28 || !s->opacity || !s->sh) { set_error("scene array is NULL"); return SDGS_ERR_INVALID_ARG; }
+    if (!aligned(s->L28, 16) || !aligned(s->sh, 16) || !aligned(s->mean7, 4) || !aligned(s->opacity, 4)) {
+      set_error("scene arrays must be aligned (L28 and sh to 16 bytes)");
+      return SDGS_ERR_INVALID_ARG;
+    }
+  }
+  return SDGS_OK;
+}
+
+static int check_view(const sdgs_view* v) {
+  if (v == nullptr) { set_error("view is NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (v->width <= 0 || v->height <= 0 || v->width > 65535 * kTile || v->height > 65535 * kTile) {
+    set_error("image size %d x %d out of range", v->width, v->height);
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (!(v->fx > 0.f) || !(v->fy > 0.f) || !std::isfinite(v->fx) || !std::isfinite(v->fy) ||
+      !std::isfinite(v->cx) || !std::isfinite(v->cy) || !(v->near_plane >= 0.f)) {
+    set_error("bad intrinsics or near plane");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(v->viewmat[k])) { set_error("viewmat is not finite"); return SDGS_ERR_INVALID_ARG; }
+  if (!std::isfinite(v->t) || !std::isfinite(v->d[0]) || !std::isfinite(v->d[1]) || !std::isfinite(v->d[2])) {
+    set_error("query t / d is not finite");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  return SDGS_OK;
+}
+
+static int check_projected(const sdgs_projected* p) {
+  if (p == nullptr) { set_error("projected is NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (p->n < 0 || p->n >= (int64_t(1) << 31)) { set_error("projected n out of range"); return SDGS_ERR_INVALID_ARG; }
+  if (p->n > 0) {
+    if (!p->mean2d || !p->conic_opacity || !p->rgb || !p->depth || !p->rect || !p->radius) {
+      set_error("projected array is NULL");
+      return SDGS_ERR_INVALID_ARG;
+    }
+    if (!aligned(p->mean2d, 8) || !aligned(p->conic_opacity, 16) || !aligned(p->rect, 8) ||
+        !aligned(p->rgb, 4) || !aligned(p->depth, 4) || !aligned(p->radius, 4)) {
+      set_error("projected arrays misaligned (mean2d 8, conic_opacity 16, rect 8 bytes)");
+      return SDGS_ERR_INVALID_ARG;
+    }
+  }
+  return SDGS_OK;
+}
+
+static int check_bins(const sdgs_bins* b) {
+  if (b == nullptr) { set_error("bins is NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (b->capacity < 0 || b->capacity >= (int64_t(1) << 31)) { set_error("bins capacity out of range [0, 2^31)"); return SDGS_ERR_INVALID_ARG; }
+  if (!b->ranges || !b->num_instances || (b->capacity > 0 && (!b->tile_keys || !b->point_list))) {
+    set_error("bins array is NULL");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (!aligned(b->ranges, 8) || !aligned(b->num_instances, 8)) { set_error("bins arrays misaligned"); return SDGS_ERR_INVALID_ARG; }
+  return SDGS_OK;
+}
+
+}  // namespace sdgs
+
+using namespace sdgs;
+
+#define SDGS_TRY(x)                 \
+  do {                              \
+    const int _rc = (x);            \
+    if (_rc != SDGS_OK) return _rc; \
+  } while (0)
+
+extern "C" {
+
+const char* sdgs_version(void) { return "sdgs 0.1.0 sm_103a"; }
+
+const char* sdgs_last_error(void) { return g_error; }
+
+int sdgs_slice_project(const sdgs_scene* scene, const sdgs_view* view, const sdgs_projected* out,
+                       void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_scene(scene));
+  SDGS_TRY(check_view(view));
+  SDGS_TRY(check_projected(out));
+  if (out->n != scene->n) { set_error("projected n (%lld) != scene n (%lld)", (long long)out->n, (long long)scene->n); return SDGS_ERR_INVALID_ARG; }
+  return cuda_status(launch_slice_project(*scene, *view, *out, (cudaStream_t)stream), "slice_project launch");
+}
+
+int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height, size_t* bytes) {
+  g_error[0] = 0;
+  if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || capacity >= (int64_t(1) << 31) ||
+      width <= 0 || height <= 0 || width > 65535 * kTile || height > 65535 * kTile) {
+    set_error("bad arguments to sdgs_bin_workspace_size");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  *bytes = plan_bins(n, capacity, width, height).total;
+  return SDGS_OK;
+}
+
+int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                  size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                  void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_projected(proj));
+  SDGS_TRY(check_view(view));
+  SDGS_TRY(check_bins(out));
+  const BinPlan plan = plan_bins(proj->n, out->capacity, view->width, view->height);
+  if (workspace == nullptr || workspace_bytes < plan.total || !aligned(workspace, 256)) {
+    set_error("workspace needs %zu bytes, 256-byte aligned (got %zu)", plan.total, workspace_bytes);
+    return SDGS_ERR_WORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st), "bin_sort launch"));
+  if (num_instances_host != nullptr) {
+    SDGS_TRY(cuda_status(cudaMemcpyAsync(num_instances_host, out->num_instances, sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, st), "copy instance count"));
+    SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "bin_sort synchronize"));
+    if (*num_instances_host > out->capacity) {
+      set_error("%lld instances exceed capacity %lld", (long long)*num_instances_host, (long long)out->capacity);
+      return SDGS_ERR_OVERFLOW;
+    }
+  }
+  return SDGS_OK;
+}
+
+int sdgs_render_fwd(const sdgs_projected* proj, const sdgs_bins* bins, const sdgs_view* view,
+                    float* image, float* final_T, uint32_t* n_contrib, uint64_t* n_evaluated,
+                    void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_projected(proj));
+  SDGS_TRY(check_bins(bins));
+  SDGS_TRY(check_view(view));
+  if (!image || !final_T || !n_contrib) { set_error("output image / final_T / n_contrib is NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (n_evaluated != nullptr && !aligned(n_evaluated, 8)) { set_error("n_evaluated misaligned"); return SDGS_ERR_INVALID_ARG; }
+  return cuda_status(launch_render_fwd(*proj, *bins, *view, image, final_T, n_contrib, n_evaluated,
+                                       (cudaStream_t)stream),
+                     "render_fwd launch");
+}
+
+int sdgs_bwd_workspace_size(int64_t n, size_t* bytes) {
+  g_error[0] = 0;
+  if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 31)) { set_error("bad arguments to sdgs_bwd_workspace_size"); return SDGS_ERR_INVALID_ARG; }
+  *bytes = bwd_workspace_bytes(n);
+  return SDGS_OK;
+}
+
+int sdgs_render_bwd(const sdgs_scene* scene, const sdgs_view* view, const sdgs_projected* proj,
+                    const sdgs_bins* bins, const float* final_T, const uint32_t* n_contrib,
+                    const float* dL_dimage, void* workspace, size_t workspace_bytes,
+                    const sdgs_grads* grads, void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_scene(scene));
+  SDGS_TRY(check_view(view));
+  SDGS_TRY(check_projected(proj));
+  SDGS_TRY(check_bins(bins));
+  if (proj->n != scene->n) { set_error("projected n != scene n"); return SDGS_ERR_INVALID_ARG; }
+  if (!final_T || !n_contrib || !dL_dimage || !grads || !grads->dmean7 || !grads->dL28 ||
+      !grads->dopacity || !grads->dsh) {
+    set_error("backward input or gradient pointer is NULL");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  const size_t need = bwd_workspace_bytes(scene->n);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) {
+    set_error("backward workspace needs %zu bytes, 256-byte aligned", need);
+    return SDGS_ERR_WORKSPACE;
+  }
+  return cuda_status(launch_render_bwd(*scene, *view, *proj, *bins, final_T, n_contrib, dL_dimage,
+                                       (char*)workspace, *grads, (cudaStream_t)stream),
+                     "render_bwd launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// Shared definitions of the CUDA path (kernels and C-ABI glue).  Nothing here is used by the
+// oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sdgs.h"
+
+namespace sdgs {
+
+constexpr int kTile = 16;
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kAlphaMin = 1.0f / 255.0f;  // compositing skip threshold and cull threshold
+constexpr float kAlphaMax = 0.99f;          // opacity clamp per pixel
+constexpr float kTMin = 1e-4f;              // transmittance stop threshold
+constexpr float kDilation = 0.3f;           // added to the 2D covariance diagonal
+constexpr float kJacClamp = 1.3f;           // x/z, y/z clamp (in units of tan(fov/2)) for J
+constexpr float kExtent = 3.0f;             // radius = ceil(3 sqrt(lambda_max))
+
+// Error reporting (api.cu).
+void set_error(const char* fmt, ...);
+int cuda_status(cudaError_t e, const char* what);
+
+inline int tiles_of(int px) { return (px + kTile - 1) / kTile; }
+
+// Internal launchers (one .cu each).
+cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o,
+                                 cudaStream_t st);
+
+struct BinPlan {
+  int64_t n;
+  int64_t capacity;
+  int num_tiles;
+  int tile_bits;
+  // workspace carve-up (byte offsets)
+  size_t off_dkeys[2], off_dvals[2], off_counts, off_ikeys, off_ivals, off_hist, off_partials,
+      off_scalars, total;
+  int64_t hist_blocks;  // max radix blocks over both sorts
+  int64_t partial_cap;  // entries available for scan partials
+};
+BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);
+cudaError_t launch_bin_sort(const sdgs_projected& p, const sdgs_view& v, const BinPlan& plan,
+                            char* ws, const sdgs_bins& out, cudaStream_t st);
+
+cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const sdgs_view& v,
+                              float* image, float* final_T, uint32_t* n_contrib,
+                              uint64_t* n_evaluated, cudaStream_t st);
+
+size_t bwd_workspace_bytes(int64_t n);
+cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& p,
+                              const sdgs_bins& b, const float* final_T, const uint32_t* n_contrib,
+                              const float* dL_dimage, char* ws, const sdgs_grads& g,
+                              cudaStream_t st);
+
+}  // namespace sdgs

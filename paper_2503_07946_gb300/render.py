@@ -1,0 +1,102 @@
+"""Pipeline wrappers over the C ABI: a reusable renderer and the autograd Function.
+
+These only sequence the library calls (slice_project -> bin_sort -> render_fwd, and
+render_bwd) and own the device buffers; all arithmetic is in the CUDA kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import sdgs
+
+
+def scene_to_device(scene, device="cuda") -> dict:
+    """Upload a synth.Scene (host float32 arrays) to contiguous CUDA tensors."""
+    return dict(mean7=torch.as_tensor(np.ascontiguousarray(scene.mean7), device=device),
+                L28=torch.as_tensor(np.ascontiguousarray(scene.L28), device=device),
+                opacity=torch.as_tensor(np.ascontiguousarray(scene.opacity), device=device),
+                sh=torch.as_tensor(np.ascontiguousarray(scene.sh), device=device).reshape(-1, 16, 3))
+
+
+class Renderer:
+    """Owns the projected record, bins and image buffers for one (n, width, height).
+
+    `capacity` bounds the (tile, Gaussian) instances; when a frame needs more, the bins are
+    reallocated at 1.25x the count and binning runs again.
+    """
+
+    def __init__(self, n: int, width: int, height: int, capacity: int | None = None, device="cuda"):
+        self.n, self.width, self.height, self.device = n, width, height, device
+        self.proj = sdgs.ProjectedBuffers(n, device)
+        self.bins = sdgs.BinBuffers(n, capacity if capacity is not None else max(4096, 16 * n), width,
+                                    height, device)
+        self.image = torch.empty(height, width, 3, dtype=torch.float32, device=device)
+        self.final_T = torch.empty(height, width, dtype=torch.float32, device=device)
+        self.n_contrib = torch.empty(height, width, dtype=torch.int32, device=device)
+        self.num_instances = 0
+
+    def grow(self, k: int):
+        self.bins = sdgs.BinBuffers(self.n, int(k * 1.25) + 1024, self.width, self.height, self.device)
+
+    def bin(self, view: sdgs.View, stream=None) -> int:
+        try:
+            k = sdgs.bin_sort(self.proj, view, self.bins, sync=True, stream=stream)
+        except sdgs.SdgsError as e:
+            if e.code != 3:
+                raise
+            self.grow(int(self.bins.num_instances.item()))
+            k = sdgs.bin_sort(self.proj, view, self.bins, sync=True, stream=stream)
+        self.num_instances = k
+        return k
+
+    def forward(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
+        sdgs.slice_project(scene, view, self.proj, stream)
+        self.bin(view, stream)
+        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream)
+        return self.image
+
+    def forward_async(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
+        """Same three calls without the host read of the instance count (capacity must suffice)."""
+        sdgs.slice_project(scene, view, self.proj, stream)
+        sdgs.bin_sort(self.proj, view, self.bins, sync=False, stream=stream)
+        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream)
+        return self.image
+
+
+class Render7DGS(torch.autograd.Function):
+    """image = render(mean7, L28, opacity, sh) for one view, with the CUDA adjoint as backward.
+
+    Gradients flow to all four parameter tensors; opacity is the activated alpha and L28 the
+    packed Cholesky factor as given (activations live in torch).
+    """
+
+    @staticmethod
+    def forward(ctx, mean7, L28, opacity, sh, view: sdgs.View, lambda_t: float, lambda_d: float,
+                renderer: Renderer):
+        t = dict(mean7=mean7.contiguous(), L28=L28.contiguous(), opacity=opacity.contiguous(),
+                 sh=sh.contiguous())
+        scene = sdgs.scene_struct(t, lambda_t, lambda_d)
+        image = renderer.forward(scene, view).clone()
+        ctx.renderer, ctx.view, ctx.lam = renderer, view, (lambda_t, lambda_d)
+        ctx.final_T = renderer.final_T.clone()
+        ctx.n_contrib = renderer.n_contrib.clone()
+        ctx.save_for_backward(t["mean7"], t["L28"], t["opacity"], t["sh"])
+        return image
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        mean7, L28, opacity, sh = ctx.saved_tensors
+        t = dict(mean7=mean7, L28=L28, opacity=opacity, sh=sh)
+        scene = sdgs.scene_struct(t, *ctx.lam)
+        grads = {k: torch.zeros_like(v) for k, v in t.items()}
+        r = ctx.renderer
+        ws = torch.empty(max(sdgs.bwd_workspace_size(r.n), 256), dtype=torch.uint8, device=mean7.device)
+        sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, ctx.final_T, ctx.n_contrib,
+                        grad_image.contiguous(), ws, grads)
+        return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], None, None, None, None
+
+
+def render_image(mean7, L28, opacity, sh, view: sdgs.View, lambda_t: float, lambda_d: float,
+                 renderer: Renderer) -> torch.Tensor:
+    return Render7DGS.apply(mean7, L28, opacity, sh, view, lambda_t, lambda_d, renderer)

@@ -1,0 +1,249 @@
+"""ctypes binding of libsdgs (include/sdgs.h): the same entry points, with torch tensors as memory.
+
+This module only marshals arguments: it fills the C structs with device pointers of torch
+tensors and calls the library.  Every step of the render path runs in the CUDA kernels of
+libsdgs; when the library is missing every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsdgs.so")
+
+OK = 0
+ERR_NAMES = {1: "INVALID_ARG", 2: "WORKSPACE", 3: "OVERFLOW", 4: "CUDA", 5: "TIMEOUT", 6: "BUSY",
+             7: "OOM_BUDGET", 8: "NOT_FOUND"}
+TILE = 16
+
+
+class SdgsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sdgs error {ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("mean7", ctypes.c_void_p), ("L28", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
+                ("lambda_t", ctypes.c_float), ("lambda_d", ctypes.c_float)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("viewmat", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("near_plane", ctypes.c_float), ("t", ctypes.c_float),
+                ("d", ctypes.c_float * 3), ("bg", ctypes.c_float * 3)]
+
+
+class Projected(ctypes.Structure):
+    _fields_ = [("mean2d", ctypes.c_void_p), ("conic_opacity", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
+                ("depth", ctypes.c_void_p), ("rect", ctypes.c_void_p), ("radius", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("tile_keys", ctypes.c_void_p), ("point_list", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
+                ("num_instances", ctypes.c_void_p), ("capacity", ctypes.c_int64)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("dmean7", ctypes.c_void_p), ("dL28", ctypes.c_void_p), ("dopacity", ctypes.c_void_p),
+                ("dsh", ctypes.c_void_p)]
+
+
+_lib = None
+
+# Exported symbols and their argument types; the CPU tests check this list against include/sdgs.h.
+SIGNATURES = {
+    "sdgs_version": ([], ctypes.c_char_p),
+    "sdgs_last_error": ([], ctypes.c_char_p),
+    "sdgs_slice_project": ([ctypes.POINTER(Scene), ctypes.POINTER(View), ctypes.POINTER(Projected),
+                            ctypes.c_void_p], ctypes.c_int),
+    "sdgs_bin_workspace_size": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sdgs_bin_sort": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p, ctypes.c_size_t,
+                       ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
+    "sdgs_render_fwd": ([ctypes.POINTER(Projected), ctypes.POINTER(Bins), ctypes.POINTER(View),
+                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                        ctypes.c_int),
+    "sdgs_bwd_workspace_size": ([ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sdgs_render_bwd": ([ctypes.POINTER(Scene), ctypes.POINTER(View), ctypes.POINTER(Projected),
+                         ctypes.POINTER(Bins), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(Grads), ctypes.c_void_p],
+                        ctypes.c_int),
+}
+
+
+def lib():
+    """Load libsdgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise SdgsError(rc, lib().sdgs_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libsdgs needs CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libsdgs needs contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------------------------------
+# Struct builders
+# ------------------------------------------------------------------------------------------
+
+def scene_struct(t: dict, lambda_t: float, lambda_d: float) -> Scene:
+    """t: dict of CUDA float32 tensors mean7 [N,7], L28 [N,28], opacity [N], sh [N,16,3]."""
+    n = t["mean7"].shape[0]
+    for k, w in (("mean7", 7), ("L28", 28), ("opacity", 1), ("sh", 48)):
+        if t[k].dtype != torch.float32 or t[k].numel() != n * w:
+            raise ValueError(f"scene tensor {k} must be float32 with {w} values per Gaussian")
+    return Scene(_ptr(t["mean7"]), _ptr(t["L28"]), _ptr(t["opacity"]), _ptr(t["sh"]), n, 3,
+                 float(lambda_t), float(lambda_d))
+
+
+def view_struct(cam) -> View:
+    """From a synth.Camera (or anything with the same attributes)."""
+    v = View()
+    vm = np.asarray(cam.viewmat, dtype=np.float64).reshape(16)
+    for i in range(16):
+        v.viewmat[i] = float(vm[i])
+    v.fx, v.fy, v.cx, v.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    v.width, v.height = int(cam.width), int(cam.height)
+    v.near_plane = float(getattr(cam, "near", 0.2))
+    v.t = float(cam.t)
+    for i in range(3):
+        v.d[i] = float(cam.d[i])
+        v.bg[i] = float(cam.bg[i])
+    return v
+
+
+class ProjectedBuffers:
+    """Device buffers of the per-Gaussian screen-space record."""
+
+    def __init__(self, n: int, device="cuda"):
+        self.n = n
+        self.mean2d = torch.empty(n, 2, dtype=torch.float32, device=device)
+        self.conic_opacity = torch.empty(n, 4, dtype=torch.float32, device=device)
+        self.rgb = torch.empty(n, 3, dtype=torch.float32, device=device)
+        self.depth = torch.empty(n, dtype=torch.float32, device=device)
+        self.rect = torch.empty(n, 4, dtype=torch.int16, device=device)  # uint16 bit pattern
+        self.radius = torch.empty(n, dtype=torch.int32, device=device)
+
+    def struct(self) -> Projected:
+        return Projected(_ptr(self.mean2d), _ptr(self.conic_opacity), _ptr(self.rgb), _ptr(self.depth),
+                         _ptr(self.rect), _ptr(self.radius), self.n)
+
+    @staticmethod
+    def from_host(rec: dict, device="cuda") -> "ProjectedBuffers":
+        """Upload screen-space records (e.g. synth.random_projected) for the binning / raster calls."""
+        n = rec["mean2d"].shape[0]
+        p = ProjectedBuffers(n, device)
+        p.mean2d.copy_(torch.as_tensor(np.asarray(rec["mean2d"], np.float32)))
+        co = np.concatenate([np.asarray(rec["conic"], np.float32),
+                             np.asarray(rec["opacity"], np.float32)[:, None]], 1)
+        p.conic_opacity.copy_(torch.as_tensor(co))
+        p.rgb.copy_(torch.as_tensor(np.asarray(rec["rgb"], np.float32)))
+        p.depth.copy_(torch.as_tensor(np.asarray(rec["depth"], np.float32)))
+        p.rect.copy_(torch.as_tensor(np.asarray(rec["rect"]).astype(np.uint16).view(np.int16)))
+        p.radius.zero_()
+        return p
+
+    def rect_host(self) -> np.ndarray:
+        return self.rect.cpu().numpy().view(np.uint16).astype(np.int64)
+
+
+class BinBuffers:
+    """Sorted instance lists, tile ranges and the workspace of sdgs_bin_sort."""
+
+    def __init__(self, n: int, capacity: int, width: int, height: int, device="cuda"):
+        self.n, self.capacity, self.width, self.height = n, int(capacity), width, height
+        self.num_tiles = ((width + TILE - 1) // TILE) * ((height + TILE - 1) // TILE)
+        self.tile_keys = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
+        self.point_list = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
+        self.ranges = torch.empty(self.num_tiles, 2, dtype=torch.int32, device=device)
+        self.num_instances = torch.zeros(1, dtype=torch.int64, device=device)
+        self.ws_bytes = bin_workspace_size(n, self.capacity, width, height)
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
+
+    def struct(self) -> Bins:
+        return Bins(_ptr(self.tile_keys), _ptr(self.point_list), _ptr(self.ranges), _ptr(self.num_instances),
+                    self.capacity)
+
+
+# ------------------------------------------------------------------------------------------
+# Entry points (same names as the C ABI, minus the prefix)
+# ------------------------------------------------------------------------------------------
+
+def version() -> str:
+    return lib().sdgs_version().decode()
+
+
+def slice_project(scene: Scene, view: View, out: ProjectedBuffers, stream=None):
+    _check(lib().sdgs_slice_project(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(out.struct()),
+                                    _stream(stream)))
+
+
+def bin_workspace_size(n: int, capacity: int, width: int, height: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().sdgs_bin_workspace_size(n, capacity, width, height, ctypes.byref(b)))
+    return int(b.value)
+
+
+def bin_sort(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = True, stream=None):
+    """Returns the instance count K when sync=True (raises SdgsError(OVERFLOW) when K > capacity)."""
+    k = ctypes.c_int64(0)
+    _check(lib().sdgs_bin_sort(ctypes.byref(proj.struct()), ctypes.byref(view), _ptr(bins.workspace),
+                               bins.ws_bytes, ctypes.byref(bins.struct()),
+                               ctypes.byref(k) if sync else None, _stream(stream)))
+    return int(k.value) if sync else None
+
+
+def render_fwd(proj: ProjectedBuffers, bins: BinBuffers, view: View, image: torch.Tensor,
+               final_T: torch.Tensor, n_contrib: torch.Tensor, n_evaluated: torch.Tensor | None = None,
+               stream=None):
+    _check(lib().sdgs_render_fwd(ctypes.byref(proj.struct()), ctypes.byref(bins.struct()), ctypes.byref(view),
+                                 _ptr(image), _ptr(final_T), _ptr(n_contrib), _ptr(n_evaluated),
+                                 _stream(stream)))
+
+
+def bwd_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().sdgs_bwd_workspace_size(n, ctypes.byref(b)))
+    return int(b.value)
+
+
+def render_bwd(scene: Scene, view: View, proj: ProjectedBuffers, bins: BinBuffers, final_T: torch.Tensor,
+               n_contrib: torch.Tensor, dL_dimage: torch.Tensor, workspace: torch.Tensor, grads: dict,
+               stream=None):
+    g = Grads(_ptr(grads["mean7"]), _ptr(grads["L28"]), _ptr(grads["opacity"]), _ptr(grads["sh"]))
+    _check(lib().sdgs_render_bwd(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(proj.struct()),
+                                 ctypes.byref(bins.struct()), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
+                                 _ptr(workspace), workspace.numel(), ctypes.byref(g), _stream(stream)))

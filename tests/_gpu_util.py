@@ -1,0 +1,79 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI and fetch results."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from paper_2503_07946_gb300 import render as prender
+from paper_2503_07946_gb300 import sdgs
+
+
+def gpu_project(scene, cam):
+    """sdgs_slice_project on a synth.Scene; returns host copies of the projected record."""
+    dev = prender.scene_to_device(scene)
+    st = sdgs.scene_struct(dev, scene.lambda_t, scene.lambda_d)
+    view = sdgs.view_struct(cam)
+    proj = sdgs.ProjectedBuffers(scene.n)
+    sdgs.slice_project(st, view, proj)
+    torch.cuda.synchronize()
+    return dict(mean2d=proj.mean2d.cpu().numpy(), conic_opacity=proj.conic_opacity.cpu().numpy(),
+                rgb=proj.rgb.cpu().numpy(), depth=proj.depth.cpu().numpy(), rect=proj.rect_host(),
+                radius=proj.radius.cpu().numpy()), (dev, st, view, proj)
+
+
+def gpu_bin(proj: sdgs.ProjectedBuffers, view, capacity=None):
+    n = proj.n
+    bins = sdgs.BinBuffers(n, capacity if capacity is not None else max(1024, 64 * max(n, 1)),
+                           view.width, view.height)
+    k = sdgs.bin_sort(proj, view, bins, sync=True)
+    keys = bins.tile_keys[:k].cpu().numpy().view(np.uint32) if k else np.zeros(0, np.uint32)
+    vals = bins.point_list[:k].cpu().numpy().view(np.uint32) if k else np.zeros(0, np.uint32)
+    ranges = bins.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
+    return k, keys, vals, ranges, bins
+
+
+def gpu_render(proj, bins, view):
+    H, W = view.height, view.width
+    image = torch.empty(H, W, 3, dtype=torch.float32, device="cuda")
+    final_T = torch.empty(H, W, dtype=torch.float32, device="cuda")
+    n_contrib = torch.empty(H, W, dtype=torch.int32, device="cuda")
+    sdgs.render_fwd(proj, bins, view, image, final_T, n_contrib)
+    torch.cuda.synchronize()
+    return image.cpu().numpy(), final_T.cpu().numpy(), n_contrib.cpu().numpy()
+
+
+def oracle_records_f32(g: dict) -> dict:
+    """The oracle's own per-Gaussian screen-space record rounded to float32 (culled -> empty rect)."""
+    vis = g["visible"].numpy()
+    rect = g["rect"].numpy().copy()
+    rect[~vis] = 0
+    return dict(mean2d=g["mean2d"].detach().numpy().astype(np.float32),
+                conic=g["conic"].detach().numpy().astype(np.float32),
+                opacity=g["alpha_cond"].detach().numpy().astype(np.float32),
+                rgb=g["rgb"].detach().numpy().astype(np.float32),
+                depth=np.where(vis, g["depth"].detach().numpy(), 1.0).astype(np.float32),
+                rect=rect)
+
+
+# Decision margins (relative or in pixels) below which an FP32 evaluation may legitimately decide
+# the other way from the FP64 oracle.
+Z_REL = 1e-5
+RADIUS_REL = 2e-6
+EDGE_PX = 5e-3
+PIX_ALPHA = 1e-4
+PIX_T = 1e-4
+PIX_DEPTH = 2e-6
+
+
+def boundary_gaussians(g: dict) -> np.ndarray:
+    m = g["margins"]
+    vis_any = np.ones(g["visible"].shape[0], bool)
+    return vis_any & ((m["z_rel"].numpy() < Z_REL) | (m["radius_rel"].numpy() < RADIUS_REL)
+                      | (m["edge_px"].numpy() < EDGE_PX))
+
+
+def pixel_ok(margin_alpha, margin_T, margin_depth=None):
+    ok = (np.asarray(margin_alpha) >= PIX_ALPHA) & (np.asarray(margin_T) >= PIX_T)
+    if margin_depth is not None:
+        ok &= np.asarray(margin_depth) >= PIX_DEPTH
+    return ok

@@ -1,0 +1,144 @@
+"""Parity of the CUDA forward path (through the C ABI) with the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import binning, render
+import _gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+COLOUR_TOL = 2e-4  # max-abs per channel, FP32 CUDA vs FP64 oracle
+
+
+def _cams():
+    """Config 0's camera, a rotated ragged-size camera, and a config-1-like camera."""
+    c0 = synth.config_cameras(0)[0]
+    c1 = synth.make_camera((1.2, -0.8, -2.6), 141, 97, 55.0, 0.3, bg=(0.2, 0.4, 0.6))
+    c2 = synth.config_cameras(1, count=1, width=160, height=120)[0]
+    return [c0, c1, c2]
+
+
+@pytest.fixture(scope="module")
+def scene0():
+    return synth.config_scene(0)
+
+
+@pytest.mark.parametrize("ci", [0, 1, 2])
+def test_slice_project_records(scene0, ci):
+    cam = _cams()[ci]
+    got, _ = U.gpu_project(scene0, cam)
+    g = render.gaussians(render.params_from_scene(scene0), cam, scene0.lambda_t, scene0.lambda_d)
+    vis_o = g["visible"].numpy()
+    vis_g = (got["rect"][:, 2] > got["rect"][:, 0]) & (got["rect"][:, 3] > got["rect"][:, 1])
+    border = U.boundary_gaussians(g)
+    assert np.array_equal(vis_o[~border], vis_g[~border])
+    both = vis_o & vis_g & ~border
+    assert both.sum() > 100
+    np.testing.assert_array_equal(got["rect"][both], g["rect"].numpy()[both])
+    np.testing.assert_array_equal(got["radius"][both], g["radius"].numpy()[both].astype(np.int32))
+    # FP32 conditioning: the shift Sigma_p,(t,d) Sigma_(t,d)^-1 (x - mu) carries ~1e-6 relative error
+    np.testing.assert_allclose(got["mean2d"][both], g["mean2d"].numpy()[both], rtol=0, atol=5e-3)
+    np.testing.assert_allclose(got["depth"][both], g["depth"].numpy()[both], rtol=5e-5)
+    co = got["conic_opacity"][both]
+    cref = g["conic"].numpy()[both]
+    scale = np.abs(cref).max(1, keepdims=True)
+    np.testing.assert_allclose(co[:, :3] / scale, cref / scale, rtol=0, atol=1e-4)
+    np.testing.assert_allclose(co[:, 3], g["alpha_cond"].numpy()[both], rtol=2e-5, atol=1e-7)
+    np.testing.assert_allclose(got["rgb"][both], g["rgb"].numpy()[both], rtol=0, atol=2e-5)
+
+
+def _random_bin_cases():
+    return [
+        (0, 64, 64, 0),          # no Gaussians
+        (1, 16, 16, 1),          # one tile: zero tile bits, no tile pass
+        (300, 100, 70, 2),       # ragged image, 7 x 5 tiles
+        (5000, 256, 256, 3),     # one tile pass, several radix blocks of Gaussians
+        (20000, 1352, 1014, 4),  # two tile passes (5440 tiles), K spans many blocks
+        (3000, 1920, 1080, 5),   # 8160 tiles
+    ]
+
+
+@pytest.mark.parametrize("n,W,H,seed", _random_bin_cases())
+def test_bin_sort_bit_exact_on_random_records(n, W, H, seed):
+    rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=12)
+    proj = U.sdgs.ProjectedBuffers.from_host(rec)
+    view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5))
+    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], (W + 15) // 16)
+    k, keys, vals, ranges, _ = U.gpu_bin(proj, view, capacity=len(okeys) + 7)
+    assert k == len(okeys)
+    np.testing.assert_array_equal(keys.astype(np.uint64), okeys >> np.uint64(32))
+    np.testing.assert_array_equal(vals, ovals)
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    np.testing.assert_array_equal(ranges, binning.tile_ranges(okeys, tiles))
+
+
+def test_bin_sort_overflow_is_reported_and_safe():
+    rec = synth.random_projected(2000, 256, 256, seed=7)
+    proj = U.sdgs.ProjectedBuffers.from_host(rec)
+    view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), 256, 256, 60.0, 0.5))
+    okeys, _ = binning.sort_keys(rec["depth"], rec["rect"], 16)
+    with pytest.raises(U.sdgs.SdgsError) as e:
+        U.gpu_bin(proj, view, capacity=len(okeys) // 3)
+    assert e.value.code == 3
+    # the truncated lists still render without faulting
+    bins = U.sdgs.BinBuffers(2000, len(okeys) // 3, 256, 256)
+    U.sdgs.bin_sort(proj, view, bins, sync=False)
+    U.gpu_render(proj, bins, view)
+    k, _, _, _, _ = U.gpu_bin(proj, view, capacity=len(okeys))
+    assert k == len(okeys)
+
+
+@pytest.mark.parametrize("ci", [0, 1, 2])
+def test_bin_and_render_on_oracle_records(scene0, ci):
+    """Binning + compositing given the oracle's float32-rounded screen-space records."""
+    cam = _cams()[ci]
+    g = render.gaussians(render.params_from_scene(scene0), cam, scene0.lambda_t, scene0.lambda_d)
+    rec = U.oracle_records_f32(g)
+    proj = U.sdgs.ProjectedBuffers.from_host(rec)
+    view = U.sdgs.view_struct(cam)
+    k, keys, vals, ranges, bins = U.gpu_bin(proj, view)
+    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], cam.tiles_x)
+    assert k == len(okeys) and k > 0
+    np.testing.assert_array_equal(vals, ovals)
+    np.testing.assert_array_equal(keys.astype(np.uint64), okeys >> np.uint64(32))
+    img, T, nc = U.gpu_render(proj, bins, view)
+    ref = render.render_projected(rec, cam.width, cam.height, cam.bg)
+    ok = U.pixel_ok(ref["margin_alpha"].numpy(), ref["margin_T"].numpy())
+    assert ok.mean() > 0.99
+    err = np.abs(img - ref["image"].numpy()).max(-1)
+    assert err[ok].max() <= COLOUR_TOL, err[ok].max()
+    np.testing.assert_allclose(T[ok], ref["final_T"].numpy()[ok], atol=COLOUR_TOL)
+    np.testing.assert_array_equal(nc[ok], ref["n_contrib"].numpy()[ok])
+
+
+@pytest.mark.parametrize("ci", [0, 1, 2])
+def test_render_end_to_end_against_fp64_oracle(scene0, ci):
+    cam = _cams()[ci]
+    got, (dev, st, view, proj) = U.gpu_project(scene0, cam)
+    k, _, _, _, bins = U.gpu_bin(proj, view)
+    img, T, nc = U.gpu_render(proj, bins, view)
+    ref = render.render(scene0, cam)
+    g = ref["g"]
+    # A Gaussian whose tile rectangle FP32 decides differently must lie within the FP32 margin of
+    # a decision boundary; the tiles where the two rectangles differ are set aside.
+    orect = g["rect"].numpy()
+    differ = np.nonzero((got["rect"] != orect).any(1))[0]
+    assert U.boundary_gaussians(g)[differ].all(), differ
+    excl = np.zeros((cam.tiles_y, cam.tiles_x), bool)
+    for i in differ:
+        a = np.zeros_like(excl)
+        b = np.zeros_like(excl)
+        a[got["rect"][i, 1]:got["rect"][i, 3], got["rect"][i, 0]:got["rect"][i, 2]] = True
+        b[orect[i, 1]:orect[i, 3], orect[i, 0]:orect[i, 2]] = True
+        excl |= a ^ b
+    excl_pix = np.kron(excl, np.ones((16, 16), bool))[:cam.height, :cam.width]
+    ok = U.pixel_ok(ref["margin_alpha"].numpy(), ref["margin_T"].numpy(), ref["margin_depth"].numpy())
+    ok &= ~excl_pix
+    assert ok.mean() > 0.9, ok.mean()
+    err = np.abs(img - ref["image"].numpy()).max(-1)
+    assert err[ok].max() <= COLOUR_TOL, err[ok].max()
+    np.testing.assert_array_equal(nc[ok], ref["n_contrib"].numpy()[ok])
