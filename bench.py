@@ -177,12 +177,9 @@ def run_reference(args, rank: int, world: int):
 
 def launches_per_frame(n: int, width: int, height: int) -> int:
     """Kernels libsdgs launches for one render: slice_project; depth keys; 4 depth radix passes
-    (upsweep, 3 scan kernels, downsweep); tile counts; 3-kernel scan; duplicate; the tile radix
-    passes; tile ranges; the rasteriser."""
-    tiles = ((width + 15) // 16) * ((height + 15) // 16)
-    bits = max(0, math.ceil(math.log2(tiles))) if tiles > 1 else 0
-    tile_passes = (bits + 7) // 8
-    return 1 + 1 + 4 * 5 + 1 + 3 + 1 + tile_passes * 5 + 1 + 1
+    (upsweep, 3 scan kernels, downsweep); the per-chunk tile histogram; a 3-kernel scan; the
+    scatter into tile lists; tile ranges; the rasteriser."""
+    return 1 + 1 + 4 * 5 + 1 + 3 + 1 + 1 + 1
 
 
 def cpu_baseline(scene, cam) -> dict:
@@ -264,6 +261,15 @@ def run_ours(args, rank: int, world: int):
     evals = int(n_eval.item())
     k_inst = int(r.bins.num_instances.item())
     visible = int(((r.proj.rect[:, 2] > r.proj.rect[:, 0]) & (r.proj.rect[:, 3] > r.proj.rect[:, 1])).sum())
+
+    if args.frames_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * W * H / (ms * 1e-3) / 1e6, "unit": "Mpix/s",
+                              "ms_per_step": ms, "frames_only": True,
+                              "phases_ms": {"slice_project": float(phase[:, 0].mean()),
+                                            "bin_sort": float(phase[:, 1].mean()),
+                                            "render_fwd": float(phase[:, 2].mean())}}), flush=True)
+        return
 
     # ---- end to end: the public API with the image read back to pinned host memory ----
     host_img = torch.empty(H, W, 3, dtype=torch.float32, pin_memory=True)
@@ -369,6 +375,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames-only", action="store_true",
+                    help="time the forward frames only (no e2e, fwd+bwd or CPU baseline); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -107,13 +107,13 @@ typedef struct sdgs_projected {
 } sdgs_projected;
 
 /* Output of sdgs_bin_sort (device, caller-allocated).
- *   tile_keys  [capacity] uint32 tile id of each sorted instance
+ *   tile_keys  [capacity] uint32 tile id of each sorted instance, or NULL to skip writing it
  *   point_list [capacity] uint32 Gaussian id of each sorted instance; instances are ordered by
  *              (tile id, float32 depth, Gaussian id)
  *   ranges     [tiles_x * tiles_y][2] uint32 [start, end) of each tile in the sorted lists
- *   num_instances  device int64: total instance count K written by the call (may exceed capacity,
- *              in which case only the first `capacity` instances in (depth, id) emission order
- *              are kept and SDGS_ERR_OVERFLOW is reported when the call synchronises)
+ *   num_instances  device int64: total instance count K written by the call.  It may exceed
+ *              capacity; then only sorted positions below capacity are stored, ranges are clipped
+ *              to capacity, and SDGS_ERR_OVERFLOW is reported when the call synchronises.
  *   capacity   number of entries allocated in tile_keys / point_list (< 2^31) */
 typedef struct sdgs_bins {
   uint32_t* tile_keys;
@@ -156,7 +156,8 @@ int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t 
  * emits one instance per tile of each visible Gaussian's rectangle in that order, stably sorts the
  * instances by tile id, and writes the per-tile ranges: the result is the stable sort of the
  * 64-bit keys tile_id << 32 | bits(depth).  `workspace` is device memory of at least
- * sdgs_bin_workspace_size() bytes, 256-byte aligned.
+ * sdgs_bin_workspace_size() bytes, 256-byte aligned.  Images up to 56,000 tiles are supported
+ * (e.g. 3840 x 3840); larger ones return SDGS_ERR_INVALID_ARG.
  * If num_instances_host is not NULL the call synchronises the stream, stores K there and returns
  * SDGS_ERR_OVERFLOW when K > capacity; otherwise it never synchronises (K stays on the device and
  * an overflow only truncates the lists).

@@ -88,7 +88,7 @@ static int check_projected(const sdgs_projected* p) {
 static int check_bins(const sdgs_bins* b) {
   if (b == nullptr) { set_error("bins is NULL"); return SDGS_ERR_INVALID_ARG; }
   if (b->capacity < 0 || b->capacity >= (int64_t(1) << 31)) { set_error("bins capacity out of range [0, 2^31)"); return SDGS_ERR_INVALID_ARG; }
-  if (!b->ranges || !b->num_instances || (b->capacity > 0 && (!b->tile_keys || !b->point_list))) {
+  if (!b->ranges || !b->num_instances || (b->capacity > 0 && !b->point_list)) {
     set_error("bins array is NULL");
     return SDGS_ERR_INVALID_ARG;
   }
@@ -140,6 +140,11 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
   SDGS_TRY(check_projected(proj));
   SDGS_TRY(check_view(view));
   SDGS_TRY(check_bins(out));
+  if (bin_smem_bytes(view->width, view->height) > kMaxBinSmem) {
+    set_error("image of %d x %d tiles exceeds the binning limit (%zu bytes of tile counters)",
+              (view->width + kTile - 1) / kTile, (view->height + kTile - 1) / kTile, kMaxBinSmem);
+    return SDGS_ERR_INVALID_ARG;
+  }
   const BinPlan plan = plan_bins(proj->n, out->capacity, view->width, view->height);
   if (workspace == nullptr || workspace_bytes < plan.total || !aligned(workspace, 256)) {
     set_error("workspace needs %zu bytes, 256-byte aligned (got %zu)", plan.total, workspace_bytes);

@@ -1,16 +1,19 @@
-// Tile binning: the stable sort of (tile << 32 | depth bits) instance keys, done as an LSD radix
-// sort whose depth digits are sorted BEFORE the instances are duplicated.
+// Tile binning: the stable sort of the (tile << 32 | float32 depth bits) instance keys as an LSD
+// sort in two digits -- depth first, then tile -- arranged so that neither pass touches more
+// data than it must.
 //
-// Every instance of one Gaussian carries the same depth, and duplication emits instances in the
-// order of the Gaussians it is given.  So the low (depth) passes of an LSD sort over the K
-// instances give the same order as sorting the n Gaussians by depth first (stable, id order for
-// ties) and emitting their instances in that order.  Only the tile digits are then sorted over
-// the K instances: ceil(log2(tiles) / 8) passes instead of ceil((log2(tiles) + 32) / 8).
+// Depth digit: every instance of one Gaussian carries that Gaussian's depth, and instances are
+// emitted in the order of the Gaussians.  So the depth passes of an LSD sort over the K instances
+// give the same order as a stable radix sort of the n Gaussians by depth (ties keep ascending id)
+// followed by emission in that order.  That sort runs over n keys, not K.
 //
-// Each radix pass is reduce-then-scan with no inter-block waiting: an upsweep writes a per-block
-// digit histogram (digit-major), a device-wide exclusive scan turns it into block offsets, and a
-// downsweep ranks the block's keys stably (warp match + per-warp counters) and scatters them
-// through shared memory so that runs of one digit are written contiguously.
+// Tile digit: one stable counting pass over the depth-ordered Gaussians that writes every
+// instance exactly once, straight into its tile's list (see the kernels below).
+//
+// The depth radix passes are reduce-then-scan with no inter-block waiting: an upsweep writes a
+// per-block digit histogram (digit-major), a device-wide exclusive scan turns it into block
+// offsets, and a downsweep ranks the block's keys stably (warp match + per-warp counters) and
+// scatters them through shared memory so that runs of one digit are written contiguously.
 #include "common.cuh"
 
 namespace sdgs {
@@ -296,72 +299,169 @@ __device__ __forceinline__ ushort4 clip_rect(ushort4 r, int tiles_x, int tiles_y
   return r;
 }
 
-__global__ void tile_counts_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                                   int64_t n, int tiles_x, int tiles_y, uint32_t* __restrict__ counts) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const ushort4 r = clip_rect(rect[order[s]], tiles_x, tiles_y);
-  const int w = (int)r.z - (int)r.x, h = (int)r.w - (int)r.y;
-  counts[s] = (w > 0 && h > 0) ? (uint32_t)(w * h) : 0u;
-}
+// ------------------------------------------------------------------------------------------
+// Stable counting sort of the instances by tile, in one pass over the depth-sorted Gaussians.
+//
+// The depth-ordered Gaussians are cut into chunks of G.  (1) Each chunk counts, per tile, how
+// many of its Gaussians' rectangles cover that tile, with a 2D difference array in shared memory
+// (four atomics per Gaussian, then prefix sums along x and y).  (2) One exclusive scan over the
+// tile-major (tile, chunk) count matrix gives every chunk its first output position per tile.
+// (3) Each chunk walks its Gaussians in depth order with one warp: the lanes cover the current
+// Gaussian's rectangle, each writing the Gaussian's id at its tile's cursor and advancing it.
+// Instances of one tile therefore land in (depth, id) order, exactly the stable sort by
+// (tile, depth) key.  Per-tile ranges come straight from the scanned matrix.
+// ------------------------------------------------------------------------------------------
 
-__global__ void duplicate_kernel(const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets,
-                                 const ushort4* __restrict__ rect, int tiles_x, int tiles_y, int64_t n,
-                                 int64_t cap, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const uint32_t g = order[s];
-  const ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
-  if (!(r.z > r.x && r.w > r.y)) return;
-  uint64_t off = offsets[s];
-  for (int y = r.y; y < r.w; ++y) {
-    for (int x = r.x; x < r.z; ++x) {
-      if (off >= (uint64_t)cap) return;
-      tile_keys[off] = (uint32_t)(y * tiles_x + x);
-      vals[off] = g;
-      ++off;
+constexpr int kHistThreads = 256;
+
+__global__ void __launch_bounds__(kHistThreads)
+chunk_hist_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t n,
+                  int G, int tiles_x, int tiles_y, int64_t chunks, uint32_t* __restrict__ counts) {
+  extern __shared__ int s_diff[];  // (tiles_y + 1) x (tiles_x + 1)
+  const int W1 = tiles_x + 1, H1 = tiles_y + 1;
+  for (int i = threadIdx.x; i < W1 * H1; i += kHistThreads) s_diff[i] = 0;
+  __syncthreads();
+  const int64_t s0 = (int64_t)blockIdx.x * G;
+  const int64_t s1 = min(n, s0 + G);
+  for (int64_t s = s0 + threadIdx.x; s < s1; s += kHistThreads) {
+    const ushort4 r = clip_rect(rect[order[s]], tiles_x, tiles_y);
+    if (r.z > r.x && r.w > r.y) {
+      atomicAdd(&s_diff[r.y * W1 + r.x], 1);
+      atomicAdd(&s_diff[r.y * W1 + r.z], -1);
+      atomicAdd(&s_diff[r.w * W1 + r.x], -1);
+      atomicAdd(&s_diff[r.w * W1 + r.z], 1);
+    }
+  }
+  __syncthreads();
+  // prefix sums along x (one warp per row), then along y (one warp per column)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int row = warp; row < tiles_y; row += kHistThreads / 32) {
+    int carry = 0;
+    for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+      const int x = x0 + lane;
+      int v = x < tiles_x ? s_diff[row * W1 + x] : 0;
+      v = warp_inclusive_scan(v) + carry;
+      if (x < tiles_x) s_diff[row * W1 + x] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  for (int x0 = warp * 32; x0 < tiles_x; x0 += kHistThreads) {
+    const int x = x0 + lane;
+    if (x < tiles_x) {
+      int run = 0;
+      for (int y = 0; y < tiles_y; ++y) {
+        run += s_diff[y * W1 + x];
+        counts[(int64_t)(y * tiles_x + x) * chunks + blockIdx.x] = (uint32_t)run;
+      }
     }
   }
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t cap,
-                              uint2* __restrict__ ranges) {
-  const int64_t n = element_count(nptr, 0, cap);
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const uint32_t t = keys[j];
-  if (j == 0 || keys[j - 1] != t) ranges[t].x = (uint32_t)j;
-  if (j == n - 1 || keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
+constexpr int kScatterWarps = 1;
+
+__global__ void __launch_bounds__(32 * kScatterWarps)
+chunk_scatter_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t n,
+                     int G, int tiles_x, int tiles_y, int64_t chunks, const uint64_t* __restrict__ base,
+                     int64_t cap, uint32_t* __restrict__ point_list, uint32_t* __restrict__ tile_keys) {
+  extern __shared__ uint32_t s_cur[];  // one cursor per tile
+  const int tiles = tiles_x * tiles_y;
+  const int lane = threadIdx.x;
+  const int64_t chunk = blockIdx.x;
+  for (int t = lane; t < tiles; t += 32) {
+    const uint64_t b = base[(int64_t)t * chunks + chunk];
+    s_cur[t] = (uint32_t)(b < (uint64_t)cap ? b : (uint64_t)cap);
+  }
+  __syncwarp();
+  const int64_t s0 = chunk * G;
+  const int64_t s1 = min(n, s0 + G);
+  for (int64_t sg = s0; sg < s1; sg += 32) {
+    // each lane fetches one Gaussian of the group; they are then handled one at a time
+    uint32_t g = 0;
+    ushort4 r = make_ushort4(0, 0, 0, 0);
+    if (sg + lane < s1) {
+      g = order[sg + lane];
+      r = clip_rect(rect[g], tiles_x, tiles_y);
+    }
+    const int m = (int)min((int64_t)32, s1 - sg);
+    for (int i = 0; i < m; ++i) {
+      const uint32_t gi = __shfl_sync(0xffffffffu, g, i);
+      const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, i);
+      const int ry0 = __shfl_sync(0xffffffffu, (int)r.y, i);
+      const int w = __shfl_sync(0xffffffffu, (int)r.z, i) - rx0;
+      const int h = __shfl_sync(0xffffffffu, (int)r.w, i) - ry0;
+      if (w > 0 && h > 0) {
+        const int cnt = w * h;
+        int dy = lane / w, dx = lane - dy * w;  // position of this lane's first tile
+        const int step_y = 32 / w, step_x = 32 - step_y * w;
+        for (int k = lane; k < cnt; k += 32) {
+          const int t = (ry0 + dy) * tiles_x + rx0 + dx;
+          const uint32_t p = s_cur[t];
+          s_cur[t] = p + 1;
+          if (p < (uint32_t)cap) {
+            point_list[p] = gi;
+            if (tile_keys != nullptr) tile_keys[p] = (uint32_t)t;
+          }
+          dx += step_x;
+          dy += step_y;
+          if (dx >= w) { dx -= w; ++dy; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void ranges_from_base_kernel(const uint64_t* __restrict__ base, int tiles, int64_t chunks,
+                                        const int64_t* __restrict__ total, int64_t cap,
+                                        uint2* __restrict__ ranges) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tiles) return;
+  const uint64_t k = (uint64_t)*total;
+  const uint64_t st = base[(int64_t)t * chunks];
+  const uint64_t en = (t + 1 < tiles) ? base[(int64_t)(t + 1) * chunks] : k;
+  ranges[t] = make_uint2((uint32_t)(st < (uint64_t)cap ? st : cap), (uint32_t)(en < (uint64_t)cap ? en : cap));
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Chunk size: 256 Gaussians, grown so that the (tile, chunk) matrix stays within 8M entries.
+int chunk_size(int64_t n, int tiles) {
+  int64_t G = 256;
+  while (G < (int64_t(1) << 20) && ((n + G - 1) / G) * (int64_t)tiles > (int64_t(8) << 20)) G *= 2;
+  return (int)G;
+}
+
 }  // namespace
+
+size_t bin_smem_bytes(int width, int height) {
+  const size_t hist = sizeof(int) * (size_t)(tiles_of(width) + 1) * (tiles_of(height) + 1);
+  const size_t cur = sizeof(uint32_t) * (size_t)tiles_of(width) * tiles_of(height);
+  return hist > cur ? hist : cur;
+}
 
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   BinPlan p;
   p.n = n;
   p.capacity = capacity;
   p.num_tiles = tiles_of(width) * tiles_of(height);
-  int bits = 0;
-  while ((1ll << bits) < p.num_tiles) ++bits;
-  p.tile_bits = bits;
+  p.tile_bits = 0;
+  p.chunk = chunk_size(n, p.num_tiles);
+  p.chunks = (n + p.chunk - 1) / p.chunk;
   const int64_t nb_d = (n + kRadixTile - 1) / kRadixTile;
-  const int64_t nb_i = (capacity + kRadixTile - 1) / kRadixTile;
-  p.hist_blocks = nb_d > nb_i ? nb_d : nb_i;
-  const int64_t hist_entries = (int64_t)kBins * p.hist_blocks;
+  p.hist_blocks = nb_d;
+  const int64_t hist_entries = (int64_t)kBins * nb_d;
+  const int64_t mat = (int64_t)p.num_tiles * p.chunks;
   const int64_t part_a = (hist_entries + kScanChunk - 1) / kScanChunk;
-  const int64_t part_b = (n + kScanChunk - 1) / kScanChunk;
+  const int64_t part_b = (mat + kScanChunk - 1) / kScanChunk;
   p.partial_cap = (part_a > part_b ? part_a : part_b) + 1;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) { p.off_dkeys[k] = off; off += align256(sizeof(uint32_t) * n); }
   for (int k = 0; k < 2; ++k) { p.off_dvals[k] = off; off += align256(sizeof(uint32_t) * n); }
-  p.off_counts = off; off += align256(sizeof(uint64_t) * (n + 1));
-  p.off_ikeys = off; off += align256(sizeof(uint32_t) * capacity);
-  p.off_ivals = off; off += align256(sizeof(uint32_t) * capacity);
+  p.off_counts = off; off += align256(sizeof(uint32_t) * mat);
+  p.off_base = off; off += align256(sizeof(uint64_t) * mat);
   p.off_hist = off; off += align256(sizeof(uint32_t) * hist_entries);
   p.off_partials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
-  p.off_scalars = off; off += align256(sizeof(uint64_t) * 8);
   p.total = off;
   return p;
 }
@@ -374,49 +474,41 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
                         reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[1])};
   uint32_t* dvals[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dvals[0]),
                         reinterpret_cast<uint32_t*>(ws + plan.off_dvals[1])};
-  uint64_t* offsets = reinterpret_cast<uint64_t*>(ws + plan.off_counts);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + plan.off_counts);
+  uint64_t* base = reinterpret_cast<uint64_t*>(ws + plan.off_base);
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + plan.off_hist);
   uint64_t* partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
   const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
 
-  cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)plan.num_tiles, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(out.num_instances, 0, sizeof(int64_t), st);
-  if (e != cudaSuccess) return e;
-  if (n == 0) return cudaGetLastError();
-
+  cudaError_t e;
+  if (n == 0) {
+    e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)plan.num_tiles, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(out.num_instances, 0, sizeof(int64_t), st);
+  }
   const int tb = 256;
   const unsigned gb = (unsigned)((n + tb - 1) / tb);
   // 1. Gaussians by float32 depth (stable; culled ones last).
   depth_keys_kernel<<<gb, tb, 0, st>>>(proj.depth, rect, n, dkeys[0], dvals[0]);
   const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, hist, partials, st);
   const uint32_t* order = dvals[dcur];
-  // 2. Instance offsets in depth order; K -> out.num_instances.
-  uint32_t* counts = dkeys[dcur ^ 1];
-  tile_counts_kernel<<<gb, tb, 0, st>>>(order, rect, n, tiles_x, tiles_y, counts);
-  e = exclusive_scan<uint32_t, uint64_t>(counts, n, offsets, partials, out.num_instances, st);
+  // 2. Per-chunk tile counts, scanned tile-major: first position of every (tile, chunk).
+  const size_t smem = bin_smem_bytes(v.width, v.height);
+  e = cudaFuncSetAttribute(chunk_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // 3. Duplicate into the buffer that makes the tile passes finish in `out`.
-  const int passes = (plan.tile_bits + 7) / 8;
-  uint32_t* ikeys[2];
-  uint32_t* ivals[2];
-  uint32_t* wk = reinterpret_cast<uint32_t*>(ws + plan.off_ikeys);
-  uint32_t* wv = reinterpret_cast<uint32_t*>(ws + plan.off_ivals);
-  if (passes % 2 == 0) {
-    ikeys[0] = out.tile_keys; ivals[0] = out.point_list; ikeys[1] = wk; ivals[1] = wv;
-  } else {
-    ikeys[0] = wk; ivals[0] = wv; ikeys[1] = out.tile_keys; ivals[1] = out.point_list;
-  }
-  duplicate_kernel<<<gb, tb, 0, st>>>(order, offsets, rect, tiles_x, tiles_y, n, plan.capacity,
-                                      ikeys[0], ivals[0]);
-  // 4. Stable sort of the instances by tile id.
-  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, hist, partials, st);
-  // 5. Tile ranges.
-  if (plan.capacity > 0) {
-    const unsigned gr = (unsigned)((plan.capacity + tb - 1) / tb);
-    ranges_kernel<<<gr, tb, 0, st>>>(out.tile_keys, out.num_instances, plan.capacity,
-                                     reinterpret_cast<uint2*>(out.ranges));
-  }
+  e = cudaFuncSetAttribute(chunk_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  chunk_hist_kernel<<<(unsigned)plan.chunks, kHistThreads, smem, st>>>(order, rect, n, plan.chunk, tiles_x,
+                                                                         tiles_y, plan.chunks, counts);
+  const int64_t mat = (int64_t)plan.num_tiles * plan.chunks;
+  e = exclusive_scan<uint32_t, uint64_t>(counts, mat, base, partials, out.num_instances, st);
+  if (e != cudaSuccess) return e;
+  // 3. Scatter the ids into their tiles' lists; 4. ranges.
+  chunk_scatter_kernel<<<(unsigned)plan.chunks, 32 * kScatterWarps, smem, st>>>(
+      order, rect, n, plan.chunk, tiles_x, tiles_y, plan.chunks, base, plan.capacity, out.point_list,
+      out.tile_keys);
+  ranges_from_base_kernel<<<(plan.num_tiles + tb - 1) / tb, tb, 0, st>>>(
+      base, plan.num_tiles, plan.chunks, out.num_instances, plan.capacity, reinterpret_cast<uint2*>(out.ranges));
   return cudaGetLastError();
 }
 

@@ -26,18 +26,21 @@ class Renderer:
     reallocated at 1.25x the count and binning runs again.
     """
 
-    def __init__(self, n: int, width: int, height: int, capacity: int | None = None, device="cuda"):
+    def __init__(self, n: int, width: int, height: int, capacity: int | None = None, device="cuda",
+                 tile_keys: bool = False):
         self.n, self.width, self.height, self.device = n, width, height, device
+        self.tile_keys = tile_keys
         self.proj = sdgs.ProjectedBuffers(n, device)
         self.bins = sdgs.BinBuffers(n, capacity if capacity is not None else max(4096, 16 * n), width,
-                                    height, device)
+                                    height, device, tile_keys=tile_keys)
         self.image = torch.empty(height, width, 3, dtype=torch.float32, device=device)
         self.final_T = torch.empty(height, width, dtype=torch.float32, device=device)
         self.n_contrib = torch.empty(height, width, dtype=torch.int32, device=device)
         self.num_instances = 0
 
     def grow(self, k: int):
-        self.bins = sdgs.BinBuffers(self.n, int(k * 1.25) + 1024, self.width, self.height, self.device)
+        self.bins = sdgs.BinBuffers(self.n, int(k * 1.25) + 1024, self.width, self.height, self.device,
+                                    tile_keys=self.tile_keys)
 
     def bin(self, view: sdgs.View, stream=None) -> int:
         try:

@@ -183,10 +183,11 @@ class ProjectedBuffers:
 class BinBuffers:
     """Sorted instance lists, tile ranges and the workspace of sdgs_bin_sort."""
 
-    def __init__(self, n: int, capacity: int, width: int, height: int, device="cuda"):
+    def __init__(self, n: int, capacity: int, width: int, height: int, device="cuda", tile_keys: bool = True):
         self.n, self.capacity, self.width, self.height = n, int(capacity), width, height
         self.num_tiles = ((width + TILE - 1) // TILE) * ((height + TILE - 1) // TILE)
-        self.tile_keys = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
+        self.tile_keys = (torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
+                          if tile_keys else None)
         self.point_list = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
         self.ranges = torch.empty(self.num_tiles, 2, dtype=torch.int32, device=device)
         self.num_instances = torch.zeros(1, dtype=torch.int64, device=device)
