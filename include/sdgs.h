@@ -166,6 +166,22 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
                   size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                   void* stream);
 
+/* sdgs_bin_sort without a workspace argument, for callers that cannot allocate device memory --
+ * for example a plugin whose host application owns every device allocation, or a latency-bound
+ * loop where cudaMalloc's implicit device synchronisation is not acceptable.  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ * Same inputs, outputs, ordering and errors as sdgs_bin_sort.  The scratch space is a fixed
+ * SDGS_STATIC_BIN_SCRATCH_BYTES (64 MiB) array in the library's device memory, which every GPU
+ * that loads the library holds until the process exits.  A problem whose
+ * sdgs_bin_workspace_size() exceeds it is rejected with SDGS_ERR_WORKSPACE (nothing enqueued).
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  The call itself allocates
+ * nothing.  All calls share the one array: calls whose work overlaps on the GPU (different streams,
+ * or host threads without ordering) race and corrupt each other's results. */
+#define SDGS_STATIC_BIN_SCRATCH_BYTES ((size_t)64 << 20)
+int sdgs_bin_sort_static(const sdgs_projected* proj, const sdgs_view* view, const sdgs_bins* out,
+                         int64_t* num_instances_host, void* stream);
+
 /* Front-to-back compositing of each 16x16 tile's sorted instances.
  * Per pixel: alpha_i = min(0.99, alpha_cond exp(-1/2 (a dx^2 + c dy^2) - b dx dy)), skipped when
  * below 1/255; the pixel stops before the Gaussian that would take its transmittance below 1e-4.

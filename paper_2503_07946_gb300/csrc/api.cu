@@ -4,6 +4,7 @@
 #include <stdio.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -152,6 +153,73 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
   }
   cudaStream_t st = (cudaStream_t)stream;
   SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st), "bin_sort launch"));
+  if (num_instances_host != nullptr) {
+    SDGS_TRY(cuda_status(cudaMemcpyAsync(num_instances_host, out->num_instances, sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, st), "copy instance count"));
+    SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "bin_sort synchronize"));
+    if (*num_instances_host > out->capacity) {
+      set_error("%lld instances exceed capacity %lld", (long long)*num_instances_host, (long long)out->capacity);
+      return SDGS_ERR_OVERFLOW;
+    }
+  }
+  return SDGS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Binning without a caller-provided workspace (sdgs_bin_sort_static).  Its scratch space is
+// this file-scope device array.  In host code `g_bin_scratch` only names a host-side stand-in,
+// so the kernels get the device address from cudaGetSymbolAddress, looked up once per device.
+// Every byte of the workspace that binning reads is written earlier in the same call, so the
+// array never needs clearing between calls.
+// ------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_bin_scratch[SDGS_STATIC_BIN_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+int static_scratch(void** ptr) {
+  int dev = 0;
+  SDGS_TRY(cuda_status(cudaGetDevice(&dev), "cudaGetDevice"));
+  if (dev < 0 || dev >= kMaxDevices) { set_error("device ordinal %d out of range", dev); return SDGS_ERR_INVALID_ARG; }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    SDGS_TRY(cuda_status(cudaGetSymbolAddress(&p, g_bin_scratch), "cudaGetSymbolAddress(bin scratch)"));
+    g_scratch_ptr[dev] = p;
+  }
+  *ptr = g_scratch_ptr[dev];
+  return SDGS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int sdgs_bin_sort_static(const sdgs_projected* proj, const sdgs_view* view, const sdgs_bins* out,
+                         int64_t* num_instances_host, void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_projected(proj));
+  SDGS_TRY(check_view(view));
+  SDGS_TRY(check_bins(out));
+  if (bin_smem_bytes(view->width, view->height) > kMaxBinSmem) {
+    set_error("image of %d x %d tiles exceeds the binning limit", (view->width + kTile - 1) / kTile,
+              (view->height + kTile - 1) / kTile);
+    return SDGS_ERR_INVALID_ARG;
+  }
+  const BinPlan plan = plan_bins(proj->n, out->capacity, view->width, view->height);
+  if (plan.total > SDGS_STATIC_BIN_SCRATCH_BYTES) {
+    set_error("binning %lld Gaussians into %d tiles needs %zu bytes of scratch; the built-in scratch "
+              "holds %zu (use sdgs_bin_sort with a workspace)",
+              (long long)proj->n, plan.num_tiles, plan.total, (size_t)SDGS_STATIC_BIN_SCRATCH_BYTES);
+    return SDGS_ERR_WORKSPACE;
+  }
+  void* ws = nullptr;
+  SDGS_TRY(static_scratch(&ws));
+  cudaStream_t st = (cudaStream_t)stream;
+  SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)ws, *out, st), "bin_sort launch"));
   if (num_instances_host != nullptr) {
     SDGS_TRY(cuda_status(cudaMemcpyAsync(num_instances_host, out->num_instances, sizeof(int64_t),
                                          cudaMemcpyDeviceToHost, st), "copy instance count"));

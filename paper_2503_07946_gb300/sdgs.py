@@ -68,6 +68,8 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sdgs_bin_sort": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p, ctypes.c_size_t,
                        ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
+    "sdgs_bin_sort_static": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.POINTER(Bins),
+                              ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
     "sdgs_render_fwd": ([ctypes.POINTER(Projected), ctypes.POINTER(Bins), ctypes.POINTER(View),
                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                         ctypes.c_int),
@@ -224,6 +226,22 @@ def bin_sort(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = 
     _check(lib().sdgs_bin_sort(ctypes.byref(proj.struct()), ctypes.byref(view), _ptr(bins.workspace),
                                bins.ws_bytes, ctypes.byref(bins.struct()),
                                ctypes.byref(k) if sync else None, _stream(stream)))
+    return int(k.value) if sync else None
+
+
+STATIC_BIN_SCRATCH_BYTES = 64 << 20
+
+
+def bin_sort_static(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = True, stream=None):
+    """sdgs_bin_sort_static: binning into the library's built-in scratch array (no workspace).
+
+    For callers that cannot allocate device memory.  Same results as bin_sort; problems whose
+    workspace would exceed the 64 MiB built-in scratch raise SdgsError(WORKSPACE).  Calls that
+    overlap on the GPU share that scratch and race.
+    """
+    k = ctypes.c_int64(0)
+    _check(lib().sdgs_bin_sort_static(ctypes.byref(proj.struct()), ctypes.byref(view), ctypes.byref(bins.struct()),
+                                      ctypes.byref(k) if sync else None, _stream(stream)))
     return int(k.value) if sync else None
 
 
