@@ -177,9 +177,10 @@ def run_reference(args, rank: int, world: int):
 
 def launches_per_frame(n: int, width: int, height: int) -> int:
     """Kernels libsdgs launches for one render: slice_project; depth keys; 4 depth radix passes
-    (upsweep, 3 scan kernels, downsweep); the per-chunk tile histogram; a 3-kernel scan; the
-    scatter into tile lists; tile ranges; the rasteriser."""
-    return 1 + 1 + 4 * 5 + 1 + 3 + 1 + 1 + 1
+    (upsweep, 3 scan kernels, downsweep); scatter-cost units + their 3-kernel scan; the per-chunk
+    tile histogram + the 3-kernel scan of the (tile, chunk) matrix; the scatter into tile lists;
+    tile ranges; the rasteriser."""
+    return 1 + 1 + 4 * 5 + 1 + 3 + 1 + 3 + 1 + 1 + 1
 
 
 def cpu_baseline(scene, cam) -> dict:

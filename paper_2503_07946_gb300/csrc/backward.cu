@@ -3,13 +3,13 @@
 // Sigma = L L^T).  Discrete decisions (culling, radius, tile rectangles, per-pixel skips and the
 // stop position) are those of the forward and carry no derivative.
 #include "geometry.cuh"
+#include "raster_common.cuh"
 
 namespace sdgs {
 
 namespace {
 
 constexpr int kThreads = kTilePixels;
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kG2 = 12;  // floats per Gaussian of screen-space gradient: u v a b c alpha r g b _ _ _
 
 struct RasterBwdArgs {
@@ -89,11 +89,10 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
         const float4 q = s_co[k];
         const float dx = fx - xy.x, dy = fy - xy.y;
         // identical arithmetic to the forward so that the skip decisions agree
-        const float qa = -0.5f * kLog2e * q.x, qb = -kLog2e * q.y, qc = -0.5f * kLog2e * q.z;
-        const float p2 = qa * dx * dx + qc * dy * dy + qb * dx * dy;
+        const float p2 = splat_power2(scaled_conic(q), dx, dy);
         if (p2 <= 0.f) {
-          const float G = exp2f(p2);
-          const float raw = q.w * G;
+          const float G = ex2_approx(p2);
+          const float raw = __fmul_rn(q.w, G);
           const float al = fminf(kAlphaMax, raw);
           if (al >= kAlphaMin) {
             contrib = true;

@@ -14,6 +14,8 @@
 // per-block digit histogram (digit-major), a device-wide exclusive scan turns it into block
 // offsets, and a downsweep ranks the block's keys stably (warp match + per-warp counters) and
 // scatters them through shared memory so that runs of one digit are written contiguously.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sdgs {
@@ -289,8 +291,22 @@ __global__ void depth_keys_kernel(const float* __restrict__ depth, const ushort4
   vals[i] = (uint32_t)i;
 }
 
-// Rectangles are clipped to the tile grid here and in duplicate_kernel, so records that come
-// from the caller rather than from slice_project can never address a tile outside the image.
+// ------------------------------------------------------------------------------------------
+// Stable counting sort of the instances by tile, in one pass over the depth-sorted Gaussians.
+//
+// The depth-ordered Gaussians are cut into C contiguous chunks of about equal scatter cost
+// (instances / 32 + 1 per Gaussian, running sum split into C equal shares).  (1) Each chunk counts, per tile, how many of its Gaussians' rectangles cover that
+// tile, with a 2D difference array in shared memory (four atomics per Gaussian, then prefix sums
+// along x and y).  (2) One exclusive scan over the tile-major (tile, chunk) count matrix gives
+// every chunk its first output position per tile.  (3) Each chunk walks its Gaussians in depth
+// order with one warp: the lanes cover the current Gaussian's rectangle, each writing the
+// Gaussian's id at its tile's cursor and advancing it.  Instances of one tile therefore land in
+// (depth, id) order, exactly the stable sort by (tile, depth) key.  Per-tile ranges come
+// straight from the scanned matrix.
+// ------------------------------------------------------------------------------------------
+
+// Rectangles are clipped to the tile grid, so records that come from the caller rather than
+// from slice_project can never address a tile outside the image.
 __device__ __forceinline__ ushort4 clip_rect(ushort4 r, int tiles_x, int tiles_y) {
   r.x = (unsigned short)min((int)r.x, tiles_x);
   r.z = (unsigned short)min((int)r.z, tiles_x);
@@ -299,30 +315,72 @@ __device__ __forceinline__ ushort4 clip_rect(ushort4 r, int tiles_x, int tiles_y
   return r;
 }
 
-// ------------------------------------------------------------------------------------------
-// Stable counting sort of the instances by tile, in one pass over the depth-sorted Gaussians.
-//
-// The depth-ordered Gaussians are cut into chunks of G.  (1) Each chunk counts, per tile, how
-// many of its Gaussians' rectangles cover that tile, with a 2D difference array in shared memory
-// (four atomics per Gaussian, then prefix sums along x and y).  (2) One exclusive scan over the
-// tile-major (tile, chunk) count matrix gives every chunk its first output position per tile.
-// (3) Each chunk walks its Gaussians in depth order with one warp: the lanes cover the current
-// Gaussian's rectangle, each writing the Gaussian's id at its tile's cursor and advancing it.
-// Instances of one tile therefore land in (depth, id) order, exactly the stable sort by
-// (tile, depth) key.  Per-tile ranges come straight from the scanned matrix.
-// ------------------------------------------------------------------------------------------
+// Scatter cost of each depth-ordered Gaussian in warp steps: one per 32 instances plus one for
+// the Gaussian itself.  Chunks are cut at equal shares of the running sum of this cost.
+__global__ void work_units_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+                                  int64_t n, int tiles_x, int tiles_y, uint32_t* __restrict__ units) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const ushort4 r = clip_rect(rect[order[s]], tiles_x, tiles_y);
+  const int w = (int)r.z - (int)r.x, h = (int)r.w - (int)r.y;
+  units[s] = (w > 0 && h > 0) ? (uint32_t)((w * h + 31) / 32 + 1) : 0u;
+}
+
+// First s in [0, n) with off[s] >= target (n if none), by a 32-way search over the warp.
+__device__ int64_t warp_lower_bound(const uint64_t* __restrict__ off, int64_t n, uint64_t target) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]; hi == n or off[hi] >= target
+  while (hi - lo > 31) {
+    const int64_t step = (hi - lo + 31) / 32;
+    int64_t p = lo + (int64_t)(lane + 1) * step - 1;
+    if (p > hi - 1) p = hi - 1;
+    const unsigned b = __ballot_sync(0xffffffffu, off[p] >= target);
+    if (b == 0) {
+      lo = hi;
+      break;
+    }
+    const int f = __ffs(b) - 1;
+    const int64_t pf = min(lo + (int64_t)(f + 1) * step - 1, hi - 1);
+    lo = lo + (int64_t)f * step;
+    hi = pf;
+  }
+  const int64_t p = lo + lane;
+  const unsigned b = __ballot_sync(0xffffffffu, p >= hi || off[p] >= target);
+  return lo + (__ffs(b) - 1);
+}
+
+// Gaussian range [s0, s1) of chunk `c` out of `chunks`: the Gaussians whose running cost `off`
+// starts inside the chunk's share of `total`.  Executed by a full warp.
+__device__ __forceinline__ void chunk_range(const uint64_t* __restrict__ off, int64_t n,
+                                            const int64_t* __restrict__ total, int64_t chunks,
+                                            int64_t c, int64_t* s0, int64_t* s1) {
+  const uint64_t k = (uint64_t)*total;
+  uint64_t per = (k + (uint64_t)chunks - 1) / (uint64_t)chunks;
+  if (per == 0) per = 1;
+  // Targets are clamped to the total: the first Gaussian whose running cost reaches the total
+  // starts the culled (zero-cost) tail, which belongs to no chunk.
+  const uint64_t t0 = (uint64_t)c * per, t1 = (uint64_t)(c + 1) * per;
+  *s0 = warp_lower_bound(off, n, t0 < k ? t0 : k);
+  *s1 = warp_lower_bound(off, n, t1 < k ? t1 : k);
+}
 
 constexpr int kHistThreads = 256;
 
 __global__ void __launch_bounds__(kHistThreads)
 chunk_hist_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t n,
-                  int G, int tiles_x, int tiles_y, int64_t chunks, uint32_t* __restrict__ counts) {
+                  const uint64_t* __restrict__ offsets, const int64_t* __restrict__ total, int tiles_x,
+                  int tiles_y, int64_t chunks, uint32_t* __restrict__ counts) {
   extern __shared__ int s_diff[];  // (tiles_y + 1) x (tiles_x + 1)
+  __shared__ int64_t s_range[2];
   const int W1 = tiles_x + 1, H1 = tiles_y + 1;
   for (int i = threadIdx.x; i < W1 * H1; i += kHistThreads) s_diff[i] = 0;
+  if (threadIdx.x < 32) {
+    int64_t a, b;
+    chunk_range(offsets, n, total, chunks, blockIdx.x, &a, &b);
+    if (threadIdx.x == 0) { s_range[0] = a; s_range[1] = b; }
+  }
   __syncthreads();
-  const int64_t s0 = (int64_t)blockIdx.x * G;
-  const int64_t s1 = min(n, s0 + G);
+  const int64_t s0 = s_range[0], s1 = s_range[1];
   for (int64_t s = s0 + threadIdx.x; s < s1; s += kHistThreads) {
     const ushort4 r = clip_rect(rect[order[s]], tiles_x, tiles_y);
     if (r.z > r.x && r.w > r.y) {
@@ -358,23 +416,23 @@ chunk_hist_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict_
   }
 }
 
-constexpr int kScatterWarps = 1;
-
-__global__ void __launch_bounds__(32 * kScatterWarps)
+__global__ void __launch_bounds__(32)
 chunk_scatter_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t n,
-                     int G, int tiles_x, int tiles_y, int64_t chunks, const uint64_t* __restrict__ base,
-                     int64_t cap, uint32_t* __restrict__ point_list, uint32_t* __restrict__ tile_keys) {
+                     const uint64_t* __restrict__ offsets, const int64_t* __restrict__ total, int tiles_x,
+                     int tiles_y, int64_t chunks, const uint64_t* __restrict__ base, int64_t cap,
+                     uint32_t* __restrict__ point_list, uint32_t* __restrict__ tile_keys) {
   extern __shared__ uint32_t s_cur[];  // one cursor per tile
   const int tiles = tiles_x * tiles_y;
   const int lane = threadIdx.x;
   const int64_t chunk = blockIdx.x;
+  int64_t s0, s1;
+  chunk_range(offsets, n, total, chunks, chunk, &s0, &s1);
+#pragma unroll 8
   for (int t = lane; t < tiles; t += 32) {
     const uint64_t b = base[(int64_t)t * chunks + chunk];
     s_cur[t] = (uint32_t)(b < (uint64_t)cap ? b : (uint64_t)cap);
   }
   __syncwarp();
-  const int64_t s0 = chunk * G;
-  const int64_t s1 = min(n, s0 + G);
   for (int64_t sg = s0; sg < s1; sg += 32) {
     // each lane fetches one Gaussian of the group; they are then handled one at a time
     uint32_t g = 0;
@@ -383,8 +441,10 @@ chunk_scatter_kernel(const uint32_t* __restrict__ order, const ushort4* __restri
       g = order[sg + lane];
       r = clip_rect(rect[g], tiles_x, tiles_y);
     }
-    const int m = (int)min((int64_t)32, s1 - sg);
-    for (int i = 0; i < m; ++i) {
+    unsigned todo = __ballot_sync(0xffffffffu, r.z > r.x && r.w > r.y);
+    while (todo) {
+      const int i = __ffs(todo) - 1;
+      todo &= todo - 1;
       const uint32_t gi = __shfl_sync(0xffffffffu, g, i);
       const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, i);
       const int ry0 = __shfl_sync(0xffffffffu, (int)r.y, i);
@@ -425,11 +485,11 @@ __global__ void ranges_from_base_kernel(const uint64_t* __restrict__ base, int t
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Chunk size: 256 Gaussians, grown so that the (tile, chunk) matrix stays within 8M entries.
-int chunk_size(int64_t n, int tiles) {
-  int64_t G = 256;
-  while (G < (int64_t(1) << 20) && ((n + G - 1) / G) * (int64_t)tiles > (int64_t(8) << 20)) G *= 2;
-  return (int)G;
+// Number of counting-sort chunks: enough for parallelism, with the (tile, chunk) matrix kept
+// within 4M entries.
+int64_t chunk_count(int tiles) {
+  int64_t c = (int64_t(4) << 20) / (tiles > 0 ? tiles : 1);
+  return c < 128 ? 128 : (c > 1024 ? 1024 : c);
 }
 
 }  // namespace
@@ -446,22 +506,25 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   p.capacity = capacity;
   p.num_tiles = tiles_of(width) * tiles_of(height);
   p.tile_bits = 0;
-  p.chunk = chunk_size(n, p.num_tiles);
-  p.chunks = (n + p.chunk - 1) / p.chunk;
+  p.chunks = chunk_count(p.num_tiles);
+  p.chunk = 0;
   const int64_t nb_d = (n + kRadixTile - 1) / kRadixTile;
   p.hist_blocks = nb_d;
   const int64_t hist_entries = (int64_t)kBins * nb_d;
   const int64_t mat = (int64_t)p.num_tiles * p.chunks;
   const int64_t part_a = (hist_entries + kScanChunk - 1) / kScanChunk;
   const int64_t part_b = (mat + kScanChunk - 1) / kScanChunk;
-  p.partial_cap = (part_a > part_b ? part_a : part_b) + 1;
+  const int64_t part_c = (n + kScanChunk - 1) / kScanChunk;
+  p.partial_cap = std::max(part_a, std::max(part_b, part_c)) + 1;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) { p.off_dkeys[k] = off; off += align256(sizeof(uint32_t) * n); }
   for (int k = 0; k < 2; ++k) { p.off_dvals[k] = off; off += align256(sizeof(uint32_t) * n); }
+  p.off_offsets = off; off += align256(sizeof(uint64_t) * n);
   p.off_counts = off; off += align256(sizeof(uint32_t) * mat);
   p.off_base = off; off += align256(sizeof(uint64_t) * mat);
   p.off_hist = off; off += align256(sizeof(uint32_t) * hist_entries);
   p.off_partials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
+  p.off_scalars = off; off += align256(sizeof(int64_t) * 4);
   p.total = off;
   return p;
 }
@@ -474,10 +537,12 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
                         reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[1])};
   uint32_t* dvals[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dvals[0]),
                         reinterpret_cast<uint32_t*>(ws + plan.off_dvals[1])};
+  uint64_t* offsets = reinterpret_cast<uint64_t*>(ws + plan.off_offsets);
   uint32_t* counts = reinterpret_cast<uint32_t*>(ws + plan.off_counts);
   uint64_t* base = reinterpret_cast<uint64_t*>(ws + plan.off_base);
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + plan.off_hist);
   uint64_t* partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
+  int64_t* total_work = reinterpret_cast<int64_t*>(ws + plan.off_scalars);
   const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
 
   cudaError_t e;
@@ -492,21 +557,26 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   depth_keys_kernel<<<gb, tb, 0, st>>>(proj.depth, rect, n, dkeys[0], dvals[0]);
   const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, hist, partials, st);
   const uint32_t* order = dvals[dcur];
-  // 2. Per-chunk tile counts, scanned tile-major: first position of every (tile, chunk).
+  // 2. Running scatter cost in depth order, to cut balanced chunks.
+  uint32_t* tcount = dkeys[dcur ^ 1];
+  work_units_kernel<<<gb, tb, 0, st>>>(order, rect, n, tiles_x, tiles_y, tcount);
+  e = exclusive_scan<uint32_t, uint64_t>(tcount, n, offsets, partials, total_work, st);
+  if (e != cudaSuccess) return e;
+  // 3. Per-chunk tile counts, scanned tile-major: first position of every (tile, chunk).
   const size_t smem = bin_smem_bytes(v.width, v.height);
   e = cudaFuncSetAttribute(chunk_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(chunk_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  chunk_hist_kernel<<<(unsigned)plan.chunks, kHistThreads, smem, st>>>(order, rect, n, plan.chunk, tiles_x,
-                                                                         tiles_y, plan.chunks, counts);
+  chunk_hist_kernel<<<(unsigned)plan.chunks, kHistThreads, smem, st>>>(
+      order, rect, n, offsets, total_work, tiles_x, tiles_y, plan.chunks, counts);
   const int64_t mat = (int64_t)plan.num_tiles * plan.chunks;
   e = exclusive_scan<uint32_t, uint64_t>(counts, mat, base, partials, out.num_instances, st);
   if (e != cudaSuccess) return e;
-  // 3. Scatter the ids into their tiles' lists; 4. ranges.
-  chunk_scatter_kernel<<<(unsigned)plan.chunks, 32 * kScatterWarps, smem, st>>>(
-      order, rect, n, plan.chunk, tiles_x, tiles_y, plan.chunks, base, plan.capacity, out.point_list,
-      out.tile_keys);
+  // 4. Scatter the ids into their tiles' lists; 5. ranges.
+  chunk_scatter_kernel<<<(unsigned)plan.chunks, 32, smem, st>>>(
+      order, rect, n, offsets, total_work, tiles_x, tiles_y, plan.chunks, base, plan.capacity,
+      out.point_list, out.tile_keys);
   ranges_from_base_kernel<<<(plan.num_tiles + tb - 1) / tb, tb, 0, st>>>(
       base, plan.num_tiles, plan.chunks, out.num_instances, plan.capacity, reinterpret_cast<uint2*>(out.ranges));
   return cudaGetLastError();

@@ -33,10 +33,11 @@ struct BinPlan {
   int64_t capacity;
   int num_tiles;
   int tile_bits;
-  int chunk;       // Gaussians per counting-sort chunk
-  int64_t chunks;  // number of chunks
+  int chunk;       // unused (chunks are balanced by instance count)
+  int64_t chunks;  // number of counting-sort chunks
   // workspace carve-up (byte offsets)
-  size_t off_dkeys[2], off_dvals[2], off_counts, off_base, off_hist, off_partials, total;
+  size_t off_dkeys[2], off_dvals[2], off_offsets, off_counts, off_base, off_hist, off_partials, off_scalars,
+      total;
   int64_t hist_blocks;  // radix blocks of the depth sort
   int64_t partial_cap;  // entries available for scan partials
 };

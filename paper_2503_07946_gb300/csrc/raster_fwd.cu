@@ -1,15 +1,19 @@
-// Forward tile rasteriser: one 256-thread block per 16x16 tile, one pixel per thread.
-// The tile's sorted instances are staged through shared memory in batches of 256; every pixel
-// walks the batch front to back (Sec. 4.3 depth-aware opacity blending with the 3DGS rules).
-// The block leaves as soon as every pixel of the tile has stopped.
-#include "common.cuh"
+// Forward tile rasteriser (Sec. 4.3 depth-aware opacity blending with the 3DGS rules).
+//
+// One 128-thread block per 16x16 tile; each thread owns two pixels of one column, rows r and
+// r + 8, so every Gaussian fetched from shared memory is evaluated twice.  The tile's sorted
+// instances are staged 128 at a time; while staging, each thread tests its Gaussian against the
+// tile's pixel-centre box and drops it when alpha_cond exp(-q/2) < 1/255 holds at every pixel of
+// the tile with a safety margin (those evaluations would all be skipped), and the survivors are
+// compacted in order together with their positions in the tile list.  The block leaves once every
+// pixel has stopped.
+#include "raster_common.cuh"
 
 namespace sdgs {
 
 namespace {
 
-constexpr int kThreads = kTilePixels;
-constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kThreads = kTilePixels / 2;
 
 struct FwdArgs {
   const float2* mean2d;
@@ -25,77 +29,121 @@ struct FwdArgs {
   unsigned long long* n_evaluated;  // optional work counter
 };
 
+struct Pixel {
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+  uint32_t last = 0, evaluated = 0;
+  bool done;
+};
+
+// One (pixel, Gaussian) evaluation written without branches, so that a thread's two pixels
+// interleave: the pixel takes the Gaussian iff it is still running, the exponent is <= 0 and
+// alpha >= 1/255; if that would take T below 1e-4 the pixel stops instead (without blending).
+__device__ __forceinline__ void blend(Pixel& px, const float4& q, const float4& c, float dx, float dy,
+                                      uint32_t pos1) {
+  const float p2 = splat_power2(q, dx, dy);
+  const float al = fminf(kAlphaMax, __fmul_rn(q.w, ex2_approx(p2)));
+  const float Tn = __fmul_rn(px.T, __fsub_rn(1.f, al));
+  const bool live = !px.done;
+  const bool hit = live && p2 <= 0.f && al >= kAlphaMin;
+  const bool stop = hit && Tn < kTMin;
+  const bool take = hit && !stop;
+  const float w = take ? al * px.T : 0.f;
+  px.evaluated += live ? 1u : 0u;
+  px.c0 += c.x * w;
+  px.c1 += c.y * w;
+  px.c2 += c.z * w;
+  px.T = take ? Tn : px.T;
+  px.last = take ? pos1 : px.last;
+  px.done = px.done || stop;
+}
+
 __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
   __shared__ float2 s_xy[kThreads];
-  __shared__ float4 s_q[kThreads];  // (-a/2, -b, -c/2) * log2(e), alpha_cond
-  __shared__ float s_rgb[3][kThreads];
+  __shared__ float4 s_q[kThreads];
+  __shared__ float4 s_rgb[kThreads];
+  __shared__ int s_pos[kThreads];
+  __shared__ int s_warp[kThreads / 32];
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < a.width && py < a.height;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int py0 = ty * kTile + (threadIdx.x / kTile);
+  const int py1 = py0 + kTile / 2;
+  const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
+  const float bx0 = (float)(tx * kTile) + 0.5f, bx1 = bx0 + (float)(kTile - 1);
+  const float by0 = (float)(ty * kTile) + 0.5f, by1 = by0 + (float)(kTile - 1);
   const uint2 range = a.ranges[tile];
   const int n = (int)(range.y - range.x);
 
-  bool done = !inside;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0;
-  uint32_t evaluated = 0;
+  Pixel p0, p1;
+  p0.done = !(px < a.width && py0 < a.height);
+  p1.done = !(px < a.width && py1 < a.height);
   for (int base = 0; base < n; base += kThreads) {
-    if (__syncthreads_count(done) == kThreads) break;
+    if (__syncthreads_count(p0.done && p1.done) == kThreads) break;
+    // stage, cull against the tile, compact in order
     const int j = base + threadIdx.x;
+    bool keep = false;
+    float2 xy;
+    float4 co;
+    uint32_t g = 0;
     if (j < n) {
-      const uint32_t g = a.point_list[range.x + j];
-      s_xy[threadIdx.x] = a.mean2d[g];
-      const float4 q = a.conic_opacity[g];
-      s_q[threadIdx.x] = make_float4(-0.5f * kLog2e * q.x, -kLog2e * q.y, -0.5f * kLog2e * q.z, q.w);
-      s_rgb[0][threadIdx.x] = a.rgb[3 * g + 0];
-      s_rgb[1][threadIdx.x] = a.rgb[3 * g + 1];
-      s_rgb[2][threadIdx.x] = a.rgb[3 * g + 2];
+      g = a.point_list[range.x + j];
+      xy = a.mean2d[g];
+      co = a.conic_opacity[g];
+      keep = !splat_misses_box(co, xy, bx0, bx1, by0, by1);
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_warp[warp] = __popc(ballot);
+    __syncthreads();
+    int off = 0, cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+      const int c = s_warp[w];
+      off += (w < warp) ? c : 0;
+      cnt += c;
+    }
+    if (keep) {
+      const int idx = off + __popc(ballot & ((1u << lane) - 1u));
+      s_xy[idx] = xy;
+      s_q[idx] = scaled_conic(co);
+      s_rgb[idx] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
+      s_pos[idx] = j;
     }
     __syncthreads();
-    if (!done) {
-      const int cnt = min(kThreads, n - base);
-      int k = 0;
-      for (; k < cnt; ++k) {
-        const float2 xy = s_xy[k];
+    if (!(p0.done && p1.done)) {
+      for (int k = 0; k < cnt; ++k) {
+        const float2 m = s_xy[k];
         const float4 q = s_q[k];
-        const float dx = fx - xy.x, dy = fy - xy.y;
-        const float p2 = q.x * dx * dx + q.z * dy * dy + q.y * dx * dy;
-        if (p2 > 0.f) continue;
-        const float al = fminf(kAlphaMax, q.w * exp2f(p2));
-        if (al < kAlphaMin) continue;
-        const float Tn = T * (1.f - al);
-        if (Tn < kTMin) {
-          done = true;
-          ++k;  // the stopping Gaussian was evaluated too
-          break;
-        }
-        const float w = al * T;
-        C0 += s_rgb[0][k] * w;
-        C1 += s_rgb[1][k] * w;
-        C2 += s_rgb[2][k] * w;
-        T = Tn;
-        last = (uint32_t)(base + k + 1);
+        const float4 c = s_rgb[k];
+        const uint32_t pos1 = (uint32_t)s_pos[k] + 1u;
+        // offsets exactly as the backward forms them, so both passes take the same decisions
+        const float dx = fx - m.x;
+        blend(p0, q, c, dx, fy0 - m.y, pos1);
+        blend(p1, q, c, dx, fy1 - m.y, pos1);
+        if (p0.done && p1.done) break;
       }
-      evaluated += (uint32_t)k;
     }
   }
   if (a.n_evaluated != nullptr) {
-    unsigned long long e = evaluated;
+    unsigned long long e = (unsigned long long)p0.evaluated + p1.evaluated;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0 && e) atomicAdd(a.n_evaluated, e);
+    if (lane == 0 && e) atomicAdd(a.n_evaluated, e);
   }
-  if (inside) {
-    const int pix = py * a.width + px;
-    a.image[3 * pix + 0] = C0 + T * a.bg[0];
-    a.image[3 * pix + 1] = C1 + T * a.bg[1];
-    a.image[3 * pix + 2] = C2 + T * a.bg[2];
-    a.final_T[pix] = T;
-    a.n_contrib[pix] = last;
+  const Pixel* pp[2] = {&p0, &p1};
+  const int rows[2] = {py0, py1};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (px < a.width && rows[r] < a.height) {
+      const int pix = rows[r] * a.width + px;
+      const Pixel& q = *pp[r];
+      a.image[3 * pix + 0] = q.c0 + q.T * a.bg[0];
+      a.image[3 * pix + 1] = q.c1 + q.T * a.bg[1];
+      a.image[3 * pix + 2] = q.c2 + q.T * a.bg[2];
+      a.final_T[pix] = q.T;
+      a.n_contrib[pix] = q.last;
+    }
   }
 }
 
