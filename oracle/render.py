@@ -155,11 +155,12 @@ def render_projected(rec: dict, width: int, height: int, bg, tiles=None) -> dict
                          torch.as_tensor(bg, dtype=F64), tiles)
 
 
-def vjp(scene, cam, dL_dimage: np.ndarray) -> dict:
+def vjp(scene, cam, dL_dimage: np.ndarray, tiles=None) -> dict:
     """Gradients of sum(dL_dimage * image) w.r.t. mean7, L28, opacity, sh (float64).
 
     The visible set is found first without gradients; the forward is then re-run on the
-    visible Gaussians only, so culled Gaussians receive exactly zero gradient.
+    visible Gaussians only, so culled Gaussians receive exactly zero gradient.  With `tiles`,
+    only those tiles are composited: exact when dL_dimage is zero outside them.
     """
     p0 = params_from_scene(scene)
     with torch.no_grad():
@@ -170,7 +171,7 @@ def vjp(scene, cam, dL_dimage: np.ndarray) -> dict:
     g = gaussians(sub, cam, scene.lambda_t, scene.lambda_d)
     bg = torch.as_tensor(cam.bg, dtype=F64)
     out = composite_all(g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], g["depth"], g["rect"],
-                        cam, bg)
+                        cam, bg, tiles)
     loss = (out["image"] * torch.as_tensor(dL_dimage, dtype=F64)).sum()
     loss.backward()
     return dict(mean7=leaf["mean7"].grad.numpy(), L28=leaf["L28"].grad.numpy(),

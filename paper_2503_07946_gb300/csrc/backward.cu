@@ -9,7 +9,7 @@ namespace sdgs {
 
 namespace {
 
-constexpr int kThreads = kTilePixels;
+constexpr int kThreads = kTilePixels / 2;
 constexpr int kG2 = 12;  // floats per Gaussian of screen-space gradient: u v a b c alpha r g b _ _ _
 
 struct RasterBwdArgs {
@@ -32,98 +32,144 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// Per-pixel state of the back-to-front replay.
+struct BwdPixel {
+  float T;                 // transmittance in front of the current position
+  float R0, R1, R2;        // colour seen behind the current position, normalised by T there
+  float d0, d1, d2;        // dL/dC of the pixel
+  uint32_t last;           // positions >= last were not blended in the forward
+};
+
+// Adjoint of one (pixel, Gaussian) blend, accumulated into g[9] = d(u, v, a, b, c, alpha_cond,
+// r, g, b).  Replays exactly the forward's decisions (same exponent, alpha and thresholds).
+__device__ __forceinline__ bool unblend(BwdPixel& px, const float4& co, const float4& q, const float4& c,
+                                        float dx, float dy, uint32_t pos, float g[9]) {
+  if (pos >= px.last) return false;
+  const float p2 = splat_power2(q, dx, dy);
+  if (!(p2 <= 0.f)) return false;
+  const float G = ex2_approx(p2);
+  const float raw = __fmul_rn(co.w, G);
+  const float al = fminf(kAlphaMax, raw);
+  if (!(al >= kAlphaMin)) return false;
+  px.T = px.T / (1.f - al);
+  const float w = al * px.T;
+  g[6] += px.d0 * w;
+  g[7] += px.d1 * w;
+  g[8] += px.d2 * w;
+  const float dal = px.T * (px.d0 * (c.x - px.R0) + px.d1 * (c.y - px.R1) + px.d2 * (c.z - px.R2));
+  px.R0 = c.x * al + (1.f - al) * px.R0;
+  px.R1 = c.y * al + (1.f - al) * px.R1;
+  px.R2 = c.z * al + (1.f - al) * px.R2;
+  if (raw < kAlphaMax) {  // no derivative through the 0.99 clamp
+    g[5] += dal * G;
+    const float dp = dal * al;  // d alpha / d(power) = alpha
+    g[0] += dp * (co.x * dx + co.y * dy);
+    g[1] += dp * (co.y * dx + co.z * dy);
+    g[2] += -0.5f * dp * dx * dx;
+    g[3] += -dp * dx * dy;
+    g[4] += -0.5f * dp * dy * dy;
+  }
+  return true;
+}
+
+// Back-to-front replay per 16x16 tile, 128 threads with two pixels each (rows r and r + 8).
+// The tile's list is staged from the back in batches of 128 with the same conservative tile cull
+// as the forward (culled Gaussians have alpha < 1/255 at every pixel, so the forward skipped them
+// everywhere); each Gaussian's gradient is summed over the thread's pixels, then over the warp,
+// and added to the per-Gaussian buffer with one atomic per component and warp.
 __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArgs a) {
   __shared__ float2 s_xy[kThreads];
-  __shared__ float4 s_co[kThreads];  // a, b, c, alpha_cond
-  __shared__ float s_rgb[3][kThreads];
+  __shared__ float4 s_co[kThreads];
+  __shared__ float4 s_rgb[kThreads];
   __shared__ uint32_t s_id[kThreads];
+  __shared__ uint32_t s_pos[kThreads];
+  __shared__ int s_warp[kThreads / 32];
   __shared__ uint32_t s_max;
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < a.width && py < a.height;
-  const int pix = py * a.width + px;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int py[2] = {ty * kTile + (int)(threadIdx.x / kTile), ty * kTile + (int)(threadIdx.x / kTile) + kTile / 2};
+  const float fx = (float)px + 0.5f;
+  const float fy[2] = {(float)py[0] + 0.5f, (float)py[1] + 0.5f};
+  const float bx0 = (float)(tx * kTile) + 0.5f, bx1 = bx0 + (float)(kTile - 1);
+  const float by0 = (float)(ty * kTile) + 0.5f, by1 = by0 + (float)(kTile - 1);
   const uint2 range = a.ranges[tile];
 
-  float T = 1.f, dL0 = 0.f, dL1 = 0.f, dL2 = 0.f;
-  uint32_t last = 0;
-  if (inside) {
-    T = a.final_T[pix];
-    last = a.n_contrib[pix];
-    dL0 = a.dL_dimage[3 * pix + 0];
-    dL1 = a.dL_dimage[3 * pix + 1];
-    dL2 = a.dL_dimage[3 * pix + 2];
+  BwdPixel pxs[2];
+  uint32_t mylast = 0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    BwdPixel& p = pxs[r];
+    p.T = 1.f; p.last = 0; p.d0 = p.d1 = p.d2 = 0.f;
+    p.R0 = a.bg[0]; p.R1 = a.bg[1]; p.R2 = a.bg[2];
+    if (px < a.width && py[r] < a.height) {
+      const int pix = py[r] * a.width + px;
+      p.T = a.final_T[pix];
+      p.last = a.n_contrib[pix];
+      p.d0 = a.dL_dimage[3 * pix + 0];
+      p.d1 = a.dL_dimage[3 * pix + 1];
+      p.d2 = a.dL_dimage[3 * pix + 2];
+    }
+    mylast = max(mylast, p.last);
   }
-  // colour seen behind the current position, normalised by the transmittance there
-  float R0 = a.bg[0], R1 = a.bg[1], R2 = a.bg[2];
-
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  atomicMax(&s_max, last);
+  atomicMax(&s_max, mylast);
   __syncthreads();
-  const int end = (int)s_max;  // positions >= end contribute to no pixel of the tile
+  const int end = (int)s_max;  // positions >= end were blended at no pixel of the tile
 
   for (int top = end; top > 0; top -= kThreads) {
     const int lo = max(0, top - kThreads);
     const int j = lo + threadIdx.x;
-    __syncthreads();
+    __syncthreads();  // the previous batch is fully consumed
+    bool keep = false;
+    uint32_t gid = 0;
+    float2 xy;
+    float4 co;
     if (j < top) {
-      const uint32_t g = a.point_list[range.x + j];
-      s_id[threadIdx.x] = g;
-      s_xy[threadIdx.x] = a.mean2d[g];
-      s_co[threadIdx.x] = a.conic_opacity[g];
-      s_rgb[0][threadIdx.x] = a.rgb[3 * g + 0];
-      s_rgb[1][threadIdx.x] = a.rgb[3 * g + 1];
-      s_rgb[2][threadIdx.x] = a.rgb[3 * g + 2];
+      gid = a.point_list[range.x + j];
+      xy = a.mean2d[gid];
+      co = a.conic_opacity[gid];
+      keep = !splat_misses_box(co, xy, bx0, bx1, by0, by1);
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_warp[warp] = __popc(ballot);
+    __syncthreads();
+    int off = 0, cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+      const int c = s_warp[w];
+      off += (w < warp) ? c : 0;
+      cnt += c;
+    }
+    if (keep) {
+      const int idx = off + __popc(ballot & ((1u << lane) - 1u));
+      s_xy[idx] = xy;
+      s_co[idx] = co;
+      s_rgb[idx] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
+      s_id[idx] = gid;
+      s_pos[idx] = (uint32_t)j;
     }
     __syncthreads();
-    for (int k = top - lo - 1; k >= 0; --k) {
-      const int pos = lo + k;  // position in the tile list
-      float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gal = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
-      bool contrib = false;
-      if ((uint32_t)pos < last) {
-        const float2 xy = s_xy[k];
-        const float4 q = s_co[k];
-        const float dx = fx - xy.x, dy = fy - xy.y;
-        // identical arithmetic to the forward so that the skip decisions agree
-        const float p2 = splat_power2(scaled_conic(q), dx, dy);
-        if (p2 <= 0.f) {
-          const float G = ex2_approx(p2);
-          const float raw = __fmul_rn(q.w, G);
-          const float al = fminf(kAlphaMax, raw);
-          if (al >= kAlphaMin) {
-            contrib = true;
-            T = T / (1.f - al);
-            const float c0 = s_rgb[0][k], c1 = s_rgb[1][k], c2 = s_rgb[2][k];
-            const float w = al * T;
-            gr = dL0 * w; gg = dL1 * w; gbl = dL2 * w;
-            const float dal = T * (dL0 * (c0 - R0) + dL1 * (c1 - R1) + dL2 * (c2 - R2));
-            R0 = c0 * al + (1.f - al) * R0;
-            R1 = c1 * al + (1.f - al) * R1;
-            R2 = c2 * al + (1.f - al) * R2;
-            if (raw < kAlphaMax) {
-              gal = dal * G;
-              const float dp = dal * al;  // d alpha / d power = alpha
-              gu = dp * (q.x * dx + q.y * dy);
-              gv = dp * (q.y * dx + q.z * dy);
-              ga = -0.5f * dp * dx * dx;
-              gb = -dp * dx * dy;
-              gc = -0.5f * dp * dy * dy;
-            }
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-        gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
-        gal = warp_sum(gal); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
-        if ((threadIdx.x & 31) == 0) {
+    for (int k = cnt - 1; k >= 0; --k) {
+      const float2 m = s_xy[k];
+      const float4 co_k = s_co[k];
+      const float4 q = scaled_conic(co_k);
+      const float4 c = s_rgb[k];
+      const uint32_t pos = s_pos[k];
+      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const float dx = fx - m.x;
+      const bool b0 = unblend(pxs[0], co_k, q, c, dx, fy[0] - m.y, pos, g);
+      const bool b1 = unblend(pxs[1], co_k, q, c, dx, fy[1] - m.y, pos, g);
+      if (__any_sync(0xffffffffu, b0 || b1)) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = warp_sum(g[i]);
+        if (lane == 0) {
           float* out = a.g2 + (size_t)kG2 * s_id[k];
-          atomicAdd(out + 0, gu); atomicAdd(out + 1, gv); atomicAdd(out + 2, ga); atomicAdd(out + 3, gb);
-          atomicAdd(out + 4, gc); atomicAdd(out + 5, gal); atomicAdd(out + 6, gr); atomicAdd(out + 7, gg);
-          atomicAdd(out + 8, gbl);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) atomicAdd(out + i, g[i]);
         }
       }
     }
@@ -248,22 +294,29 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
   const float da = (-cc * cc * dA_ + cb * cc * dB_ - cb * cb * dC_) * id2;
   const float db = (2.f * cb * cc * dA_ - (ca * cc + cb * cb) * dB_ + 2.f * ca * cb * dC_) * id2;
   const float dc = (-cb * cb * dA_ + ca * cb * dB_ - ca * ca * dC_) * id2;
-  // cov = P P^T + 0.3 I with P = Tm A (2x3)
-  float dP[2][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    dP[0][k] = 2.f * da * ps.B[0][k] + db * ps.B[1][k];
-    dP[1][k] = db * ps.B[0][k] + 2.f * dc * ps.B[1][k];
-  }
-  float dA[3][3], dTm[2][3];
+  // cov = Tm Sigma_cond Tm^T + 0.3 I with Sigma_cond = A A^T: gradients w.r.t. Sigma_cond (as a
+  // symmetric matrix) and w.r.t. Tm
+  float Sc[3][3];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dA[r][k] = ps.Tm[0][r] * dP[0][k] + ps.Tm[1][r] * dP[1][k];
+    for (int k = 0; k < 3; ++k) Sc[r][k] = s.A[r][0] * s.A[k][0] + s.A[r][1] * s.A[k][1] + s.A[r][2] * s.A[k][2];
+  const float* T0 = ps.Tm[0];
+  const float* T1 = ps.Tm[1];
+  float dS[3][3];
 #pragma unroll
-  for (int r = 0; r < 2; ++r)
+  for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) dTm[r][j] = dP[r][0] * s.A[j][0] + dP[r][1] * s.A[j][1] + dP[r][2] * s.A[j][2];
+    for (int k = 0; k < 3; ++k)
+      dS[r][k] = da * T0[r] * T0[k] + 0.5f * db * (T0[r] * T1[k] + T1[r] * T0[k]) + dc * T1[r] * T1[k];
+  float dTm[2][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float s0 = Sc[j][0] * T0[0] + Sc[j][1] * T0[1] + Sc[j][2] * T0[2];
+    const float s1 = Sc[j][0] * T1[0] + Sc[j][1] * T1[1] + Sc[j][2] * T1[2];
+    dTm[0][j] = 2.f * da * s0 + db * s1;
+    dTm[1][j] = db * s0 + 2.f * dc * s1;
+  }
 
   // ---- Tm = J R and the projected mean ----
   {
@@ -287,100 +340,59 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
     for (int k = 0; k < 3; ++k) dmu[k] += cam.R[0][k] * dp[0] + cam.R[1][k] * dp[1] + cam.R[2][k] * dp[2];
   }
 
-  // ---- mu_cond = mu_p + A z ----
-  float dz[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    dm[k] += dmu[k];
-    dz[k] = s.A[0][k] * dmu[0] + s.A[1][k] * dmu[1] + s.A[2][k] * dmu[2];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) dA[r][k] += dmu[r] * s.z[k];
-  }
-
-  // ---- A = L11 H^-T (A^T = H^-1 L11^T) and z = H^-1 u ----
-  float dH[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  float dL11[3][3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {  // column r of A^T is row r of A
-    float dX[3] = {dA[r][0], dA[r][1], dA[r][2]}, dY[3];
-    solve_upper_T<3>(s.H, dX, dY);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dL11[r][k] = dY[k];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q2 = 0; q2 <= p; ++q2) dH[p][q2] -= dY[p] * s.A[r][q2];
-  }
-  float du3[3];
-  solve_upper_T<3>(s.H, dz, du3);
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q2 = 0; q2 <= p; ++q2) dH[p][q2] -= du3[p] * s.z[q2];
-  dLg[0] += dL11[0][0];
-  dLg[1] += dL11[1][0]; dLg[2] += dL11[1][1];
-  dLg[3] += dL11[2][0]; dLg[4] += dL11[2][1]; dLg[5] += dL11[2][2];
-
-  // ---- H = chol(G), reverse of the scalar recurrences ----
-  float dG[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  {
-    const float (&H)[3][3] = s.H;
-    float h00 = dH[0][0], h10 = dH[1][0], h20 = dH[2][0], h11 = dH[1][1], h21 = dH[2][1], h22 = dH[2][2];
-    const float s22 = h22 / (2.f * H[2][2]);
-    dG[2][2] = s22; h20 += -2.f * H[2][0] * s22; h21 += -2.f * H[2][1] * s22;
-    dG[2][1] = h21 / H[1][1]; h20 += -H[1][0] * h21 / H[1][1]; h10 += -H[2][0] * h21 / H[1][1];
-    h11 += -H[2][1] * h21 / H[1][1];
-    const float s11 = h11 / (2.f * H[1][1]);
-    dG[1][1] = s11; h10 += -2.f * H[1][0] * s11;
-    dG[2][0] = h20 / H[0][0]; h00 += -H[2][0] * h20 / H[0][0];
-    dG[1][0] = h10 / H[0][0]; h00 += -H[1][0] * h10 / H[0][0];
-    dG[0][0] = h00 / (2.f * H[0][0]);
-  }
-  // ---- G = I + M^T M (lower entries), u = M^T v ----
-  float dM[4][3], dv4[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    dv4[r] = s.M[r][0] * du3[0] + s.M[r][1] * du3[1] + s.M[r][2] * du3[2];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float acc = du3[c] * s.v[r];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float gab = (c >= b) ? dG[c][b] : dG[b][c];
-        acc += gab * s.M[r][b] * (c == b ? 2.f : 1.f);
-      }
-      dM[r][c] = acc;
-    }
-  }
-  // ---- M = L22^-1 L21, v = L22^-1 e ----
-  const float L22[4][4] = {{L[9], 0.f, 0.f, 0.f}, {L[13], L[14], 0.f, 0.f},
-                           {L[18], L[19], L[20], 0.f}, {L[24], L[25], L[26], L[27]}};
-  float dL22[4][4] = {{0.f}};
-  const int iL21[4][3] = {{6, 7, 8}, {10, 11, 12}, {15, 16, 17}, {21, 22, 23}};
+  // ---- conditioning: mu_cond = mu_p + B W e,  Sigma_cond = Sigma_p - B W B^T ----
+  // with B = Sigma_p,(t,d), W = Sigma_(t,d)^-1, e = (t - mu_t, d - mu_d), evaluated through the
+  // stable factor of the forward: H = W B^T = K11^-T K21^T, w = W e = K11^-T v.
+  float Hm[4][3], w4[4];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float dX[4] = {dM[0][c], dM[1][c], dM[2][c], dM[3][c]}, dY[4];
-    solve_upper_T<4>(L22, dX, dY);
+    float h[4];
+    solve_upper_T<4>(s.K11, s.K21[c], h);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      dLg[iL21[r][c]] += dY[r];
+    for (int k = 0; k < 4; ++k) Hm[k][c] = h[k];
+  }
+  solve_upper_T<4>(s.K11, s.v, w4);
+  float Hd[4];  // H dmu = d e (the gradient w.r.t. e)
 #pragma unroll
-      for (int q2 = 0; q2 <= r; ++q2) dL22[r][q2] -= dY[r] * s.M[q2][c];
+  for (int k = 0; k < 4; ++k) Hd[k] = Hm[k][0] * dmu[0] + Hm[k][1] * dmu[1] + Hm[k][2] * dmu[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dm[k] += dmu[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dm[3 + k] -= Hd[k];
+  // G: gradient w.r.t. the symmetric 7x7 Sigma (order p, t, d), then dL = 2 G L.
+  float G[7][7];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[r][k] = dS[r][k];
+  float SH[3][4];  // dS H^T
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) SH[r][k] = dS[r][0] * Hm[k][0] + dS[r][1] * Hm[k][1] + dS[r][2] * Hm[k][2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float dB = dmu[r] * w4[k] - 2.f * SH[r][k];
+      G[r][3 + k] = 0.5f * dB;
+      G[3 + k][r] = 0.5f * dB;
     }
-  }
-  {
-    float de[4];
-    solve_upper_T<4>(L22, dv4, de);
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+  for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int q2 = 0; q2 <= r; ++q2) dL22[r][q2] -= de[r] * s.v[q2];
-    dm[3] -= de[0]; dm[4] -= de[1]; dm[5] -= de[2]; dm[6] -= de[3];
-  }
-  dLg[9] += dL22[0][0];
-  dLg[13] += dL22[1][0]; dLg[14] += dL22[1][1];
-  dLg[18] += dL22[2][0]; dLg[19] += dL22[2][1]; dLg[20] += dL22[2][2];
-  dLg[24] += dL22[3][0]; dLg[25] += dL22[3][1]; dLg[26] += dL22[3][2]; dLg[27] += dL22[3][3];
+    for (int l = 0; l < 4; ++l)
+      G[3 + k][3 + l] = Hm[k][0] * SH[0][l] + Hm[k][1] * SH[1][l] + Hm[k][2] * SH[2][l] -
+                        0.5f * (Hd[k] * w4[l] + w4[k] * Hd[l]);
+#pragma unroll
+  for (int i2 = 0; i2 < 7; ++i2)
+#pragma unroll
+    for (int j = 0; j <= i2; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = j; k < 7; ++k) acc += G[i2][k] * Lget(L, k, j);
+      dLg[i2 * (i2 + 1) / 2 + j] += 2.f * acc;
+    }
 
   // ---- alpha_cond = alpha exp(e_t) exp(e_d) ----
   {

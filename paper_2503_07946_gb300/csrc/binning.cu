@@ -158,7 +158,8 @@ cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partia
 
 __global__ void __launch_bounds__(kRadixThreads)
 radix_upsweep_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t n_static,
-                     int64_t cap, int shift, uint32_t* __restrict__ hist, int64_t nblocks) {
+                     int64_t cap, int shift, uint32_t* __restrict__ hist, int64_t nblocks,
+                     bool block_major) {
   __shared__ uint32_t s_hist[kRadixWarps][kBins];
   for (int i = threadIdx.x; i < kRadixWarps * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
@@ -181,14 +182,17 @@ radix_upsweep_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int
   uint32_t tot = 0;
 #pragma unroll
   for (int w = 0; w < kRadixWarps; ++w) tot += s_hist[w][threadIdx.x];
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = tot;
+  if (block_major)
+    hist[(int64_t)blockIdx.x * kBins + threadIdx.x] = tot;
+  else
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = tot;
 }
 
 __global__ void __launch_bounds__(kRadixThreads)
 radix_downsweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                        uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                        const int64_t* nptr, int64_t n_static, int64_t cap, int shift,
-                       const uint32_t* __restrict__ hist, int64_t nblocks) {
+                       const uint32_t* __restrict__ hist, int64_t nblocks, bool block_major) {
   __shared__ uint32_t s_keys[kRadixTile];
   __shared__ uint32_t s_vals[kRadixTile];
   __shared__ uint32_t s_whist[kRadixWarps][kBins];
@@ -235,7 +239,20 @@ radix_downsweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __r
     uint32_t tot;
     const uint32_t incl = block_inclusive_scan<uint32_t, kRadixThreads>(run, &tot);
     s_dstart[dg] = incl - run;
-    s_gbase[dg] = hist[(int64_t)dg * nblocks + blockIdx.x];
+    if (block_major) {
+      // raw per-block counts: offset = keys of smaller digits anywhere + this digit in earlier blocks
+      uint32_t before = 0, all = 0;
+      for (int64_t b = 0; b < nblocks; ++b) {
+        const uint32_t c = hist[b * kBins + dg];
+        all += c;
+        before += (b < (int64_t)blockIdx.x) ? c : 0u;
+      }
+      uint32_t dtot;
+      const uint32_t dincl = block_inclusive_scan<uint32_t, kRadixThreads>(all, &dtot);
+      s_gbase[dg] = dincl - all + before;
+    } else {
+      s_gbase[dg] = hist[(int64_t)dg * nblocks + blockIdx.x];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -260,18 +277,24 @@ radix_downsweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __r
 
 // Sorts (keys, vals) by bits [0, bits) in passes of 8 bits, ping-ponging between buffers 0 and 1;
 // returns the index of the buffer that holds the result.
+// Up to this many blocks, each downsweep block derives its offsets from the raw per-block
+// histograms itself (two kernels per pass); beyond it a device-wide scan runs between them.
+constexpr int64_t kFusedScanMaxBlocks = 128;
+
 int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_t n_static,
                int64_t cap, int bits, uint32_t* hist, uint64_t* partials, cudaStream_t st) {
   const int64_t nblocks = (cap + kRadixTile - 1) / kRadixTile;
   int cur = 0;
   if (nblocks == 0) return cur;
+  const bool fused = nblocks <= kFusedScanMaxBlocks;
   for (int shift = 0; shift < bits; shift += 8) {
     radix_upsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(keys[cur], nptr, n_static,
-                                                                        cap, shift, hist, nblocks);
-    exclusive_scan<uint32_t, uint32_t>(hist, (int64_t)kBins * nblocks, hist, partials, nullptr, st);
+                                                                        cap, shift, hist, nblocks, fused);
+    if (!fused)
+      exclusive_scan<uint32_t, uint32_t>(hist, (int64_t)kBins * nblocks, hist, partials, nullptr, st);
     radix_downsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
         keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, hist,
-        nblocks);
+        nblocks, fused);
     cur ^= 1;
   }
   return cur;

@@ -3,15 +3,15 @@
 // Algorithm 1 step 6), EWA projection and SH colour (Sec. 4.3, the 3DGS projection the paper
 // adopts).  Used by the forward kernel and recomputed by the backward kernel.
 //
-// Slicing is evaluated through the precision form of the Schur complement instead of the
-// literal Sigma_p - Sigma_p,(t,d) Sigma_(t,d)^-1 Sigma_p,(t,d)^T, which cancels badly in FP32
-// when the conditional is much narrower than Sigma_p.  With L = [[L11, 0], [L21, L22]]
-// (block 1 = p, block 2 = (t, d)) and M = L22^-1 L21 (4x3):
-//   Sigma_cond = L11 G^-1 L11^T,  G = I + M^T M      (eigenvalues >= 1)
-//   mu_cond    = mu_p + L11 G^-1 M^T L22^-1 (x2 - mu2),  x2 = (t, d)
-// which equal Eqs. cond_cov / cond_mean exactly (Sigma_12 = L11 M^T L22^T,
-// Sigma_22 = L22 (M M^T + I) L22^T and the push-through identity).  With G = H H^T (Cholesky):
-//   A = L11 H^-T,  Sigma_cond = A A^T,  mu_cond = mu_p + A H^-1 M^T v,  v = L22^-1 (x2 - mu2).
+// Slicing never forms Sigma = L L^T.  Forming it squares the conditioning of the (t, d) block,
+// and FP32 then loses several digits of mu_cond for Gaussians whose query lies many standard
+// deviations from their (t, d) mean.  Instead, the rows of L are reordered to (t, d | p) and
+// the 7x7 matrix is made lower triangular again by Givens rotations of its columns (an
+// orthogonal LQ step, backward stable):  P L Q = K,  so  K K^T = P Sigma P^T  with K the Cholesky
+// factor of Sigma in the (t, d | p) order.  With K = [[K11, 0], [K21, K22]]:
+//   mu_cond    = mu_p + K21 K11^-1 (x2 - mu2),   x2 = (t, d)     (= Eq. cond_mean)
+//   Sigma_cond = K22 K22^T                                       (= Eq. cond_cov)
+// since Sigma_(t,d) = K11 K11^T, Sigma_p,(t,d) = K21 K11^T and Sigma_p = K21 K21^T + K22 K22^T.
 // Packed index of L[i][j] (j <= i) is i*(i+1)/2 + j.
 #pragma once
 
@@ -73,79 +73,77 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16])
 
 // Intermediate values of the forward that the backward needs again.
 struct SliceState {
-  // M = L22^-1 L21 (rows r = t, dx, dy, dz; cols = p.x, p.y, p.z), v = L22^-1 (x2 - mu2)
-  float M[4][3];
-  float v[4];
-  float H[3][3];  // Cholesky factor of G = I + M^T M (lower)
-  float z[3];     // H^-1 M^T v
-  float A[3][3];  // L11 H^-T
-  float mu[3];    // mu_cond
+  float K11[4][4];  // Cholesky factor of Sigma_(t,d) (lower)
+  float K21[3][4];  // Sigma_p,(t,d) K11^-T
+  float A[3][3];    // K22: Sigma_cond = A A^T (lower)
+  float v[4];       // K11^-1 (x2 - mu2)
+  float mu[3];      // mu_cond
   // modulation
-  float St;       // Sigma_t
-  float C[3][3];  // Cholesky factor of Sigma_d (lower)
-  float y[3];     // C^-1 (d - mu_d)
-  float e_t, e_d; // exponents of f_temp and f_dir
+  float St;         // Sigma_t
+  float C[3][3];    // Cholesky factor of Sigma_d (lower)
+  float y[3];       // C^-1 (d - mu_d)
+  float e_t, e_d;   // exponents of f_temp and f_dir
 };
 
-// Conditional slicing (precision form above) and modulation for one Gaussian.
+__device__ __forceinline__ float Lget(const float L[28], int i, int j) {
+  return j <= i ? L[i * (i + 1) / 2 + j] : 0.f;
+}
+
+// Conditional slicing (Givens route above) and modulation for one Gaussian.
 // L: packed 28 entries, m: mean7.  Returns alpha_cond.
 __device__ __forceinline__ float slice_one(const float L[28], const float m[7], float alpha,
                                            const Query& q, SliceState& s) {
-  // L21 rows (t, dx, dy, dz) x cols (p.x, p.y, p.z); L22 lower 4x4.
-  const float L21[4][3] = {{L[6], L[7], L[8]}, {L[10], L[11], L[12]},
-                           {L[15], L[16], L[17]}, {L[21], L[22], L[23]}};
-  const float d0 = 1.f / L[9], d1 = 1.f / L[14], d2 = 1.f / L[20], d3 = 1.f / L[27];
+  // B = rows (t, dx, dy, dz, px, py, pz) of L
+  float B[7][7];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float m0 = L21[0][c] * d0;
-    const float m1 = (L21[1][c] - L[13] * m0) * d1;
-    const float m2 = (L21[2][c] - L[18] * m0 - L[19] * m1) * d2;
-    const float m3 = (L21[3][c] - L[24] * m0 - L[25] * m1 - L[26] * m2) * d3;
-    s.M[0][c] = m0; s.M[1][c] = m1; s.M[2][c] = m2; s.M[3][c] = m3;
+  for (int r = 0; r < 7; ++r) {
+    const int src = r < 4 ? r + 3 : r - 4;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) B[r][c] = Lget(L, src, c);
   }
-  const float e0 = q.t - m[3], e1 = q.d[0] - m[4], e2 = q.d[1] - m[5], e3 = q.d[2] - m[6];
-  s.v[0] = e0 * d0;
-  s.v[1] = (e1 - L[13] * s.v[0]) * d1;
-  s.v[2] = (e2 - L[18] * s.v[0] - L[19] * s.v[1]) * d2;
-  s.v[3] = (e3 - L[24] * s.v[0] - L[25] * s.v[1] - L[26] * s.v[2]) * d3;
-
-  float G[3][3], u[3];
+  // Zero the entries right of the diagonal, row by row, rotating column c into column r.
+  // Rows above r are already zero in both columns and are left alone.
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    u[a] = s.M[0][a] * s.v[0] + s.M[1][a] * s.v[1] + s.M[2][a] * s.v[2] + s.M[3][a] * s.v[3];
+  for (int r = 0; r < 6; ++r) {
 #pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      G[a][b] = (a == b ? 1.f : 0.f) + s.M[0][a] * s.M[0][b] + s.M[1][a] * s.M[1][b] +
-                s.M[2][a] * s.M[2][b] + s.M[3][a] * s.M[3][b];
+    for (int c = r + 1; c < 7; ++c) {
+      if (r < 4 && c > r + 3) continue;  // structurally zero: the t, d rows of L end at column r + 3
+      const float a = B[r][r], b = B[r][c];
+      const float h = sqrtf(a * a + b * b);
+      if (!(h > 0.f)) continue;
+      const float ih = 1.f / h;
+      const float cs = a * ih, sn = b * ih;
+#pragma unroll
+      for (int i = r; i < 7; ++i) {
+        const float x = B[i][r], y = B[i][c];
+        B[i][r] = cs * x + sn * y;
+        B[i][c] = cs * y - sn * x;
+      }
     }
   }
-  // H = chol(G)
-  float (&H)[3][3] = s.H;
-  H[0][0] = sqrtf(G[0][0]);
-  const float ih0 = 1.f / H[0][0];
-  H[1][0] = G[1][0] * ih0;
-  H[2][0] = G[2][0] * ih0;
-  H[1][1] = sqrtf(G[1][1] - H[1][0] * H[1][0]);
-  const float ih1 = 1.f / H[1][1];
-  H[2][1] = (G[2][1] - H[2][0] * H[1][0]) * ih1;
-  H[2][2] = sqrtf(G[2][2] - H[2][0] * H[2][0] - H[2][1] * H[2][1]);
-  const float ih2 = 1.f / H[2][2];
-  H[0][1] = H[0][2] = H[1][2] = 0.f;
-  s.z[0] = u[0] * ih0;
-  s.z[1] = (u[1] - H[1][0] * s.z[0]) * ih1;
-  s.z[2] = (u[2] - H[2][0] * s.z[0] - H[2][1] * s.z[1]) * ih2;
-  // A = L11 H^-T, row by row: H a^T = l^T
-  const float L11[3][3] = {{L[0], 0.f, 0.f}, {L[1], L[2], 0.f}, {L[3], L[4], L[5]}};
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const float a0 = L11[r][0] * ih0;
-    const float a1 = (L11[r][1] - H[1][0] * a0) * ih1;
-    const float a2 = (L11[r][2] - H[2][0] * a0 - H[2][1] * a1) * ih2;
-    s.A[r][0] = a0; s.A[r][1] = a1; s.A[r][2] = a2;
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s.K11[i][j] = j <= i ? B[i][j] : 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s.K21[i][j] = B[4 + i][j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s.A[i][j] = j <= i ? B[4 + i][4 + j] : 0.f;
+  }
+  const float e[4] = {q.t - m[3], q.d[0] - m[4], q.d[1] - m[5], q.d[2] - m[6]};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float acc = e[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) acc -= s.K11[i][j] * s.v[j];
+    s.v[i] = acc / s.K11[i][i];
   }
 #pragma unroll
   for (int r = 0; r < 3; ++r)
-    s.mu[r] = m[r] + s.A[r][0] * s.z[0] + s.A[r][1] * s.z[1] + s.A[r][2] * s.z[2];
+    s.mu[r] = m[r] + s.K21[r][0] * s.v[0] + s.K21[r][1] * s.v[1] + s.K21[r][2] * s.v[2] +
+              s.K21[r][3] * s.v[3];
 
   // Modulation with the marginal blocks: Sigma_t = |row 3 of L|^2, Sigma_d = rows 4..6 of L
   // times their transpose.
@@ -171,10 +169,10 @@ __device__ __forceinline__ float slice_one(const float L[28], const float m[7], 
   C[2][2] = sqrtf(S66 - C[2][0] * C[2][0] - C[2][1] * C[2][1]);
   const float ic2 = 1.f / C[2][2];
   C[0][1] = C[0][2] = C[1][2] = 0.f;
-  s.y[0] = e1 * ic0;
-  s.y[1] = (e2 - C[1][0] * s.y[0]) * ic1;
-  s.y[2] = (e3 - C[2][0] * s.y[0] - C[2][1] * s.y[1]) * ic2;
-  s.e_t = -0.5f * q.lambda_t * e0 * e0 / s.St;
+  s.y[0] = e[1] * ic0;
+  s.y[1] = (e[2] - C[1][0] * s.y[0]) * ic1;
+  s.y[2] = (e[3] - C[2][0] * s.y[0] - C[2][1] * s.y[1]) * ic2;
+  s.e_t = -0.5f * q.lambda_t * e[0] * e[0] / s.St;
   s.e_d = -0.5f * q.lambda_d * (s.y[0] * s.y[0] + s.y[1] * s.y[1] + s.y[2] * s.y[2]);
   return alpha * expf(s.e_t) * expf(s.e_d);
 }

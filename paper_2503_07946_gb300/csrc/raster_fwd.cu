@@ -38,6 +38,7 @@ struct Pixel {
 // One (pixel, Gaussian) evaluation written without branches, so that a thread's two pixels
 // interleave: the pixel takes the Gaussian iff it is still running, the exponent is <= 0 and
 // alpha >= 1/255; if that would take T below 1e-4 the pixel stops instead (without blending).
+template <bool kCount>
 __device__ __forceinline__ void blend(Pixel& px, const float4& q, const float4& c, float dx, float dy,
                                       uint32_t pos1) {
   const float p2 = splat_power2(q, dx, dy);
@@ -48,7 +49,7 @@ __device__ __forceinline__ void blend(Pixel& px, const float4& q, const float4& 
   const bool stop = hit && Tn < kTMin;
   const bool take = hit && !stop;
   const float w = take ? al * px.T : 0.f;
-  px.evaluated += live ? 1u : 0u;
+  if (kCount) px.evaluated += live ? 1u : 0u;
   px.c0 += c.x * w;
   px.c1 += c.y * w;
   px.c2 += c.z * w;
@@ -57,6 +58,7 @@ __device__ __forceinline__ void blend(Pixel& px, const float4& q, const float4& 
   px.done = px.done || stop;
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
   __shared__ float2 s_xy[kThreads];
   __shared__ float4 s_q[kThreads];
@@ -112,20 +114,28 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
     }
     __syncthreads();
     if (!(p0.done && p1.done)) {
-      for (int k = 0; k < cnt; ++k) {
-        const float2 m = s_xy[k];
-        const float4 q = s_q[k];
-        const float4 c = s_rgb[k];
-        const uint32_t pos1 = (uint32_t)s_pos[k] + 1u;
-        // offsets exactly as the backward forms them, so both passes take the same decisions
-        const float dx = fx - m.x;
-        blend(p0, q, c, dx, fy0 - m.y, pos1);
-        blend(p1, q, c, dx, fy1 - m.y, pos1);
+      // Entries past cnt are never read: the batch is padded by predication.  The stop test runs
+      // every 4 Gaussians; a stopped pixel ignores the rest (blend is a no-op once done).
+      for (int k0 = 0; k0 < cnt; k0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + u;
+          if (k < cnt) {
+            const float2 m = s_xy[k];
+            const float4 q = s_q[k];
+            const float4 c = s_rgb[k];
+            const uint32_t pos1 = (uint32_t)s_pos[k] + 1u;
+            // offsets exactly as the backward forms them, so both passes take the same decisions
+            const float dx = fx - m.x;
+            blend<kCount>(p0, q, c, dx, fy0 - m.y, pos1);
+            blend<kCount>(p1, q, c, dx, fy1 - m.y, pos1);
+          }
+        }
         if (p0.done && p1.done) break;
       }
     }
   }
-  if (a.n_evaluated != nullptr) {
+  if (kCount) {
     unsigned long long e = (unsigned long long)p0.evaluated + p1.evaluated;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -168,7 +178,10 @@ cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const
   a.n_evaluated = reinterpret_cast<unsigned long long*>(n_evaluated);
   const int tiles = a.tiles_x * tiles_of(v.height);
   if (tiles == 0) return cudaSuccess;
-  render_fwd_kernel<<<tiles, kThreads, 0, st>>>(a);
+  if (n_evaluated != nullptr)
+    render_fwd_kernel<true><<<tiles, kThreads, 0, st>>>(a);
+  else
+    render_fwd_kernel<false><<<tiles, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -72,8 +72,8 @@ def boundary_gaussians(g: dict) -> np.ndarray:
                       | (m["edge_px"].numpy() < EDGE_PX))
 
 
-def pixel_ok(margin_alpha, margin_T, margin_depth=None):
+def pixel_ok(margin_alpha, margin_T, margin_depth=None, depth_rel=PIX_DEPTH):
     ok = (np.asarray(margin_alpha) >= PIX_ALPHA) & (np.asarray(margin_T) >= PIX_T)
     if margin_depth is not None:
-        ok &= np.asarray(margin_depth) >= PIX_DEPTH
+        ok &= np.asarray(margin_depth) >= depth_rel
     return ok

@@ -40,9 +40,8 @@ def test_slice_project_records(scene0, ci):
     assert both.sum() > 100
     np.testing.assert_array_equal(got["rect"][both], g["rect"].numpy()[both])
     np.testing.assert_array_equal(got["radius"][both], g["radius"].numpy()[both].astype(np.int32))
-    # FP32 conditioning: the shift Sigma_p,(t,d) Sigma_(t,d)^-1 (x - mu) carries ~1e-6 relative error
-    np.testing.assert_allclose(got["mean2d"][both], g["mean2d"].numpy()[both], rtol=0, atol=5e-3)
-    np.testing.assert_allclose(got["depth"][both], g["depth"].numpy()[both], rtol=5e-5)
+    np.testing.assert_allclose(got["mean2d"][both], g["mean2d"].numpy()[both], rtol=0, atol=1e-3)
+    np.testing.assert_allclose(got["depth"][both], g["depth"].numpy()[both], rtol=4e-6)
     co = got["conic_opacity"][both]
     cref = g["conic"].numpy()[both]
     scale = np.abs(cref).max(1, keepdims=True)
@@ -59,12 +58,13 @@ def _random_bin_cases():
         (5000, 256, 256, 3),     # one tile pass, several radix blocks of Gaussians
         (20000, 1352, 1014, 4),  # two tile passes (5440 tiles), K spans many blocks
         (3000, 1920, 1080, 5),   # 8160 tiles
+        (600_000, 800, 800, 6),  # > 128 radix blocks: depth passes with a separate histogram scan
     ]
 
 
 @pytest.mark.parametrize("n,W,H,seed", _random_bin_cases())
 def test_bin_sort_bit_exact_on_random_records(n, W, H, seed):
-    rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=12)
+    rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=12 if n < 100_000 else 2)
     proj = U.sdgs.ProjectedBuffers.from_host(rec)
     view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5))
     okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], (W + 15) // 16)
