@@ -53,7 +53,7 @@ def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -68,7 +68,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         return self
@@ -298,6 +298,7 @@ def run_ours(args, rank: int, world: int):
 
     # ---- fwd + bwd (L2 loss against a target from perturbed parameters, camera 0) ----
     fb = fwd_bwd_its(scene, cams[0], steps, warm, dev)
+    serving = None if args.no_serving else serving_bench(dev)
 
     pix = W * H
     value = world * pix / (ms * 1e-3) / 1e6
@@ -319,6 +320,7 @@ def run_ours(args, rank: int, world: int):
                       "render_fwd": raster_ms},
         "workload_stats": {"instances": k_inst, "visible": visible, "evaluations_per_frame": evals // steps},
         "fwd_bwd_it_s": fb,
+        "serving": serving,
         "e2e": {"value": world * pix / e2e_s / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
                 "d2h_bytes_per_step": pix * 3 * 4 + 8},
         "gpu_launches": steps * launches_per_frame(scene.n, W, H),
@@ -343,6 +345,93 @@ def ctypes_sizeof_view() -> int:
 
     from paper_2503_07946_gb300 import sdgs
     return ctypes.sizeof(sdgs.View)
+
+
+SERVE_SIZES = [(400, 400), (800, 800), (1352, 1014), (1920, 1080)]
+
+
+def serving_trace(rate: float, count: int, seed: int, radii) -> list:
+    """Poisson arrivals at `rate` req/s; each request picks a scene, a resolution, a camera on
+    that scene's orbit and a time t, all uniformly."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    out = []
+    for i in range(count):
+        sid = int(rng.integers(0, len(radii)))
+        w, h = SERVE_SIZES[int(rng.integers(0, len(SERVE_SIZES)))]
+        d = rng.normal(size=3)
+        eye = radii[sid] * d / np.linalg.norm(d)
+        out.append((float(t[i]), sid, synth.make_camera(eye, w, h, 60.0, float(rng.uniform()))))
+    return out
+
+
+def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: int = 8) -> dict:
+    """p50/p99 latency and Mpix/s of the render server on Poisson traces, against serving the same
+    trace one request at a time through the plain path (FIFO; the measured service times of the
+    plain path are replayed against the arrival times)."""
+    from paper_2503_07946_gb300 import render as prender
+    from paper_2503_07946_gb300 import sdgs
+    scenes = synth.serving_scenes()
+    radii = [4.0, 4.0, 8.0, 8.0]
+    tens = [prender.scene_to_device(s) for s in scenes]
+    ring = 48
+    bufs = {wh: [torch.empty(wh[1], wh[0], 3, dtype=torch.float32, device=dev) for _ in range(ring)]
+            for wh in SERVE_SIZES}
+    result = {"scenes": [s.n for s in scenes], "resolutions": SERVE_SIZES, "requests_per_rate": count,
+              "slots": slots, "output": "device buffers"}
+    renderers = {}
+
+    def plain(sid, cam):
+        key = (sid, cam.width, cam.height)
+        if key not in renderers:
+            renderers[key] = prender.Renderer(scenes[sid].n, cam.width, cam.height)
+        r = renderers[key]
+        st = sdgs.scene_struct(tens[sid], scenes[sid].lambda_t, scenes[sid].lambda_d)
+        img = r.forward(st, sdgs.view_struct(cam))
+        bufs[(cam.width, cam.height)][0].copy_(img)
+        torch.cuda.synchronize()
+
+    with sdgs.Server(budget_bytes=16 << 30, slots=slots) as srv:
+        ids = [srv.add_scene(t, s.lambda_t, s.lambda_d) for t, s in zip(tens, scenes)]
+        warm = serving_trace(100.0, 16, 99, radii)
+        for _, sid, cam in warm:  # allocate slot buffers and learn instance counts
+            srv.wait(srv.submit(ids[sid], sdgs.view_struct(cam), bufs[(cam.width, cam.height)][1]), 60_000)
+            plain(sid, cam)
+        for rate in rates:
+            trace = serving_trace(rate, count, int(rate), radii)
+            # server, live
+            rids, subs = [], []
+            t0 = time.perf_counter()
+            for i, (ta, sid, cam) in enumerate(trace):
+                while time.perf_counter() - t0 < ta:
+                    pass
+                if i >= ring:
+                    srv.wait(rids[i - ring], 60_000)  # its output buffer is reused now
+                rids.append(srv.submit(ids[sid], sdgs.view_struct(cam), bufs[(cam.width, cam.height)][i % ring]))
+                subs.append(time.perf_counter() - t0)
+            lat = np.array([srv.wait(r, 60_000) for r in rids]) * 1e-3
+            srv.release()
+            done = np.array(subs) + lat
+            pix = sum(c.width * c.height for _, _, c in trace)
+            # one at a time, plain path
+            service = []
+            for _, sid, cam in trace:
+                a = time.perf_counter()
+                plain(sid, cam)
+                service.append(time.perf_counter() - a)
+            finish, lat1 = 0.0, []
+            for (ta, _, _), sv in zip(trace, service):
+                finish = max(finish, ta) + sv
+                lat1.append(finish - ta)
+            lat1 = np.array(lat1)
+            result[f"rate_{int(rate)}"] = {
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mpix_s": pix / (done.max() - trace[0][0]) / 1e6,
+                "one_at_a_time": {"p50_ms": float(np.percentile(lat1, 50) * 1e3),
+                                  "p99_ms": float(np.percentile(lat1, 99) * 1e3),
+                                  "mpix_s": pix / (finish - trace[0][0]) / 1e6}}
+        result["server_stats"] = srv.stats()
+    return result
 
 
 def fwd_bwd_its(scene, cam, steps: int, warm: int, dev) -> dict:
@@ -382,10 +471,11 @@ def fwd_bwd_its(scene, cam, steps: int, warm: int, dev) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving latency benchmark")
     ap.add_argument("--frames-only", action="store_true",
                     help="time the forward frames only (no e2e, fwd+bwd or CPU baseline); for profiling")
     args = ap.parse_args()

@@ -210,6 +210,74 @@ int sdgs_render_bwd(const sdgs_scene* scene, const sdgs_view* view, const sdgs_p
                     const float* dL_dimage, void* workspace, size_t workspace_bytes,
                     const sdgs_grads* grads, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Render server.  The paper has no serving component; this realises "render requests over
+ * resident scenes" on one GPU.  Scenes stay resident (caller-owned device arrays).  Requests --
+ * a scene, a view (camera, time t, direction d) and a destination -- enter a FIFO queue and are
+ * admitted as soon as a slot (a CUDA stream with its own buffers) is free and the device-memory
+ * budget allows: continuous batching, so requests that arrive while others run are admitted while
+ * the earlier ones are still on the GPU, and their work overlaps.  Requests admitted together
+ * share one batched slicing launch; binning and compositing run on the requests' own streams.
+ * Each request's image is bit-identical to rendering it alone through sdgs_slice_project,
+ * sdgs_bin_sort and sdgs_render_fwd (no arithmetic depends on the mix).
+ * ------------------------------------------------------------------------------------------ */
+
+enum sdgs_request_state {
+  SDGS_REQ_QUEUED = 0,
+  SDGS_REQ_RUNNING = 1,
+  SDGS_REQ_DONE = 2,
+  SDGS_REQ_FAILED = 3
+};
+
+typedef struct sdgs_server_cfg {
+  size_t hbm_budget_bytes;  /* device memory the server may hold for request buffers */
+  int32_t max_slots;        /* requests in flight at once (1..64) */
+  int32_t queue_capacity;   /* queued requests beyond which submit returns SDGS_ERR_BUSY */
+  int32_t device;           /* CUDA device ordinal */
+} sdgs_server_cfg;
+
+typedef struct sdgs_server_stats {
+  uint64_t submitted, completed, failed, retried;
+  uint64_t batches;          /* batched slicing launches */
+  uint64_t max_batch;        /* largest number of requests in one batched launch */
+  size_t bytes_allocated;    /* device memory held by the slots */
+} sdgs_server_stats;
+
+typedef struct sdgs_server sdgs_server;
+
+/* Create a server (starts its worker thread; allocates nothing until requests arrive).
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_CUDA. */
+int sdgs_server_create(const sdgs_server_cfg* cfg, sdgs_server** out);
+
+/* Register a resident scene (device arrays stay owned by the caller and must outlive the server).
+ * Writes *scene_id.  Errors: SDGS_ERR_INVALID_ARG. */
+int sdgs_server_add_scene(sdgs_server* server, const sdgs_scene* scene, int32_t* scene_id);
+
+/* Queue a render of scene_id from `view`.  out_image receives height x width x 3 float32 (HWC)
+ * when the request is DONE; it may be device memory or host memory (page-locked host memory keeps
+ * the copy asynchronous) and must stay valid until then.  Writes *req_id.
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_NOT_FOUND (scene), SDGS_ERR_BUSY (queue full),
+ * SDGS_ERR_OOM_BUDGET (the request alone needs more than the budget). */
+int sdgs_server_submit(sdgs_server* server, int32_t scene_id, const sdgs_view* view,
+                       float* out_image, uint64_t* req_id);
+
+/* State of a request and, once DONE, its latency (submit to completion, milliseconds, host
+ * monotonic clock).  Errors: SDGS_ERR_NOT_FOUND. */
+int sdgs_server_poll(sdgs_server* server, uint64_t req_id, int32_t* state, float* latency_ms);
+
+/* Wait up to timeout_ms for a request to finish.  Returns SDGS_OK when DONE, SDGS_ERR_TIMEOUT if
+ * it is still queued or running, or the request's own error code if it FAILED. */
+int sdgs_server_wait(sdgs_server* server, uint64_t req_id, int32_t timeout_ms, float* latency_ms);
+
+/* Forget finished requests (their ids become unknown).  Returns the number released. */
+int sdgs_server_release(sdgs_server* server, uint64_t req_id);
+
+int sdgs_server_get_stats(sdgs_server* server, sdgs_server_stats* stats);
+
+/* Stop the worker after the requests in flight finish, and free the server's device memory.
+ * Queued requests that never started are marked FAILED. */
+void sdgs_server_destroy(sdgs_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,12 @@ inline int tiles_of(int px) { return (px + kTile - 1) / kTile; }
 cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o,
                                  cudaStream_t st);
 
+// Batched slicing for the server: one argument block per request, uploaded by the caller.
+size_t slice_job_bytes();
+void fill_slice_job(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o, void* dst);
+cudaError_t launch_slice_project_batched(const void* jobs_device, int njobs, int64_t max_n,
+                                         cudaStream_t st);
+
 struct BinPlan {
   int64_t n;
   int64_t capacity;

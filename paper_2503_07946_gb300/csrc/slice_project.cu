@@ -1,5 +1,7 @@
 // Forward per-Gaussian kernel: conditional slicing + modulation + cull + EWA projection + SH
 // colour, fused into one pass over the scene (one thread per Gaussian).
+#include <string.h>
+
 #include "geometry.cuh"
 
 namespace sdgs {
@@ -24,10 +26,23 @@ struct SliceArgs {
 
 constexpr int kThreads = 128;
 
+__device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i);
+
 __global__ void __launch_bounds__(kThreads) slice_project_kernel(const SliceArgs a) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;
+  slice_project_one(a, i);
+}
 
+// Several requests in one launch: blockIdx.y selects the request's argument block.
+__global__ void __launch_bounds__(kThreads) slice_project_batched_kernel(const SliceArgs* __restrict__ jobs) {
+  const SliceArgs& a = jobs[blockIdx.y];
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= a.n) return;
+  slice_project_one(a, i);
+}
+
+__device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i) {
   float L[28];
   const float4* Lp = reinterpret_cast<const float4*>(a.L28 + 28 * i);  // 112-byte rows: aligned
 #pragma unroll
@@ -126,9 +141,33 @@ Query make_query(const sdgs_scene& s, const sdgs_view& v) {
   return q;
 }
 
+static SliceArgs make_args(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o);
+
 cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o,
                                  cudaStream_t st) {
   if (s.n == 0) return cudaSuccess;
+  const SliceArgs a = make_args(s, v, o);
+  const int64_t blocks = (s.n + kThreads - 1) / kThreads;
+  slice_project_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t slice_job_bytes() { return sizeof(SliceArgs); }
+
+void fill_slice_job(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o, void* dst) {
+  const SliceArgs a = make_args(s, v, o);
+  memcpy(dst, &a, sizeof(SliceArgs));
+}
+
+cudaError_t launch_slice_project_batched(const void* jobs_device, int njobs, int64_t max_n, cudaStream_t st) {
+  if (njobs == 0 || max_n == 0) return cudaSuccess;
+  const int64_t blocks = (max_n + kThreads - 1) / kThreads;
+  slice_project_batched_kernel<<<dim3((unsigned)blocks, (unsigned)njobs), kThreads, 0, st>>>(
+      reinterpret_cast<const SliceArgs*>(jobs_device));
+  return cudaGetLastError();
+}
+
+static SliceArgs make_args(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o) {
   SliceArgs a;
   a.mean7 = s.mean7; a.L28 = s.L28; a.opacity = s.opacity; a.sh = s.sh; a.n = s.n;
   a.q = make_query(s, v);
@@ -139,9 +178,7 @@ cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const 
   a.depth = o.depth;
   a.rect = reinterpret_cast<ushort4*>(o.rect);
   a.radius = o.radius;
-  const int64_t blocks = (s.n + kThreads - 1) / kThreads;
-  slice_project_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  return a;
 }
 
 }  // namespace sdgs

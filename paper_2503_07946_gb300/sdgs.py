@@ -56,6 +56,19 @@ class Grads(ctypes.Structure):
                 ("dsh", ctypes.c_void_p)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("retried", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("max_batch", ctypes.c_uint64),
+                ("bytes_allocated", ctypes.c_size_t)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 _lib = None
 
 # Exported symbols and their argument types; the CPU tests check this list against include/sdgs.h.
@@ -78,6 +91,18 @@ SIGNATURES = {
                          ctypes.POINTER(Bins), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(Grads), ctypes.c_void_p],
                         ctypes.c_int),
+    "sdgs_server_create": ([ctypes.POINTER(ServerCfg), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "sdgs_server_add_scene": ([ctypes.c_void_p, ctypes.POINTER(Scene), ctypes.POINTER(ctypes.c_int32)],
+                              ctypes.c_int),
+    "sdgs_server_submit": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(View), ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "sdgs_server_poll": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "sdgs_server_wait": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)],
+                         ctypes.c_int),
+    "sdgs_server_release": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "sdgs_server_get_stats": ([ctypes.c_void_p, ctypes.POINTER(ServerStats)], ctypes.c_int),
+    "sdgs_server_destroy": ([ctypes.c_void_p], None),
 }
 
 
@@ -266,3 +291,63 @@ def render_bwd(scene: Scene, view: View, proj: ProjectedBuffers, bins: BinBuffer
     _check(lib().sdgs_render_bwd(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(proj.struct()),
                                  ctypes.byref(bins.struct()), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
                                  _ptr(workspace), workspace.numel(), ctypes.byref(g), _stream(stream)))
+
+
+class Server:
+    """The sdgs_server_* entry points: resident scenes, continuous batching of render requests.
+
+    Scene tensors (and output images) must stay alive while the server uses them; this wrapper
+    keeps references to the scenes it registered.
+    """
+
+    def __init__(self, budget_bytes: int = 8 << 30, slots: int = 4, queue_capacity: int = 4096, device: int = 0):
+        cfg = ServerCfg(budget_bytes, slots, queue_capacity, device)
+        h = ctypes.c_void_p()
+        _check(lib().sdgs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._scenes = []
+
+    def add_scene(self, tensors: dict, lambda_t: float, lambda_d: float) -> int:
+        sid = ctypes.c_int32(-1)
+        st = scene_struct(tensors, lambda_t, lambda_d)
+        _check(lib().sdgs_server_add_scene(self.handle, ctypes.byref(st), ctypes.byref(sid)))
+        self._scenes.append(tensors)
+        return int(sid.value)
+
+    def submit(self, scene_id: int, view: View, out_image: torch.Tensor) -> int:
+        """out_image: [H, W, 3] float32, on the device or in page-locked host memory."""
+        if out_image.dtype != torch.float32 or not out_image.is_contiguous():
+            raise ValueError("out_image must be contiguous float32")
+        rid = ctypes.c_uint64(0)
+        _check(lib().sdgs_server_submit(self.handle, scene_id, ctypes.byref(view), out_image.data_ptr(),
+                                        ctypes.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, rid: int):
+        st, lat = ctypes.c_int32(-1), ctypes.c_float(0)
+        _check(lib().sdgs_server_poll(self.handle, rid, ctypes.byref(st), ctypes.byref(lat)))
+        return int(st.value), float(lat.value)
+
+    def wait(self, rid: int, timeout_ms: int = 10_000) -> float:
+        lat = ctypes.c_float(0)
+        _check(lib().sdgs_server_wait(self.handle, rid, timeout_ms, ctypes.byref(lat)))
+        return float(lat.value)
+
+    def release(self, rid: int = 0) -> int:
+        return int(lib().sdgs_server_release(self.handle, rid))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().sdgs_server_get_stats(self.handle, ctypes.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().sdgs_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

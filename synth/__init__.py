@@ -15,4 +15,7 @@ from .scenes import (  # noqa: F401
     config_cameras,
     perturb_scene,
     random_projected,
+    serving_scenes,
+    WHITE,
+    BLACK,
 )
