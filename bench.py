@@ -35,6 +35,10 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # exponent (8), opacity clamp (2), tests (2), transmittance (2), weight (1), colour FMAs (6) = 23
 # FLOP (an FMA counts 2) plus one exp2 on the MUFU pipe.
 FLOP_PER_EVAL = 23
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture summarised in
+# profiles/render_fwd_config1_800x800_300k.md.  Set to None whenever render_fwd_kernel changes
+# until it is captured again.
+RENDER_FWD_TRAFFIC_BYTES = 29.42208e6 + 0.11008e6
 
 
 def load_peaks() -> dict:
@@ -326,7 +330,7 @@ def run_ours(args, rank: int, world: int):
         "gpu_launches": steps * launches_per_frame(scene.n, W, H),
         "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
-                     "traffic": None,
+                     "traffic": RENDER_FWD_TRAFFIC_BYTES,
                      "note": "FP32 FMA peak 152 SM x 128 lanes x 2 x %.0f MHz (max clock); %d FLOP per "
                              "evaluated (pixel, Gaussian) pair" % (sm_for_peak, FLOP_PER_EVAL)},
         "slice_project_hbm": {"achieved": slice_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
