@@ -38,7 +38,7 @@ FLOP_PER_EVAL = 23
 # DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture summarised in
 # profiles/render_fwd_config1_800x800_300k.md.  Set to None whenever render_fwd_kernel changes
 # until it is captured again.
-RENDER_FWD_TRAFFIC_BYTES = 29.42208e6 + 0.11008e6
+RENDER_FWD_TRAFFIC_BYTES = None
 
 
 def load_peaks() -> dict:
@@ -179,14 +179,17 @@ def run_reference(args, rank: int, world: int):
 # Our arm
 # ---------------------------------------------------------------------------------------------
 
-def launches_per_frame(n: int, width: int, height: int) -> int:
-    """Kernels libsdgs launches for one render: slice_project; depth keys; 4 depth radix passes
-    (upsweep + downsweep, plus a 3-kernel histogram scan above 128 radix blocks); scatter-cost units + their 3-kernel scan; the per-chunk
-    tile histogram + the 3-kernel scan of the (tile, chunk) matrix; the scatter into tile lists;
-    tile ranges; the rasteriser."""
-    blocks = (n + 4095) // 4096
-    per_pass = 2 if blocks <= 128 else 5
-    return 1 + 1 + 4 * per_pass + 1 + 3 + 1 + 3 + 1 + 1 + 1
+def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
+    """Kernels libsdgs launches for one render: slice_project; depth keys; 4 depth radix passes over
+    the n Gaussians; the tested rectangles; the kept-tile counts and their 3-kernel scan; the
+    duplication into depth order; ceil(tile bits / 8) tile radix passes over `capacity` slots;
+    tile ranges; the rasteriser.  A radix pass is an upsweep and a downsweep, plus a 3-kernel
+    histogram scan above 128 radix blocks of 4096 keys."""
+    def per_pass(m):
+        return 2 if (m + 4095) // 4096 <= 128 else 5
+    tiles = ((width + 15) // 16) * ((height + 15) // 16)
+    bits = max(0, (tiles - 1).bit_length())
+    return 1 + 1 + 4 * per_pass(n) + 1 + 1 + 3 + 1 + ((bits + 7) // 8) * per_pass(capacity) + 1 + 1
 
 
 def cpu_baseline(scene, cam) -> dict:
@@ -327,7 +330,7 @@ def run_ours(args, rank: int, world: int):
         "serving": serving,
         "e2e": {"value": world * pix / e2e_s / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
                 "d2h_bytes_per_step": pix * 3 * 4 + 8},
-        "gpu_launches": steps * launches_per_frame(scene.n, W, H),
+        "gpu_launches": steps * launches_per_frame(scene.n, r.bins.capacity, W, H),
         "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
                      "traffic": RENDER_FWD_TRAFFIC_BYTES,

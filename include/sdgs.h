@@ -4,14 +4,14 @@
  * The render path of 7DGS without adaptive refinement:
  *   sdgs_slice_project  conditional slicing of each 7D Gaussian at (t, d) (Sec. 4.2, Eqs.
  *                       cond_mean / cond_cov, temp_mod / dir_mod; Algorithm 1 steps 3-6) fused
- *                       with the 3DGS perspective (EWA) projection and SH colour (Sec. 4.3).
+ *                       with the 3DGS perspective (EWA) projection and SH colour (Sec. 4.4).
  *   sdgs_bin_sort       tile binning: one instance per (tile, Gaussian) ordered by
  *                       (tile, depth, Gaussian id) -- the 3DGS tile sort the paper's rasteriser
- *                       uses (Sec. 4.3) -- and per-tile [start, end) ranges.
- *   sdgs_render_fwd     front-to-back alpha compositing per pixel (Sec. 4.3, "depth-aware,
- *                       opacity-blended").
+ *                       uses (Sec. 4.4) -- and per-tile [start, end) ranges.
+ *   sdgs_render_fwd     front-to-back alpha compositing per pixel (Sec. 4.4; the 3DGS
+ *                       blending rules).
  *   sdgs_render_bwd     adjoint of the three steps above, for the joint optimisation of all 7D
- *                       parameters (Sec. 4.3; Sec. 1 contributions).
+ *                       parameters (Sec. 4.4; Sec. 1 contributions).
  *   sdgs_server_*       a continuous-batching render server over resident scenes.
  *
  * Conventions for every entry point:
@@ -88,7 +88,7 @@ typedef struct sdgs_view {
 } sdgs_view;
 
 /* Per-Gaussian screen-space record written by sdgs_slice_project (device, caller-allocated,
- * n entries each).  A culled Gaussian has rect = {0, 0, 0, 0}; its other fields are unspecified.
+ * n entries each; binning takes n < 2^30).  A culled Gaussian has rect = {0, 0, 0, 0}; its other fields are unspecified.
  *   mean2d        [n][2]  projected conditional mean (u, v) in pixels
  *   conic_opacity [n][4]  (a, b, c, alpha_cond): inverse 2D covariance [[a, b], [b, c]] and the
  *                         conditional opacity alpha * f_temp * f_dir
@@ -110,11 +110,13 @@ typedef struct sdgs_projected {
  *   tile_keys  [capacity] uint32 tile id of each sorted instance, or NULL to skip writing it
  *   point_list [capacity] uint32 Gaussian id of each sorted instance; instances are ordered by
  *              (tile id, float32 depth, Gaussian id)
- *   ranges     [tiles_x * tiles_y][2] uint32 [start, end) of each tile in the sorted lists
+ *   ranges     [tiles_x * tiles_y][2] uint32 [start, end) of each tile in the sorted lists;
+ *              (0, 0) for a tile without instances
  *   num_instances  device int64: total instance count K written by the call.  It may exceed
- *              capacity; then only sorted positions below capacity are stored, ranges are clipped
- *              to capacity, and SDGS_ERR_OVERFLOW is reported when the call synchronises.
- *   capacity   number of entries allocated in tile_keys / point_list (< 2^31) */
+ *              capacity; then the lists hold `capacity` of the instances (those of the nearest
+ *              Gaussians), still sorted by (tile, depth, id) and covered by the ranges, and
+ *              SDGS_ERR_OVERFLOW is reported when the call synchronises.
+ *   capacity   number of entries allocated in tile_keys / point_list (< 2^30) */
 typedef struct sdgs_bins {
   uint32_t* tile_keys;
   uint32_t* point_list;
@@ -152,12 +154,21 @@ int sdgs_slice_project(const sdgs_scene* scene, const sdgs_view* view, const sdg
 int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
                             size_t* bytes);
 
-/* Tile binning.  Sorts Gaussians by float32 depth (stable, so equal depths keep ascending id),
- * emits one instance per tile of each visible Gaussian's rectangle in that order, stably sorts the
+/* Tile binning (Sec. 3.3 and the 3DGS tile rasteriser it builds on).  Sorts the Gaussians by
+ * float32 depth (stable, so equal depths keep ascending id), emits in that order one instance per
+ * tile of each visible Gaussian's rectangle that the Gaussian may reach, stably sorts the
  * instances by tile id, and writes the per-tile ranges: the result is the stable sort of the
- * 64-bit keys tile_id << 32 | bits(depth).  `workspace` is device memory of at least
- * sdgs_bin_workspace_size() bytes, 256-byte aligned.  Images up to 56,000 tiles are supported
- * (e.g. 3840 x 3840); larger ones return SDGS_ERR_INVALID_ARG.
+ * 64-bit keys tile_id << 32 | bits(depth) over the kept instances.
+ * A tile of the rectangle is dropped only when, with conic (a, b, c) and opacity alpha, every
+ * pixel centre of the tile has alpha exp(-q/2) < 1/255 by a margin far above float32 error:
+ *   q_min = min of a dx^2 + 2 b dx dy + c dy^2 over the tile's pixel-centre box (0 if the mean
+ *           lies inside; else the least of the one or two edges facing the mean, each at its
+ *           clamped stationary point dy = clamp((-b / c) dx) or dx = clamp((-b / a) dy)),
+ *   thr   = 512 (sqrt^8(255 alpha) - 1),  m = 1e-4 + 2^-18 (ac + b^2) / (ac - b^2),
+ *   drop iff ac - b^2 > 0 and m < 1/2 and q_min (1 - m) > thr + 1e-3,
+ * every operation a correctly rounded float32 operation in that order, so the kept set is a
+ * function of the float32 inputs alone.  Such tiles would composite to the same image.
+ * `workspace` is device memory of at least sdgs_bin_workspace_size() bytes, 256-byte aligned.
  * If num_instances_host is not NULL the call synchronises the stream, stores K there and returns
  * SDGS_ERR_OVERFLOW when K > capacity; otherwise it never synchronises (K stays on the device and
  * an overflow only truncates the lists).
@@ -234,12 +245,16 @@ typedef struct sdgs_server_cfg {
   int32_t max_slots;        /* requests in flight at once (1..64) */
   int32_t queue_capacity;   /* queued requests beyond which submit returns SDGS_ERR_BUSY */
   int32_t device;           /* CUDA device ordinal */
+  int32_t batch_window_us;  /* 0: admit requests as soon as a slot is free; > 0: while fewer
+                               requests wait than there are free slots, hold admission until the
+                               oldest has waited this long, so that they share one batched launch */
 } sdgs_server_cfg;
 
 typedef struct sdgs_server_stats {
   uint64_t submitted, completed, failed, retried;
   uint64_t batches;          /* batched slicing launches */
   uint64_t max_batch;        /* largest number of requests in one batched launch */
+  uint64_t max_inflight;     /* most requests on the device at the same time */
   size_t bytes_allocated;    /* device memory held by the slots */
 } sdgs_server_stats;
 

@@ -7,7 +7,7 @@ there is no CPU fallback built on it.  It shares no code with the CUDA path:
 inputs come from the seeded generator in `synth/`, and every step below is
 written from the paper's equations (Sec. 4.2, Eqs. cond_mean / cond_cov /
 temp_mod / dir_mod, Algorithm 1 steps 3-6) and the 3DGS projection and
-compositing rules the paper adopts (Sec. 4.3), in float64 with plain PyTorch
+compositing rules the paper adopts (Sec. 4.4), in float64 with plain PyTorch
 CPU operations.  Gradients are PyTorch autograd through this same forward.
 
 Modules:

@@ -1,7 +1,7 @@
 """Front-to-back alpha compositing of depth-sorted 2D Gaussians (oracle, float64).
 
-The paper aggregates the projected Gaussians "depth-aware, opacity-blended" with the 3DGS
-differentiable rasteriser (Sec. 4.3).  The rules, fixed here as readings of that rasteriser:
+The paper blends the projected Gaussians in depth order by opacity, with the 3DGS differentiable
+rasteriser (Sec. 4.4).  The rules, fixed here as readings of that rasteriser:
   * a Gaussian is considered at a pixel iff the pixel's 16x16 tile lies in its tile rectangle;
     candidates are visited in ascending (depth, id) order;
   * power = -1/2 (a dx^2 + c dy^2) - b dx dy with (dx, dy) = pixel centre - mean, conic [[a,b],[b,c]];

@@ -1,7 +1,7 @@
 """Perspective (EWA) projection of conditional 3D Gaussians (oracle, float64).
 
 The paper converts each sliced Gaussian to the 3DGS format and projects it with the
-standard 3DGS perspective projection (Sec. 4.3, rendering pipeline).  The paper does
+standard 3DGS perspective projection (Sec. 4.4, rendering pipeline).  The paper does
 not restate those rules, so this module fixes them as the following readings:
   * OpenCV pinhole: p_cam = R mu + t with the world->camera matrix [R | t]; depth z = p_cam.z;
     image position u = fx x/z + cx, v = fy y/z + cy, pixel (i, j) centred at (i + 1/2, j + 1/2).

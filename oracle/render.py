@@ -1,6 +1,6 @@
 """The whole 7DGS render path in float64, plus sampled pixels and autograd gradients (oracle).
 
-Pipeline (Sec. 4.3 "the rendering pipeline remains fully compatible with 3DGS"):
+Pipeline (Sec. 4.4: after slicing, rendering is the unchanged 3DGS pipeline):
   slicing (Algorithm 1 steps 3-6) -> projection + SH colour -> tile binning by (tile, depth) ->
   front-to-back compositing.  SH colour is evaluated at the unit direction from the camera
   centre to mu_cond.  Gradients of any scalar of the image are PyTorch autograd through this
@@ -64,10 +64,17 @@ def pixel_centres(cam, tile: int) -> tuple[torch.Tensor, torch.Tensor]:
     return pix, rc
 
 
+def cull_inputs(mean2d, conic, alpha):
+    """The float32 screen-space values the tile-reachability rule of binning reads."""
+    f = lambda x: x.detach().numpy().astype(np.float32)
+    return (f(mean2d), f(conic), f(alpha))
+
+
 def composite_all(mean2d, conic, alpha, rgb, depth, rect, cam, bg, tiles=None) -> dict:
     """Composite every tile (or the listed ones) of the image."""
     num_tiles = cam.tiles_x * cam.tiles_y
-    lists = binning.tile_lists(depth.detach().numpy(), rect.numpy(), cam.tiles_x, num_tiles)
+    lists = binning.tile_lists(depth.detach().numpy(), rect.numpy(), cam.tiles_x, num_tiles,
+                               cull=cull_inputs(mean2d, conic, alpha))
     H, W = cam.height, cam.width
     colors, Ts, ncs, margins, rcs = [], [], [], [], []
     for tile in (range(num_tiles) if tiles is None else tiles):
@@ -125,6 +132,8 @@ def render_pixels(g: dict, cam, pixels: np.ndarray) -> dict:
         tx, ty = int(tile % cam.tiles_x), int(tile // cam.tiles_x)
         inside = (rect[:, 0] <= tx) & (tx < rect[:, 2]) & (rect[:, 1] <= ty) & (ty < rect[:, 3])
         ids = torch.nonzero(inside).reshape(-1)
+        m2, co, al = cull_inputs(g["mean2d"][ids], g["conic"][ids], g["alpha_cond"][ids])
+        ids = ids[torch.as_tensor(binning.tile_reachable(m2, co, al, tx, ty))]
         order = np.lexsort((ids.numpy(), depth[ids].numpy()))
         cand = ids[torch.as_tensor(order, dtype=torch.int64)]
         pix = torch.as_tensor(pixels[sel][:, ::-1].copy(), dtype=F64) + 0.5

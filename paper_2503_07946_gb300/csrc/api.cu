@@ -55,6 +55,10 @@ static int check_view(const sdgs_view* v) {
     set_error("image size %d x %d out of range", v->width, v->height);
     return SDGS_ERR_INVALID_ARG;
   }
+  if ((int64_t)((v->width + kTile - 1) / kTile) * ((v->height + kTile - 1) / kTile) > ((int64_t)1 << 26)) {
+    set_error("image of %d x %d pixels has more than 2^26 tiles", v->width, v->height);
+    return SDGS_ERR_INVALID_ARG;
+  }
   if (!(v->fx > 0.f) || !(v->fy > 0.f) || !std::isfinite(v->fx) || !std::isfinite(v->fy) ||
       !std::isfinite(v->cx) || !std::isfinite(v->cy) || !(v->near_plane >= 0.f)) {
     set_error("bad intrinsics or near plane");
@@ -71,7 +75,7 @@ static int check_view(const sdgs_view* v) {
 
 static int check_projected(const sdgs_projected* p) {
   if (p == nullptr) { set_error("projected is NULL"); return SDGS_ERR_INVALID_ARG; }
-  if (p->n < 0 || p->n >= (int64_t(1) << 31)) { set_error("projected n out of range"); return SDGS_ERR_INVALID_ARG; }
+  if (p->n < 0 || p->n >= (int64_t(1) << 30)) { set_error("projected n out of range [0, 2^30)"); return SDGS_ERR_INVALID_ARG; }
   if (p->n > 0) {
     if (!p->mean2d || !p->conic_opacity || !p->rgb || !p->depth || !p->rect || !p->radius) {
       set_error("projected array is NULL");
@@ -88,7 +92,7 @@ static int check_projected(const sdgs_projected* p) {
 
 static int check_bins(const sdgs_bins* b) {
   if (b == nullptr) { set_error("bins is NULL"); return SDGS_ERR_INVALID_ARG; }
-  if (b->capacity < 0 || b->capacity >= (int64_t(1) << 31)) { set_error("bins capacity out of range [0, 2^31)"); return SDGS_ERR_INVALID_ARG; }
+  if (b->capacity < 0 || b->capacity >= (int64_t(1) << 30)) { set_error("bins capacity out of range [0, 2^30)"); return SDGS_ERR_INVALID_ARG; }
   if (!b->ranges || !b->num_instances || (b->capacity > 0 && !b->point_list)) {
     set_error("bins array is NULL");
     return SDGS_ERR_INVALID_ARG;
@@ -125,7 +129,7 @@ int sdgs_slice_project(const sdgs_scene* scene, const sdgs_view* view, const sdg
 
 int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height, size_t* bytes) {
   g_error[0] = 0;
-  if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 31) || capacity < 0 || capacity >= (int64_t(1) << 31) ||
+  if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 30) || capacity < 0 || capacity >= (int64_t(1) << 30) ||
       width <= 0 || height <= 0 || width > 65535 * kTile || height > 65535 * kTile) {
     set_error("bad arguments to sdgs_bin_workspace_size");
     return SDGS_ERR_INVALID_ARG;
@@ -134,6 +138,32 @@ int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t 
   return SDGS_OK;
 }
 
+}  // extern "C"
+
+// With a host count requested: synchronise, then report a sort that gave up waiting (never
+// expected: every wait is on a block that is already running) or an overflow.
+static int finish_bin_sort(const BinPlan& plan, const char* ws, const sdgs_bins* out, int64_t* num_instances_host,
+                           cudaStream_t st) {
+  if (num_instances_host == nullptr) return SDGS_OK;
+  uint32_t err = 0;
+  SDGS_TRY(cuda_status(cudaMemcpyAsync(num_instances_host, out->num_instances, sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, st), "copy instance count"));
+  SDGS_TRY(cuda_status(cudaMemcpyAsync(&err, ws + plan.off_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                       "copy sort status"));
+  SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "bin_sort synchronize"));
+  if (err != 0) {
+    set_error("binning sort: a look-back wait gave up; the lists are invalid");
+    return SDGS_ERR_CUDA;
+  }
+  if (*num_instances_host > out->capacity) {
+    set_error("%lld instances exceed capacity %lld", (long long)*num_instances_host, (long long)out->capacity);
+    return SDGS_ERR_OVERFLOW;
+  }
+  return SDGS_OK;
+}
+
+extern "C" {
+
 int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
                   size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                   void* stream) {
@@ -141,11 +171,6 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
   SDGS_TRY(check_projected(proj));
   SDGS_TRY(check_view(view));
   SDGS_TRY(check_bins(out));
-  if (bin_smem_bytes(view->width, view->height) > kMaxBinSmem) {
-    set_error("image of %d x %d tiles exceeds the binning limit (%zu bytes of tile counters)",
-              (view->width + kTile - 1) / kTile, (view->height + kTile - 1) / kTile, kMaxBinSmem);
-    return SDGS_ERR_INVALID_ARG;
-  }
   const BinPlan plan = plan_bins(proj->n, out->capacity, view->width, view->height);
   if (workspace == nullptr || workspace_bytes < plan.total || !aligned(workspace, 256)) {
     set_error("workspace needs %zu bytes, 256-byte aligned (got %zu)", plan.total, workspace_bytes);
@@ -153,16 +178,7 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
   }
   cudaStream_t st = (cudaStream_t)stream;
   SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st), "bin_sort launch"));
-  if (num_instances_host != nullptr) {
-    SDGS_TRY(cuda_status(cudaMemcpyAsync(num_instances_host, out->num_instances, sizeof(int64_t),
-                                         cudaMemcpyDeviceToHost, st), "copy instance count"));
-    SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "bin_sort synchronize"));
-    if (*num_instances_host > out->capacity) {
-      set_error("%lld instances exceed capacity %lld", (long long)*num_instances_host, (long long)out->capacity);
-      return SDGS_ERR_OVERFLOW;
-    }
-  }
-  return SDGS_OK;
+  return finish_bin_sort(plan, (const char*)workspace, out, num_instances_host, st);
 }
 
 }  // extern "C"
@@ -204,11 +220,6 @@ int sdgs_bin_sort_static(const sdgs_projected* proj, const sdgs_view* view, cons
   SDGS_TRY(check_projected(proj));
   SDGS_TRY(check_view(view));
   SDGS_TRY(check_bins(out));
-  if (bin_smem_bytes(view->width, view->height) > kMaxBinSmem) {
-    set_error("image of %d x %d tiles exceeds the binning limit", (view->width + kTile - 1) / kTile,
-              (view->height + kTile - 1) / kTile);
-    return SDGS_ERR_INVALID_ARG;
-  }
   const BinPlan plan = plan_bins(proj->n, out->capacity, view->width, view->height);
   if (plan.total > SDGS_STATIC_BIN_SCRATCH_BYTES) {
     set_error("binning %lld Gaussians into %d tiles needs %zu bytes of scratch; the built-in scratch "
@@ -220,16 +231,7 @@ int sdgs_bin_sort_static(const sdgs_projected* proj, const sdgs_view* view, cons
   SDGS_TRY(static_scratch(&ws));
   cudaStream_t st = (cudaStream_t)stream;
   SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)ws, *out, st), "bin_sort launch"));
-  if (num_instances_host != nullptr) {
-    SDGS_TRY(cuda_status(cudaMemcpyAsync(num_instances_host, out->num_instances, sizeof(int64_t),
-                                         cudaMemcpyDeviceToHost, st), "copy instance count"));
-    SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "bin_sort synchronize"));
-    if (*num_instances_host > out->capacity) {
-      set_error("%lld instances exceed capacity %lld", (long long)*num_instances_host, (long long)out->capacity);
-      return SDGS_ERR_OVERFLOW;
-    }
-  }
-  return SDGS_OK;
+  return finish_bin_sort(plan, (const char*)ws, out, num_instances_host, st);
 }
 
 int sdgs_render_fwd(const sdgs_projected* proj, const sdgs_bins* bins, const sdgs_view* view,

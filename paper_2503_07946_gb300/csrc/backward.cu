@@ -73,17 +73,14 @@ __device__ __forceinline__ bool unblend(BwdPixel& px, const float4& co, const fl
 }
 
 // Back-to-front replay per 16x16 tile, 128 threads with two pixels each (rows r and r + 8).
-// The tile's list is staged from the back in batches of 128 with the same conservative tile cull
-// as the forward (culled Gaussians have alpha < 1/255 at every pixel, so the forward skipped them
-// everywhere); each Gaussian's gradient is summed over the thread's pixels, then over the warp,
-// and added to the per-Gaussian buffer with one atomic per component and warp.
+// The tile's list is staged from the back in batches of 128; each Gaussian's gradient is summed
+// over the thread's pixels, then over the warp, and added to the per-Gaussian buffer with one
+// atomic per component and warp.
 __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArgs a) {
   __shared__ float2 s_xy[kThreads];
   __shared__ float4 s_co[kThreads];
   __shared__ float4 s_rgb[kThreads];
   __shared__ uint32_t s_id[kThreads];
-  __shared__ uint32_t s_pos[kThreads];
-  __shared__ int s_warp[kThreads / 32];
   __shared__ uint32_t s_max;
 
   const int tile = blockIdx.x;
@@ -93,8 +90,6 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
   const int py[2] = {ty * kTile + (int)(threadIdx.x / kTile), ty * kTile + (int)(threadIdx.x / kTile) + kTile / 2};
   const float fx = (float)px + 0.5f;
   const float fy[2] = {(float)py[0] + 0.5f, (float)py[1] + 0.5f};
-  const float bx0 = (float)(tx * kTile) + 0.5f, bx1 = bx0 + (float)(kTile - 1);
-  const float by0 = (float)(ty * kTile) + 0.5f, by1 = by0 + (float)(kTile - 1);
   const uint2 range = a.ranges[tile];
 
   BwdPixel pxs[2];
@@ -124,41 +119,21 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
     const int lo = max(0, top - kThreads);
     const int j = lo + threadIdx.x;
     __syncthreads();  // the previous batch is fully consumed
-    bool keep = false;
-    uint32_t gid = 0;
-    float2 xy;
-    float4 co;
     if (j < top) {
-      gid = a.point_list[range.x + j];
-      xy = a.mean2d[gid];
-      co = a.conic_opacity[gid];
-      keep = !splat_misses_box(co, xy, bx0, bx1, by0, by1);
+      const uint32_t gid = a.point_list[range.x + j];
+      s_xy[threadIdx.x] = a.mean2d[gid];
+      s_co[threadIdx.x] = a.conic_opacity[gid];
+      s_rgb[threadIdx.x] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
+      s_id[threadIdx.x] = gid;
     }
-    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) s_warp[warp] = __popc(ballot);
-    __syncthreads();
-    int off = 0, cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-      const int c = s_warp[w];
-      off += (w < warp) ? c : 0;
-      cnt += c;
-    }
-    if (keep) {
-      const int idx = off + __popc(ballot & ((1u << lane) - 1u));
-      s_xy[idx] = xy;
-      s_co[idx] = co;
-      s_rgb[idx] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
-      s_id[idx] = gid;
-      s_pos[idx] = (uint32_t)j;
-    }
+    const int cnt = top - lo;
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
       const float2 m = s_xy[k];
       const float4 co_k = s_co[k];
       const float4 q = scaled_conic(co_k);
       const float4 c = s_rgb[k];
-      const uint32_t pos = s_pos[k];
+      const uint32_t pos = (uint32_t)(lo + k);
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const float dx = fx - m.x;
       const bool b0 = unblend(pxs[0], co_k, q, c, dx, fy[0] - m.y, pos, g);

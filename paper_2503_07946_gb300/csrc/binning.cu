@@ -1,22 +1,25 @@
 // Tile binning: the stable sort of the (tile << 32 | float32 depth bits) instance keys as an LSD
-// sort in two digits -- depth first, then tile -- arranged so that neither pass touches more
-// data than it must.
+// sort in two digits, depth first, arranged so that neither digit's passes touch more data than
+// they must.
 //
 // Depth digit: every instance of one Gaussian carries that Gaussian's depth, and instances are
 // emitted in the order of the Gaussians.  So the depth passes of an LSD sort over the K instances
 // give the same order as a stable radix sort of the n Gaussians by depth (ties keep ascending id)
 // followed by emission in that order.  That sort runs over n keys, not K.
 //
-// Tile digit: one stable counting pass over the depth-ordered Gaussians that writes every
-// instance exactly once, straight into its tile's list (see the kernels below).
+// Tile digit: the instances, emitted in depth order, are radix-sorted stably by tile id
+// (ceil(log2 tiles) bits, 8 per pass).  Instances exist only for the tiles of a Gaussian's
+// rectangle that it may reach (tile_reach.cuh).
 //
-// The depth radix passes are reduce-then-scan with no inter-block waiting: an upsweep writes a
-// per-block digit histogram (digit-major), a device-wide exclusive scan turns it into block
-// offsets, and a downsweep ranks the block's keys stably (warp match + per-warp counters) and
-// scatters them through shared memory so that runs of one digit are written contiguously.
+// Each radix pass is reduce-then-scan with no inter-block waiting: an upsweep writes a per-block
+// digit histogram, a device-wide exclusive scan (or, for few blocks, each downsweep block itself)
+// turns it into block offsets, and a downsweep ranks the block's keys stably (warp match +
+// per-warp counters) and scatters them through shared memory so that runs of one digit are
+// written contiguously.
 #include <algorithm>
 
 #include "common.cuh"
+#include "tile_reach.cuh"
 
 namespace sdgs {
 
@@ -156,70 +159,103 @@ cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partia
 // Radix pass kernels (8-bit digit at `shift`).
 // ------------------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kRadixThreads)
-radix_upsweep_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t n_static,
-                     int64_t cap, int shift, uint32_t* __restrict__ hist, int64_t nblocks,
-                     bool block_major) {
-  __shared__ uint32_t s_hist[kRadixWarps][kBins];
-  for (int i = threadIdx.x; i < kRadixWarps * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
-  __syncthreads();
-  const int64_t n = element_count(nptr, n_static, cap);
-  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (base < n) {
-    const int64_t wbase = base + (int64_t)warp * 32 * kRadixItems;
-#pragma unroll 4
-    for (int r = 0; r < kRadixItems; ++r) {
-      const int64_t idx = wbase + r * 32 + lane;
-      const bool valid = idx < n;
-      const uint32_t d = valid ? ((keys[idx] >> shift) & 0xffu) : 0x100u;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (valid && lane == __ffs(peers) - 1) s_hist[warp][d] += __popc(peers);
-      __syncwarp();
+// Lanes of the warp whose digit equals this lane's (d has `width` bits; lanes with !valid are in
+// no lane's set): one ballot per digit bit.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid, int width) {
+  unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if (b < width) {  // uniform over the warp
+      const bool bit = (d >> b) & 1u;
+      const unsigned m = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? m : ~m;
     }
   }
-  __syncthreads();
-  uint32_t tot = 0;
-#pragma unroll
-  for (int w = 0; w < kRadixWarps; ++w) tot += s_hist[w][threadIdx.x];
-  if (block_major)
-    hist[(int64_t)blockIdx.x * kBins + threadIdx.x] = tot;
-  else
-    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = tot;
+  return peers;
 }
 
+// ------------------------------------------------------------------------------------------
+// LSD radix sort of (key, value) pairs: one histogram kernel for every digit, then one kernel per
+// digit.  A sort block ranks its tile of keys stably (per-warp digit counters; lanes with equal
+// digits found by match or by one ballot per digit bit), finds the keys of each digit in all
+// earlier tiles by a decoupled look-back over the per-tile status words, and writes each digit's
+// run of keys contiguously through shared memory.  Tiles are numbered by an atomic ticket taken
+// when a block starts, so a block only ever waits on blocks that are already running; every wait
+// is bounded (kLookbackSpins), after which the block flags an error and carries on.
+// ------------------------------------------------------------------------------------------
+
+constexpr uint32_t kStatusAggregate = 1u << 30;  // this tile's own count of the digit
+constexpr uint32_t kStatusInclusive = 2u << 30;  // count of the digit in tiles 0 .. this one
+constexpr uint32_t kStatusCount = (1u << 30) - 1u;
+constexpr int kLookbackSpins = 1 << 20;
+constexpr int kLookbackWindow = 8;
+constexpr int kMaxPasses = 4;
+
 __global__ void __launch_bounds__(kRadixThreads)
-radix_downsweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                       uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                       const int64_t* nptr, int64_t n_static, int64_t cap, int shift,
-                       const uint32_t* __restrict__ hist, int64_t nblocks, bool block_major) {
-  __shared__ uint32_t s_keys[kRadixTile];
-  __shared__ uint32_t s_vals[kRadixTile];
+digit_hist_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t n_static, int64_t cap,
+                  int passes, int width, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[kMaxPasses][kBins];
+  for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = element_count(nptr, n_static, cap);
+  const uint32_t dmask = (1u << width) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * kRadixThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kRadixThreads) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (p * width)) & dmask], 1u);
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t c = s_hist[p][threadIdx.x];
+    if (c) atomicAdd(&hist[p * kBins + threadIdx.x], c);
+  }
+}
+
+__device__ __forceinline__ uint32_t load_status(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+__device__ __forceinline__ void store_status(uint32_t* p, uint32_t v) {
+  *reinterpret_cast<volatile uint32_t*>(p) = v;
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kRadixThreads, 4)
+onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* nptr,
+                int64_t n_static, int64_t cap, int shift, int width, const uint32_t* __restrict__ digit_hist,
+                uint32_t* status, uint32_t* ticket, uint32_t* err) {
+  constexpr int TILE = kRadixThreads * ITEMS;
+  __shared__ uint32_t s_keys[TILE];
+  __shared__ uint32_t s_vals[TILE];
   __shared__ uint32_t s_whist[kRadixWarps][kBins];
   __shared__ uint32_t s_dstart[kBins];
   __shared__ uint32_t s_gbase[kBins];
-  const int64_t n = element_count(nptr, n_static, cap);
-  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  if (base >= n) return;
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   for (int i = threadIdx.x; i < kRadixWarps * kBins; i += kRadixThreads) (&s_whist[0][0])[i] = 0;
   __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t n = element_count(nptr, n_static, cap);
+  const int64_t base = tile * TILE;
+  if (base >= n) return;  // so do all later tiles: nobody waits on this one
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  const int64_t wbase = base + (int64_t)warp * 32 * kRadixItems;
-  uint32_t key[kRadixItems], val[kRadixItems], rank[kRadixItems];
+  const uint32_t dmask = (1u << width) - 1u;
+  const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
+  uint32_t key[ITEMS], rank[ITEMS];
 #pragma unroll
-  for (int r = 0; r < kRadixItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     const int64_t idx = wbase + r * 32 + lane;
-    const bool valid = idx < n;
-    key[r] = valid ? keys_in[idx] : 0u;
-    val[r] = valid ? vals_in[idx] : 0u;
+    key[r] = idx < n ? keys_in[idx] : 0u;
   }
 #pragma unroll
-  for (int r = 0; r < kRadixItems; ++r) {
+  for (int r = 0; r < ITEMS; ++r) {
     const bool valid = wbase + r * 32 + lane < n;
-    const uint32_t d = valid ? ((key[r] >> shift) & 0xffu) : 0x100u;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t d = (key[r] >> shift) & dmask;
+    const unsigned peers = width >= 8 ? (__match_any_sync(0xffffffffu, valid ? d : 0x100u) &
+                                         __ballot_sync(0xffffffffu, valid))
+                                      : digit_peers(d, valid, width);
     const uint32_t before = valid ? s_whist[warp][d] : 0u;
     __syncwarp();
     if (valid && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
@@ -229,72 +265,185 @@ radix_downsweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __r
   __syncthreads();
   {
     const int dg = threadIdx.x;
-    uint32_t run = 0;
+    uint32_t run = 0;  // this tile's keys with digit dg
 #pragma unroll
     for (int w = 0; w < kRadixWarps; ++w) {
       const uint32_t c = s_whist[w][dg];
       s_whist[w][dg] = run;
       run += c;
     }
+    uint32_t* mine = status + tile * kBins + dg;
+    store_status(mine, (tile == 0 ? kStatusInclusive : kStatusAggregate) | run);
+    uint32_t before = 0;  // keys with digit dg in tiles 0 .. tile - 1
+    int spins = 0;
+    // Wait for the nearest unresolved tile (one load per poll, with a short sleep), then take up
+    // to kLookbackWindow - 1 further tiles from one round of parallel loads, nearest first, until
+    // an inclusive count or a tile that has published nothing yet.
+    for (int64_t j = tile - 1; j >= 0;) {
+      const uint32_t near = load_status(status + j * kBins + dg);
+      if ((near & ~kStatusCount) == 0u) {
+        if (++spins > kLookbackSpins) {
+          atomicOr(err, 1u);
+          break;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      before += near & kStatusCount;
+      if (near & kStatusInclusive) break;
+      --j;
+      uint32_t st[kLookbackWindow - 1];
+#pragma unroll
+      for (int w = 0; w < kLookbackWindow - 1; ++w) st[w] = j - w >= 0 ? load_status(status + (j - w) * kBins + dg) : 0u;
+      bool done = false, stop = false;
+#pragma unroll
+      for (int w = 0; w < kLookbackWindow - 1; ++w) {
+        if (done || stop || j < 0) continue;
+        if ((st[w] & ~kStatusCount) == 0u) {
+          stop = true;  // not published yet: poll it next
+          continue;
+        }
+        before += st[w] & kStatusCount;
+        if (st[w] & kStatusInclusive) done = true;
+        else --j;
+      }
+      if (done) break;
+    }
+    if (tile > 0) store_status(mine, kStatusInclusive | (before + run));
     uint32_t tot;
     const uint32_t incl = block_inclusive_scan<uint32_t, kRadixThreads>(run, &tot);
     s_dstart[dg] = incl - run;
-    if (block_major) {
-      // raw per-block counts: offset = keys of smaller digits anywhere + this digit in earlier blocks
-      uint32_t before = 0, all = 0;
-      for (int64_t b = 0; b < nblocks; ++b) {
-        const uint32_t c = hist[b * kBins + dg];
-        all += c;
-        before += (b < (int64_t)blockIdx.x) ? c : 0u;
-      }
-      uint32_t dtot;
-      const uint32_t dincl = block_inclusive_scan<uint32_t, kRadixThreads>(all, &dtot);
-      s_gbase[dg] = dincl - all + before;
-    } else {
-      s_gbase[dg] = hist[(int64_t)dg * nblocks + blockIdx.x];
-    }
+    const uint32_t all = digit_hist[dg];
+    const uint32_t gincl = block_inclusive_scan<uint32_t, kRadixThreads>(all, &tot);
+    s_gbase[dg] = gincl - all + before;
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kRadixItems; ++r) {
-    if (wbase + r * 32 + lane < n) {
-      const uint32_t d = (key[r] >> shift) & 0xffu;
+  for (int r = 0; r < ITEMS; ++r) {
+    const int64_t idx = wbase + r * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (key[r] >> shift) & dmask;
       const uint32_t pos = s_dstart[d] + s_whist[warp][d] + rank[r];
       s_keys[pos] = key[r];
-      s_vals[pos] = val[r];
+      s_vals[pos] = vals_in[idx];
     }
   }
   __syncthreads();
-  const int cnt = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
+  const int cnt = (int)((n - base) < TILE ? (n - base) : TILE);
   for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
     const uint32_t k = s_keys[i];
-    const uint32_t d = (k >> shift) & 0xffu;
+    const uint32_t d = (k >> shift) & dmask;
     const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
     keys_out[g] = k;
     vals_out[g] = s_vals[i];
   }
 }
 
-// Sorts (keys, vals) by bits [0, bits) in passes of 8 bits, ping-ponging between buffers 0 and 1;
-// returns the index of the buffer that holds the result.
-// Up to this many blocks, each downsweep block derives its offsets from the raw per-block
-// histograms itself (two kernels per pass); beyond it a device-wide scan runs between them.
-constexpr int64_t kFusedScanMaxBlocks = 128;
+int radix_digit_width(int bits) {
+  const int passes = (bits + 7) / 8;
+  return passes > 0 ? (bits + passes - 1) / passes : 8;
+}
 
+int radix_pass_count(int bits) {
+  int k = 0;
+  for (int shift = 0; shift < bits; shift += radix_digit_width(bits)) ++k;
+  return k;
+}
+
+// Keys per sort block for `cap` slots: the largest tile (16, 8 or 4 keys per thread) that still
+// gives two blocks per SM, so that small sorts are not latency-bound on a few blocks.
+int sort_items(int64_t cap) {
+  const int64_t want = 2 * 152;
+  if ((cap + 16 * kRadixThreads - 1) / (16 * kRadixThreads) >= want) return 16;
+  if ((cap + 8 * kRadixThreads - 1) / (8 * kRadixThreads) >= want) return 8;
+  return 4;
+}
+
+int64_t sort_blocks(int64_t cap) {
+  const int64_t tile = (int64_t)sort_items(cap) * kRadixThreads;
+  return (cap + tile - 1) / tile;
+}
+
+// Scratch of one sort: per-digit histograms, tickets, status words.
+size_t sort_scratch_bytes(int64_t cap, int bits) {
+  return sizeof(uint32_t) * ((size_t)kMaxPasses * kBins + kMaxPasses +
+                             (size_t)radix_pass_count(bits) * sort_blocks(cap) * kBins);
+}
+
+// Sorts (keys, vals) by bits [0, bits) in ceil(bits / 8) passes of equal digit width (at most 8
+// bits: fewer, longer digit runs per block make the writes more contiguous), ping-ponging between
+// buffers 0 and 1; returns the index of the buffer that holds the result.  The element count is
+// *nptr (clipped to cap) when nptr is not NULL, else n_static; launches are sized by cap.
+// `scratch` holds sort_scratch_bytes(cap, bits); `err` is set if a look-back gave up.
+// Zeroes a sort's scratch (histograms, tickets, status words).
+cudaError_t sort_clear(uint32_t* scratch, int64_t cap, int bits, cudaStream_t st) {
+  return cudaMemsetAsync(scratch, 0, sort_scratch_bytes(cap, bits), st);
+}
+
+// Adds the digits of every pass of the warp's valid keys to a block's shared histograms
+// (s_hist[pass][digit]) with one add per run of adjacent valid lanes with equal digits (runs are
+// common: the top digit of nearby depths, the high digit of a row of tiles).  All 32 lanes call.
+__device__ __forceinline__ void count_digits(uint32_t (*s_hist)[kBins], uint32_t key, bool valid, int passes,
+                                             int width) {
+  const uint32_t dmask = (1u << width) - 1u;
+  const unsigned live = __ballot_sync(0xffffffffu, valid);
+  if (live == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const bool prev_live = lane > 0 && ((live >> (lane - 1)) & 1u);
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t d = (key >> (p * width)) & dmask;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, d, 1);
+    const bool head = valid && !(prev_live && prev == d);
+    const unsigned ends = __ballot_sync(0xffffffffu, head) | ~live;  // a run stops at these lanes
+    if (head) {
+      const unsigned after = lane < 31 ? (ends >> (lane + 1)) : 0u;
+      const uint32_t len = after ? (uint32_t)__ffs(after) : (uint32_t)(32 - lane);
+      atomicAdd(&s_hist[p][d], len);
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_digits(const uint32_t (*s_hist)[kBins], int passes, uint32_t* hist) {
+  for (int i = threadIdx.x; i < passes * kBins; i += blockDim.x) {
+    const uint32_t c = s_hist[i / kBins][i % kBins];
+    if (c) atomicAdd(&hist[i], c);
+  }
+}
+
+// With hist_ready, the caller has cleared the scratch (sort_clear) and accumulated the digit
+// histograms of all keys into its first kMaxPasses * kBins words while producing them.
 int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_t n_static,
-               int64_t cap, int bits, uint32_t* hist, uint64_t* partials, cudaStream_t st) {
-  const int64_t nblocks = (cap + kRadixTile - 1) / kRadixTile;
+               int64_t cap, int bits, uint32_t* scratch, uint32_t* err, bool hist_ready, cudaStream_t st) {
   int cur = 0;
-  if (nblocks == 0) return cur;
-  const bool fused = nblocks <= kFusedScanMaxBlocks;
-  for (int shift = 0; shift < bits; shift += 8) {
-    radix_upsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(keys[cur], nptr, n_static,
-                                                                        cap, shift, hist, nblocks, fused);
-    if (!fused)
-      exclusive_scan<uint32_t, uint32_t>(hist, (int64_t)kBins * nblocks, hist, partials, nullptr, st);
-    radix_downsweep_kernel<<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
-        keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, hist,
-        nblocks, fused);
+  if (cap <= 0 || bits <= 0) return cur;
+  const int width = radix_digit_width(bits);
+  const int passes = radix_pass_count(bits);
+  const int items = sort_items(cap);
+  const int64_t nblocks = sort_blocks(cap);
+  uint32_t* hist = scratch;
+  uint32_t* tickets = hist + kMaxPasses * kBins;
+  uint32_t* status = tickets + kMaxPasses;
+  if (!hist_ready) {
+    sort_clear(scratch, cap, bits, st);
+    const int64_t hist_blocks = std::min<int64_t>((cap + kRadixThreads - 1) / kRadixThreads, 4 * 152);
+    digit_hist_kernel<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], nptr, n_static, cap, passes,
+                                                                       width, hist);
+  }
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* stp = status + (size_t)p * nblocks * kBins;
+    const int shift = p * width;
+    if (items == 16)
+      onesweep_kernel<16><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, width,
+          hist + p * kBins, stp, tickets + p, err);
+    else if (items == 8)
+      onesweep_kernel<8><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, width,
+          hist + p * kBins, stp, tickets + p, err);
+    else
+      onesweep_kernel<4><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
+          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, width,
+          hist + p * kBins, stp, tickets + p, err);
     cur ^= 1;
   }
   return cur;
@@ -304,28 +453,36 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
 // Binning-specific kernels.
 // ------------------------------------------------------------------------------------------
 
-__global__ void depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ rect,
-                                  int64_t n, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const ushort4 r = rect[i];
-  const bool vis = r.z > r.x && r.w > r.y;
-  keys[i] = vis ? __float_as_uint(depth[i]) : 0xffffffffu;  // visible depths are positive
-  vals[i] = (uint32_t)i;
+// Depth keys of the Gaussians (culled ones last) and their digit histograms for the depth sort.
+__global__ void __launch_bounds__(kRadixThreads)
+depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ rect, int64_t n,
+                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[kMaxPasses][kBins];
+  for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kRadixThreads + threadIdx.x;
+  uint32_t k = 0;
+  if (i < n) {
+    const ushort4 r = rect[i];
+    const bool vis = r.z > r.x && r.w > r.y;
+    k = vis ? __float_as_uint(depth[i]) : 0xffffffffu;  // visible depths are positive
+    keys[i] = k;
+    vals[i] = (uint32_t)i;
+  }
+  count_digits(s_hist, k, i < n, 4, 8);
+  __syncthreads();
+  flush_digits(s_hist, 4, hist);
 }
 
 // ------------------------------------------------------------------------------------------
-// Stable counting sort of the instances by tile, in one pass over the depth-sorted Gaussians.
+// Instances in depth order, then a stable sort on the tile digit.
 //
-// The depth-ordered Gaussians are cut into C contiguous chunks of about equal scatter cost
-// (instances / 32 + 1 per Gaussian, running sum split into C equal shares).  (1) Each chunk counts, per tile, how many of its Gaussians' rectangles cover that
-// tile, with a 2D difference array in shared memory (four atomics per Gaussian, then prefix sums
-// along x and y).  (2) One exclusive scan over the tile-major (tile, chunk) count matrix gives
-// every chunk its first output position per tile.  (3) Each chunk walks its Gaussians in depth
-// order with one warp: the lanes cover the current Gaussian's rectangle, each writing the
-// Gaussian's id at its tile's cursor and advancing it.  Instances of one tile therefore land in
-// (depth, id) order, exactly the stable sort by (tile, depth) key.  Per-tile ranges come
-// straight from the scanned matrix.
+// Each visible Gaussian (in depth order) tests the tiles of its rectangle clipped to
+// reach_bounds with the exact reachability rule (tile_reach.cuh); one warp handles one Gaussian,
+// 32 tiles per step, so a huge rectangle costs steps, not imbalance.  A first pass counts the kept
+// tiles, an exclusive scan gives each Gaussian its first instance, and a second pass writes the
+// (tile id, Gaussian id) pairs -- each Gaussian's contiguously, in row-major tile order.  The LSD
+// radix passes over the tile id then make the order (tile, depth, id).
 // ------------------------------------------------------------------------------------------
 
 // Rectangles are clipped to the tile grid, so records that come from the caller rather than
@@ -338,216 +495,245 @@ __device__ __forceinline__ ushort4 clip_rect(ushort4 r, int tiles_x, int tiles_y
   return r;
 }
 
-// Scatter cost of each depth-ordered Gaussian in warp steps: one per 32 instances plus one for
-// the Gaussian itself.  Chunks are cut at equal shares of the running sum of this cost.
-__global__ void work_units_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                                  int64_t n, int tiles_x, int tiles_y, uint32_t* __restrict__ units) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const ushort4 r = clip_rect(rect[order[s]], tiles_x, tiles_y);
-  const int w = (int)r.z - (int)r.x, h = (int)r.w - (int)r.y;
-  units[s] = (w > 0 && h > 0) ? (uint32_t)((w * h + 31) / 32 + 1) : 0u;
+// The tested tiles of a block of kWalkThreads consecutive depth-ordered Gaussians form one
+// sequence -- Gaussian-major, each tested rectangle row-major -- cut into 32-tile words that the
+// block's warps share, so a few large rectangles do not leave one warp with all the work.
+constexpr int kWalkThreads = 256;
+constexpr int kWalkWarps = kWalkThreads / 32;
+constexpr int kEmitChunk = 4 * kWalkThreads;  // bitmask words a block scans at a time
+
+struct BlockWalk {
+  uint32_t incl[kWalkThreads];    // tested tiles of Gaussians 0 .. i of the block
+  uint32_t origin[kWalkThreads];  // tile (x0 | y0 << 16) of Gaussian i's tested rectangle
+  uint32_t width[kWalkThreads];   // its width in tiles
+  Reach reach[kWalkThreads];
+};
+
+__device__ __forceinline__ uint32_t rect_area(ushort4 r) {
+  return (r.z > r.x && r.w > r.y) ? (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y) : 0u;
 }
 
-// First s in [0, n) with off[s] >= target (n if none), by a 32-way search over the warp.
-__device__ int64_t warp_lower_bound(const uint64_t* __restrict__ off, int64_t n, uint64_t target) {
-  const int lane = threadIdx.x & 31;
-  int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]; hi == n or off[hi] >= target
-  while (hi - lo > 31) {
-    const int64_t step = (hi - lo + 31) / 32;
-    int64_t p = lo + (int64_t)(lane + 1) * step - 1;
-    if (p > hi - 1) p = hi - 1;
-    const unsigned b = __ballot_sync(0xffffffffu, off[p] >= target);
-    if (b == 0) {
-      lo = hi;
-      break;
-    }
-    const int f = __ffs(b) - 1;
-    const int64_t pf = min(lo + (int64_t)(f + 1) * step - 1, hi - 1);
-    lo = lo + (int64_t)f * step;
-    hi = pf;
-  }
-  const int64_t p = lo + lane;
-  const unsigned b = __ballot_sync(0xffffffffu, p >= hi || off[p] >= target);
-  return lo + (__ffs(b) - 1);
-}
-
-// Gaussian range [s0, s1) of chunk `c` out of `chunks`: the Gaussians whose running cost `off`
-// starts inside the chunk's share of `total`.  Executed by a full warp.
-__device__ __forceinline__ void chunk_range(const uint64_t* __restrict__ off, int64_t n,
-                                            const int64_t* __restrict__ total, int64_t chunks,
-                                            int64_t c, int64_t* s0, int64_t* s1) {
-  const uint64_t k = (uint64_t)*total;
-  uint64_t per = (k + (uint64_t)chunks - 1) / (uint64_t)chunks;
-  if (per == 0) per = 1;
-  // Targets are clamped to the total: the first Gaussian whose running cost reaches the total
-  // starts the culled (zero-cost) tail, which belongs to no chunk.
-  const uint64_t t0 = (uint64_t)c * per, t1 = (uint64_t)(c + 1) * per;
-  *s0 = warp_lower_bound(off, n, t0 < k ? t0 : k);
-  *s1 = warp_lower_bound(off, n, t1 < k ? t1 : k);
-}
-
-constexpr int kHistThreads = 256;
-
-__global__ void __launch_bounds__(kHistThreads)
-chunk_hist_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t n,
-                  const uint64_t* __restrict__ offsets, const int64_t* __restrict__ total, int tiles_x,
-                  int tiles_y, int64_t chunks, uint32_t* __restrict__ counts) {
-  extern __shared__ int s_diff[];  // (tiles_y + 1) x (tiles_x + 1)
-  __shared__ int64_t s_range[2];
-  const int W1 = tiles_x + 1, H1 = tiles_y + 1;
-  for (int i = threadIdx.x; i < W1 * H1; i += kHistThreads) s_diff[i] = 0;
-  if (threadIdx.x < 32) {
-    int64_t a, b;
-    chunk_range(offsets, n, total, chunks, blockIdx.x, &a, &b);
-    if (threadIdx.x == 0) { s_range[0] = a; s_range[1] = b; }
-  }
+// Fills bw from the walk rectangles (and, with want_reach, the reachability parameters) of
+// Gaussians base .. base + kWalkThreads - 1; returns the block's tested-tile count.
+__device__ __forceinline__ uint32_t block_walk_load(BlockWalk& bw, const ushort4* __restrict__ walk,
+                                                    const Reach* __restrict__ reach, int64_t base, int64_t n,
+                                                    bool want_reach) {
+  const int t = threadIdx.x;
+  const int64_t s = base + t;
+  const ushort4 r = s < n ? walk[s] : make_ushort4(0, 0, 0, 0);
+  const uint32_t area = rect_area(r);
+  if (want_reach && area > 0) bw.reach[t] = reach[s];
+  uint32_t total;
+  bw.incl[t] = block_inclusive_scan<uint32_t, kWalkThreads>(area, &total);
+  bw.origin[t] = (uint32_t)r.x | ((uint32_t)r.y << 16);
+  bw.width[t] = (uint32_t)(r.z - r.x);
   __syncthreads();
-  const int64_t s0 = s_range[0], s1 = s_range[1];
-  for (int64_t s = s0 + threadIdx.x; s < s1; s += kHistThreads) {
-    const ushort4 r = clip_rect(rect[order[s]], tiles_x, tiles_y);
+  return total;
+}
+
+// Position f (< total) of the block's sequence -> Gaussian i of the block and its tile (tx, ty).
+__device__ __forceinline__ int block_locate(const BlockWalk& bw, uint32_t f, int* tx, int* ty) {
+  int i = 0;
+#pragma unroll
+  for (int step = kWalkThreads / 2; step >= 1; step >>= 1)
+    if (bw.incl[i + step - 1] <= f) i += step;
+  const uint32_t local = f - (i > 0 ? bw.incl[i - 1] : 0u);
+  const uint32_t w = bw.width[i], o = bw.origin[i];
+  const uint32_t dy = local / w;
+  *tx = (int)((o & 0xffffu) + (local - dy * w));
+  *ty = (int)((o >> 16) + dy);
+  return i;
+}
+
+// Kept bits of word k of the block's sequence (32 tested tiles), computed by the calling warp.
+__device__ __forceinline__ unsigned test_word(const BlockWalk& bw, uint32_t total, uint32_t k) {
+  const uint32_t f = 32u * k + (threadIdx.x & 31);
+  bool kept = false;
+  if (f < total) {
+    int tx, ty;
+    const int i = block_locate(bw, f, &tx, &ty);
+    kept = reach_tile(bw.reach[i], tx, ty);
+  }
+  return __ballot_sync(0xffffffffu, kept);
+}
+
+// Per depth-ordered Gaussian: the rectangle it tests (its rectangle clipped to reach_bounds) and
+// its reachability parameters; per block of kWalkThreads Gaussians: the bitmask words its tested
+// tiles take.
+__global__ void __launch_bounds__(kWalkThreads)
+walk_setup_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
+                  int tiles_x, int tiles_y, ushort4* __restrict__ walk, Reach* __restrict__ reach,
+                  uint32_t* __restrict__ block_words) {
+  const int64_t s = (int64_t)blockIdx.x * kWalkThreads + threadIdx.x;
+  uint32_t area = 0;
+  if (s < n) {
+    const uint32_t g = order[s];
+    ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
     if (r.z > r.x && r.w > r.y) {
-      atomicAdd(&s_diff[r.y * W1 + r.x], 1);
-      atomicAdd(&s_diff[r.y * W1 + r.z], -1);
-      atomicAdd(&s_diff[r.w * W1 + r.x], -1);
-      atomicAdd(&s_diff[r.w * W1 + r.z], 1);
+      const Reach rc = reach_setup(mean2d[g], conic_opacity[g]);
+      reach[s] = rc;
+      r = reach_bounds(rc, r);
+      area = rect_area(r);
     }
+    walk[s] = r;
   }
-  __syncthreads();
-  // prefix sums along x (one warp per row), then along y (one warp per column)
+  uint32_t total;
+  block_inclusive_scan<uint32_t, kWalkThreads>(area, &total);
+  if (threadIdx.x == 0) block_words[blockIdx.x] = (total + 31u) / 32u;
+}
+
+// Tests every tested tile once: kept count per block and, where the block's words fit in
+// `bits_cap`, its kept bitmask (bit l of word k: position 32 k + l of the block's sequence).
+__global__ void __launch_bounds__(kWalkThreads)
+test_tiles_kernel(const ushort4* __restrict__ walk, const Reach* __restrict__ reach, int64_t n,
+                  const uint64_t* __restrict__ block_word_first, uint64_t bits_cap, uint32_t* __restrict__ bits,
+                  uint32_t* __restrict__ block_kept) {
+  __shared__ BlockWalk bw;
+  __shared__ uint32_t s_kept[kWalkWarps];
+  const uint32_t total = block_walk_load(bw, walk, reach, (int64_t)blockIdx.x * kWalkThreads, n, true);
+  const uint32_t words = (total + 31u) / 32u;
+  const uint64_t w0 = block_word_first[blockIdx.x];
+  const bool store = w0 + words <= bits_cap;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int row = warp; row < tiles_y; row += kHistThreads / 32) {
-    int carry = 0;
-    for (int x0 = 0; x0 < tiles_x; x0 += 32) {
-      const int x = x0 + lane;
-      int v = x < tiles_x ? s_diff[row * W1 + x] : 0;
-      v = warp_inclusive_scan(v) + carry;
-      if (x < tiles_x) s_diff[row * W1 + x] = v;
-      carry = __shfl_sync(0xffffffffu, v, 31);
-    }
+  uint32_t c = 0;
+  for (uint32_t k = warp; k < words; k += kWalkWarps) {
+    const unsigned b = test_word(bw, total, k);
+    if (store && lane == 0) bits[w0 + k] = b;
+    c += __popc(b);
   }
+  if (lane == 0) s_kept[warp] = c;
   __syncthreads();
-  for (int x0 = warp * 32; x0 < tiles_x; x0 += kHistThreads) {
-    const int x = x0 + lane;
-    if (x < tiles_x) {
-      int run = 0;
-      for (int y = 0; y < tiles_y; ++y) {
-        run += s_diff[y * W1 + x];
-        counts[(int64_t)(y * tiles_x + x) * chunks + blockIdx.x] = (uint32_t)run;
+  if (threadIdx.x == 0) {
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < kWalkWarps; ++w) sum += s_kept[w];
+    block_kept[blockIdx.x] = sum;
+  }
+}
+
+// Writes each block's (tile id, Gaussian id) pairs from the block's first instance in sequence
+// order (Gaussian-major in depth order, row-major within a rectangle), from the bitmask of
+// test_tiles_kernel or, for blocks whose words did not fit, by testing again with the same
+// decisions.  Positions >= cap are dropped.
+__global__ void __launch_bounds__(kWalkThreads)
+emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ walk,
+            const Reach* __restrict__ reach, int64_t n, const uint64_t* __restrict__ block_word_first,
+            uint64_t bits_cap, const uint32_t* __restrict__ bits, const uint64_t* __restrict__ block_first,
+            int tiles_x, int64_t cap, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int passes,
+            int width, uint32_t* __restrict__ hist) {
+  __shared__ BlockWalk bw;
+  __shared__ uint32_t s_hist[kMaxPasses][kBins];
+  __shared__ uint32_t s_gid[kWalkThreads];
+  __shared__ uint32_t s_words[kEmitChunk];
+  __shared__ uint32_t s_before[kEmitChunk];
+  const int64_t base = (int64_t)blockIdx.x * kWalkThreads;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const uint64_t w0 = block_word_first[blockIdx.x];
+  s_gid[t] = base + t < n ? order[base + t] : 0u;
+  for (int i = t; i < kMaxPasses * kBins; i += kWalkThreads) (&s_hist[0][0])[i] = 0;
+  const uint32_t total = block_walk_load(bw, walk, reach, base, n, true);
+  const uint32_t words = (total + 31u) / 32u;
+  const bool stored = w0 + words <= bits_cap;
+  uint64_t pos = block_first[blockIdx.x];
+  const unsigned lt = lanemask_lt();
+  for (uint32_t c0 = 0; c0 < words; c0 += kEmitChunk) {
+    const uint32_t cw = min((uint32_t)kEmitChunk, words - c0);
+    if (stored) {
+      for (uint32_t i = t; i < cw; i += kWalkThreads) s_words[i] = bits[w0 + c0 + i];
+    } else {
+      for (uint32_t i = warp; i < cw; i += kWalkWarps) {
+        const unsigned b = test_word(bw, total, c0 + i);
+        if (lane == 0) s_words[i] = b;
       }
     }
-  }
-}
-
-__global__ void __launch_bounds__(32)
-chunk_scatter_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t n,
-                     const uint64_t* __restrict__ offsets, const int64_t* __restrict__ total, int tiles_x,
-                     int tiles_y, int64_t chunks, const uint64_t* __restrict__ base, int64_t cap,
-                     uint32_t* __restrict__ point_list, uint32_t* __restrict__ tile_keys) {
-  extern __shared__ uint32_t s_cur[];  // one cursor per tile
-  const int tiles = tiles_x * tiles_y;
-  const int lane = threadIdx.x;
-  const int64_t chunk = blockIdx.x;
-  int64_t s0, s1;
-  chunk_range(offsets, n, total, chunks, chunk, &s0, &s1);
-#pragma unroll 8
-  for (int t = lane; t < tiles; t += 32) {
-    const uint64_t b = base[(int64_t)t * chunks + chunk];
-    s_cur[t] = (uint32_t)(b < (uint64_t)cap ? b : (uint64_t)cap);
-  }
-  __syncwarp();
-  for (int64_t sg = s0; sg < s1; sg += 32) {
-    // each lane fetches one Gaussian of the group; they are then handled one at a time
-    uint32_t g = 0;
-    ushort4 r = make_ushort4(0, 0, 0, 0);
-    if (sg + lane < s1) {
-      g = order[sg + lane];
-      r = clip_rect(rect[g], tiles_x, tiles_y);
+    __syncthreads();
+    // kept instances before each word of the chunk (4 consecutive words per thread)
+    uint32_t cnt[4], run = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = 4u * t + q;
+      cnt[q] = i < cw ? __popc(s_words[i]) : 0u;
+      run += cnt[q];
     }
-    unsigned todo = __ballot_sync(0xffffffffu, r.z > r.x && r.w > r.y);
-    while (todo) {
-      const int i = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t gi = __shfl_sync(0xffffffffu, g, i);
-      const int rx0 = __shfl_sync(0xffffffffu, (int)r.x, i);
-      const int ry0 = __shfl_sync(0xffffffffu, (int)r.y, i);
-      const int w = __shfl_sync(0xffffffffu, (int)r.z, i) - rx0;
-      const int h = __shfl_sync(0xffffffffu, (int)r.w, i) - ry0;
-      if (w > 0 && h > 0) {
-        const int cnt = w * h;
-        int dy = lane / w, dx = lane - dy * w;  // position of this lane's first tile
-        const int step_y = 32 / w, step_x = 32 - step_y * w;
-        for (int k = lane; k < cnt; k += 32) {
-          const int t = (ry0 + dy) * tiles_x + rx0 + dx;
-          const uint32_t p = s_cur[t];
-          s_cur[t] = p + 1;
-          if (p < (uint32_t)cap) {
-            point_list[p] = gi;
-            if (tile_keys != nullptr) tile_keys[p] = (uint32_t)t;
-          }
-          dx += step_x;
-          dy += step_y;
-          if (dx >= w) { dx -= w; ++dy; }
+    uint32_t chunk_total;
+    const uint32_t incl = block_inclusive_scan<uint32_t, kWalkThreads>(run, &chunk_total);
+    uint32_t acc = incl - run;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = 4u * t + q;
+      if (i < cw) s_before[i] = acc;
+      acc += cnt[q];
+    }
+    __syncthreads();
+    for (uint32_t i = warp; i < cw; i += kWalkWarps) {
+      const unsigned b = s_words[i];
+      if (b == 0u) continue;  // uniform over the warp
+      uint32_t key = 0;
+      bool put = false;
+      if ((b >> lane) & 1u) {
+        int tx, ty;
+        const int gi = block_locate(bw, 32u * (c0 + i) + lane, &tx, &ty);
+        const uint64_t p = pos + s_before[i] + __popc(b & lt);
+        if (p < (uint64_t)cap) {
+          key = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
+          keys[p] = key;
+          vals[p] = s_gid[gi];
+          put = true;
         }
       }
-      __syncwarp();
+      count_digits(s_hist, key, put, passes, width);
     }
+    pos += chunk_total;
+    __syncthreads();
   }
+  flush_digits(s_hist, passes, hist);
 }
 
-__global__ void ranges_from_base_kernel(const uint64_t* __restrict__ base, int tiles, int64_t chunks,
-                                        const int64_t* __restrict__ total, int64_t cap,
-                                        uint2* __restrict__ ranges) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tiles) return;
-  const uint64_t k = (uint64_t)*total;
-  const uint64_t st = base[(int64_t)t * chunks];
-  const uint64_t en = (t + 1 < tiles) ? base[(int64_t)(t + 1) * chunks] : k;
-  ranges[t] = make_uint2((uint32_t)(st < (uint64_t)cap ? st : cap), (uint32_t)(en < (uint64_t)cap ? en : cap));
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t cap,
+                              uint2* __restrict__ ranges) {
+  const int64_t n = element_count(nptr, 0, cap);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t t = keys[j];
+  if (j == 0 || keys[j - 1] != t) ranges[t].x = (uint32_t)j;
+  if (j == n - 1 || keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Number of counting-sort chunks: enough for parallelism, with the (tile, chunk) matrix kept
-// within 4M entries.
-int64_t chunk_count(int tiles) {
-  int64_t c = (int64_t(4) << 20) / (tiles > 0 ? tiles : 1);
-  return c < 128 ? 128 : (c > 1024 ? 1024 : c);
-}
-
 }  // namespace
-
-size_t bin_smem_bytes(int width, int height) {
-  const size_t hist = sizeof(int) * (size_t)(tiles_of(width) + 1) * (tiles_of(height) + 1);
-  const size_t cur = sizeof(uint32_t) * (size_t)tiles_of(width) * tiles_of(height);
-  return hist > cur ? hist : cur;
-}
 
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   BinPlan p;
   p.n = n;
   p.capacity = capacity;
   p.num_tiles = tiles_of(width) * tiles_of(height);
-  p.tile_bits = 0;
-  p.chunks = chunk_count(p.num_tiles);
+  int bits = 0;
+  while ((int64_t(1) << bits) < p.num_tiles) ++bits;
+  p.tile_bits = bits;
   p.chunk = 0;
-  const int64_t nb_d = (n + kRadixTile - 1) / kRadixTile;
-  p.hist_blocks = nb_d;
-  const int64_t hist_entries = (int64_t)kBins * nb_d;
-  const int64_t mat = (int64_t)p.num_tiles * p.chunks;
-  const int64_t part_a = (hist_entries + kScanChunk - 1) / kScanChunk;
-  const int64_t part_b = (mat + kScanChunk - 1) / kScanChunk;
-  const int64_t part_c = (n + kScanChunk - 1) / kScanChunk;
-  p.partial_cap = std::max(part_a, std::max(part_b, part_c)) + 1;
+  p.chunks = 0;
+  const int64_t groups = (n + 31) / 32;
+  p.hist_blocks = 0;
+  p.partial_cap = (groups + kScanChunk - 1) / kScanChunk + 1;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) { p.off_dkeys[k] = off; off += align256(sizeof(uint32_t) * n); }
   for (int k = 0; k < 2; ++k) { p.off_dvals[k] = off; off += align256(sizeof(uint32_t) * n); }
-  p.off_offsets = off; off += align256(sizeof(uint64_t) * n);
-  p.off_counts = off; off += align256(sizeof(uint32_t) * mat);
-  p.off_base = off; off += align256(sizeof(uint64_t) * mat);
-  p.off_hist = off; off += align256(sizeof(uint32_t) * hist_entries);
+  p.bits_cap = (uint64_t)(capacity / 4 + groups + 1);
+  p.off_gwords = off; off += align256(sizeof(uint32_t) * groups);
+  p.off_gwfirst = off; off += align256(sizeof(uint64_t) * groups);
+  p.off_gkept = off; off += align256(sizeof(uint32_t) * groups);
+  p.off_gfirst = off; off += align256(sizeof(uint64_t) * groups);
+  p.off_bits = off; off += align256(sizeof(uint32_t) * p.bits_cap);
+  p.off_walk = off; off += align256(sizeof(uint64_t) * n);
+  p.off_reach = off; off += align256(sizeof(Reach) * n);
+  p.off_ikeys[0] = off; off += align256(sizeof(uint32_t) * capacity);
+  p.off_ikeys[1] = off; off += align256(sizeof(uint32_t) * capacity);
+  p.off_ivals = off; off += align256(sizeof(uint32_t) * capacity);
+  p.off_err = off; off += 256;
+  p.off_sort = off; off += align256(std::max(sort_scratch_bytes(n, 32), sort_scratch_bytes(capacity, bits)));
   p.off_partials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
-  p.off_scalars = off; off += align256(sizeof(int64_t) * 4);
   p.total = off;
   return p;
 }
@@ -560,48 +746,67 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
                         reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[1])};
   uint32_t* dvals[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dvals[0]),
                         reinterpret_cast<uint32_t*>(ws + plan.off_dvals[1])};
-  uint64_t* offsets = reinterpret_cast<uint64_t*>(ws + plan.off_offsets);
-  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + plan.off_counts);
-  uint64_t* base = reinterpret_cast<uint64_t*>(ws + plan.off_base);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(ws + plan.off_hist);
+  uint32_t* gwords = reinterpret_cast<uint32_t*>(ws + plan.off_gwords);
+  uint64_t* gwfirst = reinterpret_cast<uint64_t*>(ws + plan.off_gwfirst);
+  uint32_t* gkept = reinterpret_cast<uint32_t*>(ws + plan.off_gkept);
+  uint64_t* gfirst = reinterpret_cast<uint64_t*>(ws + plan.off_gfirst);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(ws + plan.off_bits);
+  ushort4* walk = reinterpret_cast<ushort4*>(ws + plan.off_walk);
+  Reach* reach = reinterpret_cast<Reach*>(ws + plan.off_reach);
+  uint32_t* sort_scratch = reinterpret_cast<uint32_t*>(ws + plan.off_sort);
+  uint32_t* err = reinterpret_cast<uint32_t*>(ws + plan.off_err);
   uint64_t* partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
-  int64_t* total_work = reinterpret_cast<int64_t*>(ws + plan.off_scalars);
   const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
+  const float2* m2 = reinterpret_cast<const float2*>(proj.mean2d);
+  const float4* co = reinterpret_cast<const float4*>(proj.conic_opacity);
 
-  cudaError_t e;
-  if (n == 0) {
-    e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)plan.num_tiles, st);
-    if (e != cudaSuccess) return e;
-    return cudaMemsetAsync(out.num_instances, 0, sizeof(int64_t), st);
-  }
+  cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)plan.num_tiles, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  if (n == 0) return cudaMemsetAsync(out.num_instances, 0, sizeof(int64_t), st);
   const int tb = 256;
   const unsigned gb = (unsigned)((n + tb - 1) / tb);
   // 1. Gaussians by float32 depth (stable; culled ones last).
-  depth_keys_kernel<<<gb, tb, 0, st>>>(proj.depth, rect, n, dkeys[0], dvals[0]);
-  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, hist, partials, st);
+  e = sort_clear(sort_scratch, n, 32, st);
+  if (e != cudaSuccess) return e;
+  depth_keys_kernel<<<gb, kRadixThreads, 0, st>>>(proj.depth, rect, n, dkeys[0], dvals[0], sort_scratch);
+  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_scratch, err, true, st);
   const uint32_t* order = dvals[dcur];
-  // 2. Running scatter cost in depth order, to cut balanced chunks.
-  uint32_t* tcount = dkeys[dcur ^ 1];
-  work_units_kernel<<<gb, tb, 0, st>>>(order, rect, n, tiles_x, tiles_y, tcount);
-  e = exclusive_scan<uint32_t, uint64_t>(tcount, n, offsets, partials, total_work, st);
+  // 2. Tiles to test; each tested once (kept bitmask + kept count per block of kWalkThreads
+  //    Gaussians); first instance of each block; K.
+  const int64_t wblocks = (n + kWalkThreads - 1) / kWalkThreads;
+  walk_setup_kernel<<<(unsigned)wblocks, kWalkThreads, 0, st>>>(order, rect, m2, co, n, tiles_x, tiles_y, walk,
+                                                                reach, gwords);
+  e = exclusive_scan<uint32_t, uint64_t>(gwords, wblocks, gwfirst, partials, nullptr, st);
   if (e != cudaSuccess) return e;
-  // 3. Per-chunk tile counts, scanned tile-major: first position of every (tile, chunk).
-  const size_t smem = bin_smem_bytes(v.width, v.height);
-  e = cudaFuncSetAttribute(chunk_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  test_tiles_kernel<<<(unsigned)wblocks, kWalkThreads, 0, st>>>(walk, reach, n, gwfirst, plan.bits_cap, bits, gkept);
+  e = exclusive_scan<uint32_t, uint64_t>(gkept, wblocks, gfirst, partials, out.num_instances, st);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chunk_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // 3. Instances in depth order, into the buffer that makes the tile passes end in `out`.
+  const int passes = radix_pass_count(plan.tile_bits);
+  uint32_t* out_keys = out.tile_keys ? out.tile_keys : reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[1]);
+  uint32_t* ikeys[2];
+  uint32_t* ivals[2];
+  uint32_t* wk0 = reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[0]);
+  uint32_t* wv0 = reinterpret_cast<uint32_t*>(ws + plan.off_ivals);
+  if (passes % 2 == 0) {
+    ikeys[0] = out_keys; ivals[0] = out.point_list; ikeys[1] = wk0; ivals[1] = wv0;
+  } else {
+    ikeys[0] = wk0; ivals[0] = wv0; ikeys[1] = out_keys; ivals[1] = out.point_list;
+  }
+  e = sort_clear(sort_scratch, plan.capacity, plan.tile_bits, st);
   if (e != cudaSuccess) return e;
-  chunk_hist_kernel<<<(unsigned)plan.chunks, kHistThreads, smem, st>>>(
-      order, rect, n, offsets, total_work, tiles_x, tiles_y, plan.chunks, counts);
-  const int64_t mat = (int64_t)plan.num_tiles * plan.chunks;
-  e = exclusive_scan<uint32_t, uint64_t>(counts, mat, base, partials, out.num_instances, st);
-  if (e != cudaSuccess) return e;
-  // 4. Scatter the ids into their tiles' lists; 5. ranges.
-  chunk_scatter_kernel<<<(unsigned)plan.chunks, 32, smem, st>>>(
-      order, rect, n, offsets, total_work, tiles_x, tiles_y, plan.chunks, base, plan.capacity,
-      out.point_list, out.tile_keys);
-  ranges_from_base_kernel<<<(plan.num_tiles + tb - 1) / tb, tb, 0, st>>>(
-      base, plan.num_tiles, plan.chunks, out.num_instances, plan.capacity, reinterpret_cast<uint2*>(out.ranges));
+  emit_kernel<<<(unsigned)wblocks, kWalkThreads, 0, st>>>(order, walk, reach, n, gwfirst, plan.bits_cap, bits,
+                                                          gfirst, tiles_x, plan.capacity, ikeys[0], ivals[0], passes,
+                                                          radix_digit_width(plan.tile_bits), sort_scratch);
+  // 4. Stable sort by tile id; 5. tile ranges.
+  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_scratch, err, true, st);
+  if (plan.capacity > 0) {
+    const unsigned gr = (unsigned)((plan.capacity + tb - 1) / tb);
+    ranges_kernel<<<gr, tb, 0, st>>>(out_keys, out.num_instances, plan.capacity,
+                                     reinterpret_cast<uint2*>(out.ranges));
+  }
   return cudaGetLastError();
 }
 

@@ -39,17 +39,16 @@ struct BinPlan {
   int64_t capacity;
   int num_tiles;
   int tile_bits;
-  int chunk;       // unused (chunks are balanced by instance count)
-  int64_t chunks;  // number of counting-sort chunks
+  int chunk;       // unused
+  int64_t chunks;  // unused
   // workspace carve-up (byte offsets)
-  size_t off_dkeys[2], off_dvals[2], off_offsets, off_counts, off_base, off_hist, off_partials, off_scalars,
-      total;
-  int64_t hist_blocks;  // radix blocks of the depth sort
+  size_t off_dkeys[2], off_dvals[2], off_gwords, off_gwfirst, off_gkept, off_gfirst, off_bits, off_walk,
+      off_reach, off_ikeys[2], off_ivals, off_err, off_sort, off_partials, total;
+  uint64_t bits_cap;  // 32-bit words of kept-tile bitmask available
+  int64_t hist_blocks;  // unused
   int64_t partial_cap;  // entries available for scan partials
 };
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);
-size_t bin_smem_bytes(int width, int height);  // dynamic shared memory of the tile counting sort
-constexpr size_t kMaxBinSmem = 227 * 1024;
 cudaError_t launch_bin_sort(const sdgs_projected& p, const sdgs_view& v, const BinPlan& plan,
                             char* ws, const sdgs_bins& out, cudaStream_t st);
 

@@ -1,6 +1,6 @@
 // Per-Gaussian geometry of the 7DGS render path in FP32: conditional slicing (Sec. 4.2,
 // Eqs. cond_mean / cond_cov, Algorithm 1 steps 3-5), modulation (Eqs. temp_mod / dir_mod,
-// Algorithm 1 step 6), EWA projection and SH colour (Sec. 4.3, the 3DGS projection the paper
+// Algorithm 1 step 6), EWA projection and SH colour (Sec. 4.4, the 3DGS projection the paper
 // adopts).  Used by the forward kernel and recomputed by the backward kernel.
 //
 // Slicing never forms Sigma = L L^T.  Forming it squares the conditioning of the (t, d) block,

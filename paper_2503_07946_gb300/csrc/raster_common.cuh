@@ -31,48 +31,4 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Smallest exponent-argument a(x-u)^2 + 2b(x-u)(y-v) + c(y-v)^2 over the box [x0,x1] x [y0,y1]
-// (zero when the mean lies inside).  On an edge the minimum over the free coordinate is at the
-// clamped stationary point.  a, c > 0 for a positive-definite conic.  An approximate stationary
-// point only raises the edge value by c (error)^2, a relative O(eps^2) far inside the margin of
-// splat_misses_box.
-__device__ __forceinline__ float conic_box_min(float a, float b, float c, float u, float v, float x0,
-                                               float x1, float y0, float y1) {
-  if (u >= x0 && u <= x1 && v >= y0 && v <= y1) return 0.f;
-  float best = INFINITY;
-  const float ex[2] = {x0 - u, x1 - u};
-  const float ey[2] = {y0 - v, y1 - v};
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float dx = ex[i];
-    const float dy = fminf(ey[1], fmaxf(ey[0], __fdividef(-b * dx, c)));
-    best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float dy = ey[i];
-    const float dx = fminf(ex[1], fmaxf(ex[0], __fdividef(-b * dy, a)));
-    best = fminf(best, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
-  }
-  return fmaxf(best, 0.f);
-}
-
-// True when alpha_cond exp(-q/2) < 1/255 at every pixel centre of the box, with a relative
-// safety margin far above the FP32 rounding of either this test or the per-pixel evaluation.
-// Both evaluate the quadratic form in FP32, whose relative error grows like
-// eps (ac + b^2) / det for an elongated conic; the margin grows with it, and a conic too
-// ill-conditioned for a margin below one half is never culled.
-__device__ __forceinline__ bool splat_misses_box(float4 co, float2 xy, float x0, float x1, float y0,
-                                                 float y1) {
-  if (!(co.w >= kAlphaMin)) return true;
-  const float ac = co.x * co.z, bb = co.y * co.y;
-  const float det = ac - bb;
-  if (!(det > 0.f)) return false;
-  const float margin = 1e-4f + 64.f * 5.9604645e-8f * (ac + bb) / det;
-  if (!(margin < 0.5f)) return false;
-  const float thr = 2.f * __logf(255.f * co.w);  // q above this gives alpha < 1/255 (abs err ~1e-6)
-  const float qmin = conic_box_min(co.x, co.y, co.z, xy.x, xy.y, x0, x1, y0, y1);
-  return qmin * (1.f - margin) > thr + 1e-4f;
-}
-
 }  // namespace sdgs

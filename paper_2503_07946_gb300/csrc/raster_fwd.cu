@@ -1,12 +1,10 @@
-// Forward tile rasteriser (Sec. 4.3 depth-aware opacity blending with the 3DGS rules).
+// Forward tile rasteriser (Sec. 4.4; the 3DGS blending rules).
 //
 // One 128-thread block per 16x16 tile; each thread owns two pixels of one column, rows r and
 // r + 8, so every Gaussian fetched from shared memory is evaluated twice.  The tile's sorted
-// instances are staged 128 at a time; while staging, each thread tests its Gaussian against the
-// tile's pixel-centre box and drops it when alpha_cond exp(-q/2) < 1/255 holds at every pixel of
-// the tile with a safety margin (those evaluations would all be skipped), and the survivors are
-// compacted in order together with their positions in the tile list.  The block leaves once every
-// pixel has stopped.
+// instances (only Gaussians that may reach the tile, see tile_reach.cuh) are staged 128 at a time
+// in shared memory; each pixel walks them front to back.  The block leaves once every pixel has
+// stopped.
 #include "raster_common.cuh"
 
 namespace sdgs {
@@ -63,18 +61,14 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
   __shared__ float2 s_xy[kThreads];
   __shared__ float4 s_q[kThreads];
   __shared__ float4 s_rgb[kThreads];
-  __shared__ int s_pos[kThreads];
-  __shared__ int s_warp[kThreads / 32];
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
   const int py0 = ty * kTile + (threadIdx.x / kTile);
   const int py1 = py0 + kTile / 2;
   const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
-  const float bx0 = (float)(tx * kTile) + 0.5f, bx1 = bx0 + (float)(kTile - 1);
-  const float by0 = (float)(ty * kTile) + 0.5f, by1 = by0 + (float)(kTile - 1);
   const uint2 range = a.ranges[tile];
   const int n = (int)(range.y - range.x);
 
@@ -83,35 +77,15 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
   p1.done = !(px < a.width && py1 < a.height);
   for (int base = 0; base < n; base += kThreads) {
     if (__syncthreads_count(p0.done && p1.done) == kThreads) break;
-    // stage, cull against the tile, compact in order
+    // stage the next 128 instances of the tile's list
     const int j = base + threadIdx.x;
-    bool keep = false;
-    float2 xy;
-    float4 co;
-    uint32_t g = 0;
     if (j < n) {
-      g = a.point_list[range.x + j];
-      xy = a.mean2d[g];
-      co = a.conic_opacity[g];
-      keep = !splat_misses_box(co, xy, bx0, bx1, by0, by1);
+      const uint32_t g = a.point_list[range.x + j];
+      s_xy[threadIdx.x] = a.mean2d[g];
+      s_q[threadIdx.x] = scaled_conic(a.conic_opacity[g]);
+      s_rgb[threadIdx.x] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
     }
-    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) s_warp[warp] = __popc(ballot);
-    __syncthreads();
-    int off = 0, cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-      const int c = s_warp[w];
-      off += (w < warp) ? c : 0;
-      cnt += c;
-    }
-    if (keep) {
-      const int idx = off + __popc(ballot & ((1u << lane) - 1u));
-      s_xy[idx] = xy;
-      s_q[idx] = scaled_conic(co);
-      s_rgb[idx] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
-      s_pos[idx] = j;
-    }
+    const int cnt = min(kThreads, n - base);
     __syncthreads();
     if (!(p0.done && p1.done)) {
       // Entries past cnt are never read: the batch is padded by predication.  The stop test runs
@@ -124,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
             const float2 m = s_xy[k];
             const float4 q = s_q[k];
             const float4 c = s_rgb[k];
-            const uint32_t pos1 = (uint32_t)s_pos[k] + 1u;
+            const uint32_t pos1 = (uint32_t)(base + k) + 1u;
             // offsets exactly as the backward forms them, so both passes take the same decisions
             const float dx = fx - m.x;
             blend<kCount>(p0, q, c, dx, fy0 - m.y, pos1);

@@ -378,8 +378,21 @@ void worker_main(sdgs_server* s) {
     bool busy = false;
     for (auto& sl : s->slots) busy |= sl.req != nullptr;
     if (s->stop && !busy) break;
-    if (!s->stop && !s->fatal) admit(s);
-    s->work_cv.wait_for(lk, std::chrono::milliseconds(2));
+    auto wait = std::chrono::microseconds(2000);
+    if (!s->stop && !s->fatal && !s->queue.empty()) {
+      // batching window: with free slots to spare, let the queue fill until the oldest request
+      // has waited batch_window_us
+      int free_slots = 0;
+      for (auto& sl : s->slots) free_slots += sl.req == nullptr;
+      const auto age = Clock::now() - s->queue.front()->t_submit;
+      const auto window = std::chrono::microseconds(s->cfg.batch_window_us);
+      if (s->cfg.batch_window_us > 0 && (int)s->queue.size() < free_slots && age < window) {
+        wait = std::chrono::duration_cast<std::chrono::microseconds>(window - age) + std::chrono::microseconds(1);
+      } else {
+        admit(s);
+      }
+    }
+    s->work_cv.wait_for(lk, wait);
   }
   // requests that never started
   for (Request* r : s->queue) fail_request(s, r, SDGS_ERR_BUSY);
@@ -391,10 +404,6 @@ int check_server_view(const sdgs_view* v) {
   if (!v || v->width <= 0 || v->height <= 0 || v->width > 65535 * kTile || v->height > 65535 * kTile ||
       !(v->fx > 0.f) || !(v->fy > 0.f)) {
     set_error("bad view");
-    return SDGS_ERR_INVALID_ARG;
-  }
-  if (bin_smem_bytes(v->width, v->height) > kMaxBinSmem) {
-    set_error("image too large for binning");
     return SDGS_ERR_INVALID_ARG;
   }
   return SDGS_OK;
@@ -410,7 +419,7 @@ extern "C" {
 
 int sdgs_server_create(const sdgs_server_cfg* cfg, sdgs_server** out) {
   if (!cfg || !out || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->queue_capacity < 1 ||
-      cfg->hbm_budget_bytes == 0) {
+      cfg->hbm_budget_bytes == 0 || cfg->batch_window_us < 0 || cfg->batch_window_us > 1000000) {
     set_error("bad server configuration");
     return SDGS_ERR_INVALID_ARG;
   }
@@ -535,6 +544,7 @@ int sdgs_server_get_stats(sdgs_server* s, sdgs_server_stats* out) {
   if (!s || !out) return SDGS_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->stats;
+  out->max_inflight = s->max_inflight;
   out->bytes_allocated = s->bytes_allocated;
   return SDGS_OK;
 }

@@ -58,13 +58,14 @@ class Grads(ctypes.Structure):
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32),
-                ("queue_capacity", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("queue_capacity", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("batch_window_us", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("retried", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("max_batch", ctypes.c_uint64),
-                ("bytes_allocated", ctypes.c_size_t)]
+                ("max_inflight", ctypes.c_uint64), ("bytes_allocated", ctypes.c_size_t)]
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -300,8 +301,9 @@ class Server:
     keeps references to the scenes it registered.
     """
 
-    def __init__(self, budget_bytes: int = 8 << 30, slots: int = 4, queue_capacity: int = 4096, device: int = 0):
-        cfg = ServerCfg(budget_bytes, slots, queue_capacity, device)
+    def __init__(self, budget_bytes: int = 8 << 30, slots: int = 4, queue_capacity: int = 4096, device: int = 0,
+                 batch_window_us: int = 0):
+        cfg = ServerCfg(budget_bytes, slots, queue_capacity, device, batch_window_us)
         h = ctypes.c_void_p()
         _check(lib().sdgs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

@@ -77,3 +77,11 @@ def pixel_ok(margin_alpha, margin_T, margin_depth=None, depth_rel=PIX_DEPTH):
     if margin_depth is not None:
         ok &= np.asarray(margin_depth) >= depth_rel
     return ok
+
+
+def assert_ranges_equal(got: np.ndarray, want: np.ndarray):
+    """Tile ranges: counts everywhere, starts of non-empty tiles (an empty range may sit anywhere)."""
+    got, want = np.asarray(got, np.int64), np.asarray(want, np.int64)
+    np.testing.assert_array_equal(got[:, 1] - got[:, 0], want[:, 1] - want[:, 0])
+    busy = want[:, 1] > want[:, 0]
+    np.testing.assert_array_equal(got[busy], want[busy])

@@ -58,7 +58,7 @@ def _random_bin_cases():
         (5000, 256, 256, 3),     # one tile pass, several radix blocks of Gaussians
         (20000, 1352, 1014, 4),  # two tile passes (5440 tiles), K spans many blocks
         (3000, 1920, 1080, 5),   # 8160 tiles
-        (600_000, 800, 800, 6),  # > 128 radix blocks: depth passes with a separate histogram scan
+        (600_000, 800, 800, 6),  # hundreds of sort tiles in both sorts
     ]
 
 
@@ -67,20 +67,22 @@ def test_bin_sort_bit_exact_on_random_records(n, W, H, seed):
     rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=12 if n < 100_000 else 2)
     proj = U.sdgs.ProjectedBuffers.from_host(rec)
     view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5))
-    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], (W + 15) // 16)
+    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], (W + 15) // 16,
+                                     cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
     k, keys, vals, ranges, _ = U.gpu_bin(proj, view, capacity=len(okeys) + 7)
     assert k == len(okeys)
     np.testing.assert_array_equal(keys.astype(np.uint64), okeys >> np.uint64(32))
     np.testing.assert_array_equal(vals, ovals)
     tiles = ((W + 15) // 16) * ((H + 15) // 16)
-    np.testing.assert_array_equal(ranges, binning.tile_ranges(okeys, tiles))
+    U.assert_ranges_equal(ranges, binning.tile_ranges(okeys, tiles))
 
 
 def test_bin_sort_overflow_is_reported_and_safe():
     rec = synth.random_projected(2000, 256, 256, seed=7)
     proj = U.sdgs.ProjectedBuffers.from_host(rec)
     view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), 256, 256, 60.0, 0.5))
-    okeys, _ = binning.sort_keys(rec["depth"], rec["rect"], 16)
+    okeys, _ = binning.sort_keys(rec["depth"], rec["rect"], 16,
+                                 cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
     with pytest.raises(U.sdgs.SdgsError) as e:
         U.gpu_bin(proj, view, capacity=len(okeys) // 3)
     assert e.value.code == 3
@@ -92,6 +94,34 @@ def test_bin_sort_overflow_is_reported_and_safe():
     assert k == len(okeys)
 
 
+@pytest.mark.parametrize("frac", [5, 40])
+def test_bin_sort_overflow_keeps_the_nearest_instances(frac):
+    """With K > capacity the lists hold the first `capacity` instances in emission order (Gaussians
+    by (float32 depth, id), each rectangle's kept tiles row-major), sorted by tile.  A small
+    capacity also leaves the kept-tile bitmask too small for the later Gaussians, whose tiles are
+    then tested a second time while writing: both ways must give the same lists."""
+    W, H = 1352, 1014
+    rec = synth.random_projected(20000, W, H, seed=4, max_half_tiles=12)
+    proj = U.sdgs.ProjectedBuffers.from_host(rec)
+    view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5))
+    tile, gid = binning.instances(rec["rect"], (W + 15) // 16, cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
+    dbits = np.asarray(rec["depth"], np.float32).view(np.uint32)
+    emitted = np.argsort(dbits[gid], kind="stable")  # Gaussian-id order, then rows, kept among ties
+    cap = len(tile) // frac
+    first = emitted[:cap]
+    by_tile = first[np.argsort(tile[first], kind="stable")]
+    bins = U.sdgs.BinBuffers(proj.n, cap, W, H)
+    with pytest.raises(U.sdgs.SdgsError) as e:
+        U.sdgs.bin_sort(proj, view, bins, sync=True)
+    assert e.value.code == 3
+    np.testing.assert_array_equal(bins.point_list.cpu().numpy().view(np.uint32), gid[by_tile])
+    np.testing.assert_array_equal(bins.tile_keys.cpu().numpy().view(np.uint32), tile[by_tile])
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    keys = tile[by_tile].astype(np.uint64) << np.uint64(32)
+    U.assert_ranges_equal(bins.ranges.cpu().numpy().view(np.uint32).astype(np.int64),
+                          binning.tile_ranges(keys, tiles))
+
+
 @pytest.mark.parametrize("ci", [0, 1, 2])
 def test_bin_and_render_on_oracle_records(scene0, ci):
     """Binning + compositing given the oracle's float32-rounded screen-space records."""
@@ -101,7 +131,8 @@ def test_bin_and_render_on_oracle_records(scene0, ci):
     proj = U.sdgs.ProjectedBuffers.from_host(rec)
     view = U.sdgs.view_struct(cam)
     k, keys, vals, ranges, bins = U.gpu_bin(proj, view)
-    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], cam.tiles_x)
+    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], cam.tiles_x,
+                                     cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
     assert k == len(okeys) and k > 0
     np.testing.assert_array_equal(vals, ovals)
     np.testing.assert_array_equal(keys.astype(np.uint64), okeys >> np.uint64(32))
@@ -141,4 +172,7 @@ def test_render_end_to_end_against_fp64_oracle(scene0, ci):
     assert ok.mean() > 0.9, ok.mean()
     err = np.abs(img - ref["image"].numpy()).max(-1)
     assert err[ok].max() <= COLOUR_TOL, err[ok].max()
-    np.testing.assert_array_equal(nc[ok], ref["n_contrib"].numpy()[ok])
+    # n_contrib counts list positions: equal wherever both sides' tile lists hold the same entries
+    # (they may differ by Gaussians on the reachability boundary, which reach no pixel)
+    match = np.mean(nc[ok] == ref["n_contrib"].numpy()[ok])
+    assert match > 0.99, match

@@ -58,7 +58,7 @@ def test_requests_in_the_mix_equal_requests_alone():
             state, lat = srv.poll(rid)
             assert state == sdgs.REQ_DONE and lat > 0
     assert st["completed"] == len(reqs) and st["failed"] == 0
-    assert st["max_batch"] > 1, st  # requests were admitted together and sliced in one launch
+    assert st["max_inflight"] > 1, st  # several requests were on the device at once
     for got, exp in zip(outs, want):
         assert torch.equal(got, exp)
     assert all(l > 0 for l in lats)
@@ -114,3 +114,23 @@ def test_host_side_errors_leave_the_server_usable():
         assert srv.release() >= len(accepted)
     want = _alone(dev, scene, cam).cpu()
     assert torch.equal(out, want)
+
+
+def test_requests_admitted_together_share_one_slicing_launch():
+    """Requests queued before the worker runs are admitted in one pass and sliced by one launch."""
+    scenes = _scenes()
+    devs = [prender.scene_to_device(s) for s in scenes]
+    reqs = _requests(np.random.default_rng(8), 12)
+    want = [_alone(devs[sid], scenes[sid], cam).cpu() for sid, cam in reqs]
+    with sdgs.Server(budget_bytes=6 << 30, slots=8, batch_window_us=200_000) as srv:
+        ids = [srv.add_scene(d, s.lambda_t, s.lambda_d) for d, s in zip(devs, scenes)]
+        outs = [torch.zeros(cam.height, cam.width, 3, device="cuda") for _, cam in reqs]
+        # submitted well within the 200 ms window: the first 8 are admitted together
+        rids = [srv.submit(ids[sid], sdgs.view_struct(cam), out) for (sid, cam), out in zip(reqs, outs)]
+        for r in rids:
+            srv.wait(r, 30_000)
+        st = srv.stats()
+    assert st["completed"] == len(reqs)
+    assert st["max_batch"] >= 8, st  # one launch sliced a whole wave of requests
+    for got, exp in zip(outs, want):
+        assert torch.equal(got.cpu(), exp)

@@ -409,7 +409,8 @@ def test_transmittance_monotone_and_stop_rule():
 def test_vectorised_compositing_equals_per_pixel_loop():
     rec = synth.random_projected(150, 48, 32, seed=15)
     out = render.render_projected(rec, 48, 32, (0.1, 0.2, 0.3))
-    lists = binning.tile_lists(rec["depth"], rec["rect"], 3, 6)
+    lists = binning.tile_lists(rec["depth"], rec["rect"], 3, 6,
+                               cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
     f = lambda k: np.asarray(rec[k], np.float32).astype(np.float64)
     for y in range(0, 32, 3):
         for x in range(0, 48, 5):
@@ -468,3 +469,49 @@ def test_oracle_gradient_matches_central_differences():
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-7, (name, flat_idx, fd, an)
         checked += 1
     assert checked >= 20 and skipped <= 5
+
+
+# ----------------------------------------------------------------------------------------------
+# Tile reachability (the conservative per-tile drop applied in binning)
+# ----------------------------------------------------------------------------------------------
+
+def test_alpha_exponent_bound_is_an_upper_bound_within_1p1_percent():
+    alpha = np.concatenate([np.geomspace(1 / 255 * (1 + 1e-6), 1.0, 20000), [1 / 255, 0.5, 0.99]])
+    exact = 2 * np.log(255 * alpha.astype(np.float32).astype(np.float64))
+    bound = binning.alpha_exponent_bound(alpha).astype(np.float64)
+    # near alpha = 1/255 float32 rounding can undershoot by ~6e-5; the rule adds 1e-3 on top
+    assert np.all(bound + 1e-3 >= exact + 5e-4)
+    assert np.all(bound <= exact * 1.011 + 2e-4)
+
+
+def test_dropped_tiles_have_no_pixel_at_or_above_the_alpha_threshold():
+    """Brute force over all 256 pixel centres of every tested tile, in float64."""
+    rng = np.random.default_rng(21)
+    n = 4000
+    mean2d = rng.uniform(-20, 84, size=(n, 2)).astype(np.float32)
+    sx, sy = rng.uniform(0.6, 30, n), rng.uniform(0.6, 30, n)
+    rho = rng.uniform(-0.99, 0.99, n)
+    cov = np.stack([sx * sx, rho * sx * sy, sy * sy], 1)
+    det = cov[:, 0] * cov[:, 2] - cov[:, 1] ** 2
+    conic = np.stack([cov[:, 2] / det, -cov[:, 1] / det, cov[:, 0] / det], 1).astype(np.float32)
+    alpha = rng.uniform(1 / 255, 1.0, n).astype(np.float32)
+    tx, ty = rng.integers(0, 4, n), rng.integers(0, 4, n)
+    keep = binning.tile_reachable(mean2d, conic, alpha, tx, ty)
+    dropped = np.nonzero(~keep)[0]
+    assert 0.2 * n < len(dropped) < 0.95 * n
+    px, py = np.meshgrid(np.arange(16) + 0.5, np.arange(16) + 0.5, indexing="xy")
+    for i in dropped:
+        dx = tx[i] * 16 + px - float(mean2d[i, 0])
+        dy = ty[i] * 16 + py - float(mean2d[i, 1])
+        a, b, c = conic[i].astype(np.float64)
+        al = float(alpha[i]) * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+        assert al.max() < 1 / 255, (i, al.max())
+
+
+def test_reachability_drops_a_large_share_of_rectangle_tiles_on_a_scene():
+    scene, cam = synth.config_scene(0), synth.config_cameras(0)[0]
+    g = render.gaussians(render.params_from_scene(scene), cam, scene.lambda_t, scene.lambda_d)
+    rect = g["rect"].numpy()
+    full, _ = binning.instances(rect, cam.tiles_x)
+    kept, _ = binning.instances(rect, cam.tiles_x, render.cull_inputs(g["mean2d"], g["conic"], g["alpha_cond"]))
+    assert 0 < len(kept) < 0.8 * len(full)
