@@ -69,6 +69,10 @@ typedef struct sdgs_scene {
   int32_t sh_degree; /* must be 3 */
   float lambda_t;
   float lambda_d;
+  int32_t dir_mode;  /* conditioning direction d: 0 = the request's view direction (sdgs_view.d);
+                        1 = per Gaussian, the unit vector from the camera centre to its mu_p (the
+                        6DGS-style reading of "view direction", Sec. 3); gradients then flow
+                        through d into mu_p */
 } sdgs_scene;
 
 /* One render request: camera, query time t and conditioning view direction d (Sec. 4.2).
@@ -132,6 +136,7 @@ typedef struct sdgs_grads {
   float* dL28;
   float* dopacity;
   float* dsh;
+  float* dlambda; /* [2] d/d(lambda_t, lambda_d), accumulated (+=) like the others; may be NULL */
 } sdgs_grads;
 
 /* Library version string, e.g. "sdgs 0.1.0 sm_103a". */
@@ -220,6 +225,37 @@ int sdgs_render_bwd(const sdgs_scene* scene, const sdgs_view* view, const sdgs_p
                     const sdgs_bins* bins, const float* final_T, const uint32_t* n_contrib,
                     const float* dL_dimage, void* workspace, size_t workspace_bytes,
                     const sdgs_grads* grads, void* stream);
+
+/* Densification statistics (Algorithm 1 step 7 and Sec. 4.4), per Gaussian at the view's (t, d):
+ *   scale  [n][3]  S = sqrt of the eigenvalues of Sigma_cond (= its singular values), descending
+ *   rot    [n][9]  R row-major, columns the matching unit axes (Sigma_cond = R diag(S)^2 R^T),
+ *                  last column multiplied by sign(det R) so that det R = +1; the sign of each
+ *                  axis is otherwise arbitrary
+ *   pt_norm  [n]   |Sigma_pt|, the norm of the space-time coupling block
+ *   t_scale  [n]   sqrt(Sigma_t), the temporal scale (time normalised to [0, 1])
+ *   split    [n]   uint8: pt_norm > split_pt * extent and t_scale > split_t
+ *   prune    [n]   uint8: base opacity < prune_alpha
+ * Any output pointer may be NULL (not written).  All device memory, caller-allocated.
+ * The paper's thresholds: split_pt = 0.05 (relative to the scene extent), split_t = 0.25,
+ * prune_alpha = tau_min = 0.01.  Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_CUDA. */
+typedef struct sdgs_densify_cfg {
+  float extent;
+  float split_pt;
+  float split_t;
+  float prune_alpha;
+} sdgs_densify_cfg;
+
+typedef struct sdgs_densify {
+  float* scale;
+  float* rot;
+  float* pt_norm;
+  float* t_scale;
+  uint8_t* split;
+  uint8_t* prune;
+} sdgs_densify;
+
+int sdgs_densify_stats(const sdgs_scene* scene, const sdgs_view* view, const sdgs_densify_cfg* cfg,
+                       const sdgs_densify* out, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Render server.  The paper has no serving component; this realises "render requests over

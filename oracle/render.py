@@ -28,10 +28,10 @@ def params_from_scene(scene, requires_grad: bool = False) -> dict:
     return p
 
 
-def gaussians(params: dict, cam, lambda_t: float, lambda_d: float) -> dict:
+def gaussians(params: dict, cam, lambda_t, lambda_d, dir_mode: int = 0) -> dict:
     """Per-Gaussian slicing, modulation, projection, radius, tile rectangle, colour, visibility."""
     sl = slicing.slice_gaussians(params["mean7"], params["L28"], params["opacity"], cam.t, cam.d,
-                                 lambda_t, lambda_d)
+                                 lambda_t, lambda_d, dir_mode, np.asarray(cam.center))
     pr = projection.project(sl["mu_cond"], sl["Sigma_cond"], cam)
     centre = torch.as_tensor(np.asarray(cam.center), dtype=F64)
     diff = sl["mu_cond"] - centre
@@ -106,7 +106,7 @@ def composite_all(mean2d, conic, alpha, rgb, depth, rect, cam, bg, tiles=None) -
 def render(scene, cam, tiles=None, params: dict | None = None) -> dict:
     """Full-image (or listed-tile) render of a scene; returns image [H, W, 3] and per-Gaussian data."""
     p = params if params is not None else params_from_scene(scene)
-    g = gaussians(p, cam, scene.lambda_t, scene.lambda_d)
+    g = gaussians(p, cam, scene.lambda_t, scene.lambda_d, scene.dir_mode)
     bg = torch.as_tensor(cam.bg, dtype=F64)
     out = composite_all(g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], g["depth"], g["rect"],
                         cam, bg, tiles)
@@ -165,7 +165,8 @@ def render_projected(rec: dict, width: int, height: int, bg, tiles=None) -> dict
 
 
 def vjp(scene, cam, dL_dimage: np.ndarray, tiles=None) -> dict:
-    """Gradients of sum(dL_dimage * image) w.r.t. mean7, L28, opacity, sh (float64).
+    """Gradients of sum(dL_dimage * image) w.r.t. mean7, L28, opacity, sh and (lambda_t,
+    lambda_d), in float64.
 
     The visible set is found first without gradients; the forward is then re-run on the
     visible Gaussians only, so culled Gaussians receive exactly zero gradient.  With `tiles`,
@@ -173,11 +174,12 @@ def vjp(scene, cam, dL_dimage: np.ndarray, tiles=None) -> dict:
     """
     p0 = params_from_scene(scene)
     with torch.no_grad():
-        vis = gaussians(p0, cam, scene.lambda_t, scene.lambda_d)["visible"]
+        vis = gaussians(p0, cam, scene.lambda_t, scene.lambda_d, scene.dir_mode)["visible"]
     idx = torch.nonzero(vis).reshape(-1)
     leaf = params_from_scene(scene, requires_grad=True)
+    lam = torch.tensor([scene.lambda_t, scene.lambda_d], dtype=F64, requires_grad=True)
     sub = {k: v[idx] for k, v in leaf.items()}
-    g = gaussians(sub, cam, scene.lambda_t, scene.lambda_d)
+    g = gaussians(sub, cam, lam[0], lam[1], scene.dir_mode)
     bg = torch.as_tensor(cam.bg, dtype=F64)
     out = composite_all(g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], g["depth"], g["rect"],
                         cam, bg, tiles)
@@ -185,4 +187,4 @@ def vjp(scene, cam, dL_dimage: np.ndarray, tiles=None) -> dict:
     loss.backward()
     return dict(mean7=leaf["mean7"].grad.numpy(), L28=leaf["L28"].grad.numpy(),
                 opacity=leaf["opacity"].grad.numpy(), sh=leaf["sh"].grad.numpy(),
-                image=out["image"].detach().numpy(), loss=float(loss.detach()))
+                lam=lam.grad.numpy(), image=out["image"].detach().numpy(), loss=float(loss.detach()))

@@ -12,6 +12,11 @@ Follows Sec. 4.1-4.2 literally:
     f_dir  = exp(-1/2 lambda_d (d - mu_d)^T Sigma_d^{-1} (d - mu_d))             (Eq. dir_mod)
     alpha_cond = alpha f_temp f_dir                                              (Algorithm 1 step 6)
   The modulation uses the marginal Sigma_t and Sigma_d blocks of Sigma, exactly as printed.
+
+The conditioning direction d is the request's view direction, or (dir_mode = 1, the 6DGS-style
+reading of "view direction", Sec. 3) each Gaussian's own unit direction from the camera centre
+to its spatial mean mu_p; then d depends on mu_p and gradients flow through it.  lambda_t and
+lambda_d may be tensors that require gradients.
 """
 from __future__ import annotations
 
@@ -48,7 +53,7 @@ def condition(mean7: torch.Tensor, Sigma: torch.Tensor, t: float, d) -> tuple[to
     """Eq. cond_mean and Eq. cond_cov with an explicit inverse of Sigma_{(t,d)}."""
     S_p, S_p_td, S_td = partition(Sigma)
     S_td_inv = torch.linalg.inv(S_td)
-    d = torch.as_tensor(d, dtype=mean7.dtype).reshape(1, 3)
+    d = torch.as_tensor(d, dtype=mean7.dtype).reshape(-1, 3)  # one direction, or one per Gaussian
     dev = torch.cat([t - mean7[:, 3:4], d - mean7[:, 4:7]], dim=1)  # (t - mu_t, d - mu_d)
     gain = S_p_td @ S_td_inv
     mu_cond = mean7[:, 0:3] + (gain @ dev.unsqueeze(-1)).squeeze(-1)
@@ -63,15 +68,26 @@ def modulation(mean7: torch.Tensor, Sigma: torch.Tensor, t: float, d, lambda_t: 
     S_d = Sigma[:, 4:7, 4:7]
     dt = t - mean7[:, 3]
     f_temp = torch.exp(-0.5 * lambda_t * dt * dt / S_t)
-    d = torch.as_tensor(d, dtype=mean7.dtype).reshape(1, 3)
+    d = torch.as_tensor(d, dtype=mean7.dtype).reshape(-1, 3)
     dd = d - mean7[:, 4:7]
     q = (dd.unsqueeze(1) @ torch.linalg.inv(S_d) @ dd.unsqueeze(-1)).reshape(-1)
     f_dir = torch.exp(-0.5 * lambda_d * q)
     return f_temp, f_dir
 
 
-def slice_gaussians(mean7, L28, opacity, t: float, d, lambda_t: float, lambda_d: float) -> dict:
+def gaussian_directions(mean7: torch.Tensor, center) -> torch.Tensor:
+    """Unit direction from the camera centre to each spatial mean mu_p (dir_mode = 1)."""
+    w = mean7[:, 0:3] - torch.as_tensor(center, dtype=mean7.dtype).reshape(1, 3)
+    return w / torch.linalg.norm(w, dim=1, keepdim=True)
+
+
+def slice_gaussians(mean7, L28, opacity, t: float, d, lambda_t, lambda_d, dir_mode: int = 0,
+                    center=None) -> dict:
     """Algorithm 1 steps 3-6 for every Gaussian (no adaptive refinement)."""
+    if dir_mode == 1:
+        d = gaussian_directions(mean7, center)
+    elif dir_mode != 0:
+        raise ValueError("dir_mode must be 0 or 1")
     Sigma = covariance(unpack_L(L28))
     mu_cond, Sigma_cond = condition(mean7, Sigma, t, d)
     f_temp, f_dir = modulation(mean7, Sigma, t, d, lambda_t, lambda_d)

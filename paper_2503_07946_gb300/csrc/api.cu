@@ -34,6 +34,7 @@ static int check_scene(const sdgs_scene* s) {
     return SDGS_ERR_INVALID_ARG;
   }
   if (s->sh_degree != 3) { set_error("sh_degree must be 3 (got %d)", s->sh_degree); return SDGS_ERR_INVALID_ARG; }
+  if (s->dir_mode != 0 && s->dir_mode != 1) { set_error("dir_mode must be 0 or 1 (got %d)", s->dir_mode); return SDGS_ERR_INVALID_ARG; }
   if (!(s->lambda_t >= 0.f) || !(s->lambda_d >= 0.f) || !std::isfinite(s->lambda_t) ||
       !std::isfinite(s->lambda_d)) {
     set_error("lambda_t / lambda_d must be finite and >= 0");
@@ -248,6 +249,25 @@ int sdgs_render_fwd(const sdgs_projected* proj, const sdgs_bins* bins, const sdg
                      "render_fwd launch");
 }
 
+int sdgs_densify_stats(const sdgs_scene* scene, const sdgs_view* view, const sdgs_densify_cfg* cfg,
+                       const sdgs_densify* out, void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_scene(scene));
+  SDGS_TRY(check_view(view));
+  if (cfg == nullptr || out == nullptr) { set_error("densify cfg / outputs are NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (!std::isfinite(cfg->extent) || !std::isfinite(cfg->split_pt) || !std::isfinite(cfg->split_t) ||
+      !std::isfinite(cfg->prune_alpha)) {
+    set_error("densify thresholds must be finite");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if ((out->scale && !aligned(out->scale, 4)) || (out->rot && !aligned(out->rot, 4)) ||
+      (out->pt_norm && !aligned(out->pt_norm, 4)) || (out->t_scale && !aligned(out->t_scale, 4))) {
+    set_error("densify outputs misaligned");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  return cuda_status(launch_densify(*scene, *view, *cfg, *out, (cudaStream_t)stream), "densify launch");
+}
+
 int sdgs_bwd_workspace_size(int64_t n, size_t* bytes) {
   g_error[0] = 0;
   if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 31)) { set_error("bad arguments to sdgs_bwd_workspace_size"); return SDGS_ERR_INVALID_ARG; }
@@ -270,6 +290,7 @@ int sdgs_render_bwd(const sdgs_scene* scene, const sdgs_view* view, const sdgs_p
     set_error("backward input or gradient pointer is NULL");
     return SDGS_ERR_INVALID_ARG;
   }
+  if (grads->dlambda != nullptr && !aligned(grads->dlambda, 4)) { set_error("dlambda misaligned"); return SDGS_ERR_INVALID_ARG; }
   const size_t need = bwd_workspace_bytes(scene->n);
   if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) {
     set_error("backward workspace needs %zu bytes, 256-byte aligned", need);

@@ -165,6 +165,7 @@ struct GeomBwdArgs {
   float* dL28;
   float* dopacity;
   float* dsh;
+  float* dlambda;  // [2] or NULL
 };
 
 // For X = Lw^-1 Y with Lw lower triangular n x n (n = 3 or 4), given dX returns dY = Lw^-T dX.
@@ -179,11 +180,29 @@ __device__ __forceinline__ void solve_upper_T(const float Lw[N][N], const float 
   }
 }
 
+// One visible Gaussian's adjoint; returns its d/d(lambda_t, lambda_d) in *dlt, *dld.
+__device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, float* dlt, float* dld);
+
 __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
   const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
-  if (i >= a.n) return;
-  const ushort4 rc = a.rect[i];
-  if (!(rc.z > rc.x && rc.w > rc.y)) return;
+  float dlt = 0.f, dld = 0.f;
+  if (i < a.n) {
+    const ushort4 rc = a.rect[i];
+    if (rc.z > rc.x && rc.w > rc.y) geom_bwd_one(a, i, &dlt, &dld);
+  }
+  if (a.dlambda == nullptr) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dlt += __shfl_xor_sync(0xffffffffu, dlt, o);
+    dld += __shfl_xor_sync(0xffffffffu, dld, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (dlt != 0.f || dld != 0.f)) {
+    atomicAdd(a.dlambda, dlt);
+    atomicAdd(a.dlambda + 1, dld);
+  }
+}
+
+__device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, float* dlt, float* dld) {
 
   float L[28];
 #pragma unroll
@@ -197,7 +216,9 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
   const float drgb[3] = {gp[6], gp[7], gp[8]};
 
   SliceState s;
-  const float alpha_c = slice_one(L, m, alpha, a.q, s);
+  float rnd;
+  const Query q = query_for(a.q, m, &rnd);
+  const float alpha_c = slice_one(L, m, alpha, q, s);
   ProjState ps;
   project_one(a.cam, s, ps);
   const Camera& cam = a.cam;
@@ -334,6 +355,7 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
   for (int k = 0; k < 3; ++k) dm[k] += dmu[k];
 #pragma unroll
   for (int k = 0; k < 4; ++k) dm[3 + k] -= Hd[k];
+  float ded[3] = {Hd[1], Hd[2], Hd[3]};  // gradient w.r.t. the conditioning direction d
   // G: gradient w.r.t. the symmetric 7x7 Sigma (order p, t, d), then dL = 2 G L.
   float G[7][7];
 #pragma unroll
@@ -374,18 +396,23 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
     const float ft = expf(s.e_t), fd = expf(s.e_d);
     a.dopacity[i] += dalc * ft * fd;
     const float de_ = dalc * alpha_c;  // d alpha_c / d e_t = d alpha_c / d e_d = alpha_c
-    const float e0 = a.q.t - m[3];
+    const float e0 = q.t - m[3];
     // e_t = -1/2 lambda_t e0^2 / S_t
-    dm[3] += de_ * a.q.lambda_t * e0 / s.St;
-    const float dSt = de_ * 0.5f * a.q.lambda_t * e0 * e0 / (s.St * s.St);
+    dm[3] += de_ * q.lambda_t * e0 / s.St;
+    *dlt = de_ * (-0.5f * e0 * e0 / s.St);
+    const float dSt = de_ * 0.5f * q.lambda_t * e0 * e0 / (s.St * s.St);
 #pragma unroll
     for (int k = 0; k < 4; ++k) dLg[6 + k] += 2.f * dSt * L[6 + k];
     // e_d = -1/2 lambda_d q, q = delta^T Sigma_d^-1 delta = |y|^2, y = C^-1 delta
-    const float dq = -0.5f * a.q.lambda_d * de_;
+    const float dq = -0.5f * q.lambda_d * de_;
+    *dld = de_ * (-0.5f * (s.y[0] * s.y[0] + s.y[1] * s.y[1] + s.y[2] * s.y[2]));
     float w[3];
     solve_upper_T<3>(s.C, s.y, w);  // w = C^-T y = Sigma_d^-1 delta
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dm[4 + k] -= 2.f * dq * w[k];
+    for (int k = 0; k < 3; ++k) {
+      dm[4 + k] -= 2.f * dq * w[k];
+      ded[k] += 2.f * dq * w[k];
+    }
     // d Sigma_d = -dq w w^T; d L_d = 2 dSigma_d L_d on the stored (lower) entries of rows 4..6
     const int row0[3] = {10, 15, 21};
     const int len[3] = {5, 6, 7};
@@ -401,6 +428,13 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
         dLg[row0[ra] + k] += -2.f * dq * w[ra] * acc;
       }
     }
+  }
+
+  // ---- d = (mu_p - campos) / |mu_p - campos| (dir_mode = 1): dmu_p += (I - d d^T) ded / |w| ----
+  if (q.dir_mode == 1) {
+    const float dot = ded[0] * q.d[0] + ded[1] * q.d[1] + ded[2] * q.d[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dm[k] += (ded[k] - dot * q.d[k]) * rnd;
   }
 
 #pragma unroll
@@ -444,7 +478,7 @@ cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdg
   a.cam = make_camera(v);
   a.rect = reinterpret_cast<const ushort4*>(p.rect);
   a.g2 = g2;
-  a.dmean7 = g.dmean7; a.dL28 = g.dL28; a.dopacity = g.dopacity; a.dsh = g.dsh;
+  a.dmean7 = g.dmean7; a.dL28 = g.dL28; a.dopacity = g.dopacity; a.dsh = g.dsh; a.dlambda = g.dlambda;
   geom_bwd_kernel<<<(unsigned)((s.n + 127) / 128), 128, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -57,6 +57,8 @@ cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const
                               uint64_t* n_evaluated, cudaStream_t st);
 
 size_t bwd_workspace_bytes(int64_t n);
+cudaError_t launch_densify(const sdgs_scene& s, const sdgs_view& v, const sdgs_densify_cfg& cfg,
+                           const sdgs_densify& out, cudaStream_t st);
 cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& p,
                               const sdgs_bins& b, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, char* ws, const sdgs_grads& g,

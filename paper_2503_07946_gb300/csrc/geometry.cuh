@@ -33,7 +33,23 @@ struct Query {
   float t;
   float d[3];
   float lambda_t, lambda_d;
+  int dir_mode;       // 1: d is each Gaussian's unit direction from campos to its mu_p
+  float campos[3];
 };
+
+// The query Gaussian m is conditioned on: the request's, or with dir_mode = 1 its own
+// direction d = (mu_p - campos) / |mu_p - campos|; *rn gets 1 / |mu_p - campos|.
+__device__ __forceinline__ Query query_for(const Query& q, const float m[7], float* rn) {
+  Query r = q;
+  *rn = 0.f;
+  if (q.dir_mode == 1) {
+    const float w0 = m[0] - q.campos[0], w1 = m[1] - q.campos[1], w2 = m[2] - q.campos[2];
+    const float inv = 1.f / sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+    r.d[0] = w0 * inv; r.d[1] = w1 * inv; r.d[2] = w2 * inv;
+    *rn = inv;
+  }
+  return r;
+}
 
 // Real SH constants of degree <= 3 (the standard Cartesian table, with the Condon-Shortley
 // phase carried as the sign of the m != 0 entries).

@@ -56,7 +56,9 @@ __device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i)
   const float alpha = __ldg(a.opacity + i);
 
   SliceState s;
-  const float alpha_c = slice_one(L, m, alpha, a.q, s);
+  float rnd;
+  const Query qi = query_for(a.q, m, &rnd);
+  const float alpha_c = slice_one(L, m, alpha, qi, s);
   ProjState ps;
   bool keep = alpha_c >= kAlphaMin && project_one(a.cam, s, ps);
   float u = 0.f, v = 0.f, r = 0.f;
@@ -138,6 +140,9 @@ Query make_query(const sdgs_scene& s, const sdgs_view& v) {
   q.d[0] = v.d[0]; q.d[1] = v.d[1]; q.d[2] = v.d[2];
   q.lambda_t = s.lambda_t;
   q.lambda_d = s.lambda_d;
+  q.dir_mode = s.dir_mode;
+  const Camera c = make_camera(v);
+  q.campos[0] = c.campos[0]; q.campos[1] = c.campos[1]; q.campos[2] = c.campos[2];
   return q;
 }
 

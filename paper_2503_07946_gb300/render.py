@@ -68,20 +68,20 @@ class Renderer:
 
 
 class Render7DGS(torch.autograd.Function):
-    """image = render(mean7, L28, opacity, sh) for one view, with the CUDA adjoint as backward.
+    """image = render(mean7, L28, opacity, sh, lam) for one view, with the CUDA adjoint as backward.
 
-    Gradients flow to all four parameter tensors; opacity is the activated alpha and L28 the
-    packed Cholesky factor as given (activations live in torch).
+    Gradients flow to all four parameter tensors and to lam = (lambda_t, lambda_d); opacity is
+    the activated alpha and L28 the packed Cholesky factor as given (activations live in torch).
     """
 
     @staticmethod
-    def forward(ctx, mean7, L28, opacity, sh, view: sdgs.View, lambda_t: float, lambda_d: float,
-                renderer: Renderer):
+    def forward(ctx, mean7, L28, opacity, sh, lam, view: sdgs.View, renderer: Renderer, dir_mode: int):
         t = dict(mean7=mean7.contiguous(), L28=L28.contiguous(), opacity=opacity.contiguous(),
                  sh=sh.contiguous())
-        scene = sdgs.scene_struct(t, lambda_t, lambda_d)
+        lam_t, lam_d = (float(x) for x in lam.detach().cpu().tolist())
+        scene = sdgs.scene_struct(t, lam_t, lam_d, dir_mode)
         image = renderer.forward(scene, view).clone()
-        ctx.renderer, ctx.view, ctx.lam = renderer, view, (lambda_t, lambda_d)
+        ctx.renderer, ctx.view, ctx.lam, ctx.dir_mode = renderer, view, (lam_t, lam_d), dir_mode
         ctx.final_T = renderer.final_T.clone()
         ctx.n_contrib = renderer.n_contrib.clone()
         ctx.save_for_backward(t["mean7"], t["L28"], t["opacity"], t["sh"])
@@ -91,15 +91,20 @@ class Render7DGS(torch.autograd.Function):
     def backward(ctx, grad_image):
         mean7, L28, opacity, sh = ctx.saved_tensors
         t = dict(mean7=mean7, L28=L28, opacity=opacity, sh=sh)
-        scene = sdgs.scene_struct(t, *ctx.lam)
+        scene = sdgs.scene_struct(t, *ctx.lam, ctx.dir_mode)
         grads = {k: torch.zeros_like(v) for k, v in t.items()}
+        grads["lam"] = torch.zeros(2, dtype=torch.float32, device=mean7.device)
         r = ctx.renderer
         ws = torch.empty(max(sdgs.bwd_workspace_size(r.n), 256), dtype=torch.uint8, device=mean7.device)
         sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, ctx.final_T, ctx.n_contrib,
                         grad_image.contiguous(), ws, grads)
-        return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], None, None, None, None
+        return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], grads["lam"], None, None, None
 
 
-def render_image(mean7, L28, opacity, sh, view: sdgs.View, lambda_t: float, lambda_d: float,
-                 renderer: Renderer) -> torch.Tensor:
-    return Render7DGS.apply(mean7, L28, opacity, sh, view, lambda_t, lambda_d, renderer)
+def render_image(mean7, L28, opacity, sh, view: sdgs.View, lambda_t, lambda_d, renderer: Renderer,
+                 dir_mode: int = 0) -> torch.Tensor:
+    """lambda_t, lambda_d: floats or 0-d tensors (gradients reach tensors that require them)."""
+    dev = mean7.device
+    lam = torch.stack([torch.as_tensor(lambda_t, dtype=torch.float32, device=dev).reshape(()),
+                       torch.as_tensor(lambda_d, dtype=torch.float32, device=dev).reshape(())])
+    return Render7DGS.apply(mean7, L28, opacity, sh, lam, view, renderer, dir_mode)

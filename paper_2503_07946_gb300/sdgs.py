@@ -30,7 +30,7 @@ class SdgsError(RuntimeError):
 class Scene(ctypes.Structure):
     _fields_ = [("mean7", ctypes.c_void_p), ("L28", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
                 ("sh", ctypes.c_void_p), ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
-                ("lambda_t", ctypes.c_float), ("lambda_d", ctypes.c_float)]
+                ("lambda_t", ctypes.c_float), ("lambda_d", ctypes.c_float), ("dir_mode", ctypes.c_int32)]
 
 
 class View(ctypes.Structure):
@@ -53,7 +53,17 @@ class Bins(ctypes.Structure):
 
 class Grads(ctypes.Structure):
     _fields_ = [("dmean7", ctypes.c_void_p), ("dL28", ctypes.c_void_p), ("dopacity", ctypes.c_void_p),
-                ("dsh", ctypes.c_void_p)]
+                ("dsh", ctypes.c_void_p), ("dlambda", ctypes.c_void_p)]
+
+
+class DensifyCfg(ctypes.Structure):
+    _fields_ = [("extent", ctypes.c_float), ("split_pt", ctypes.c_float), ("split_t", ctypes.c_float),
+                ("prune_alpha", ctypes.c_float)]
+
+
+class Densify(ctypes.Structure):
+    _fields_ = [("scale", ctypes.c_void_p), ("rot", ctypes.c_void_p), ("pt_norm", ctypes.c_void_p),
+                ("t_scale", ctypes.c_void_p), ("split", ctypes.c_void_p), ("prune", ctypes.c_void_p)]
 
 
 class ServerCfg(ctypes.Structure):
@@ -92,6 +102,8 @@ SIGNATURES = {
                          ctypes.POINTER(Bins), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(Grads), ctypes.c_void_p],
                         ctypes.c_int),
+    "sdgs_densify_stats": ([ctypes.POINTER(Scene), ctypes.POINTER(View), ctypes.POINTER(DensifyCfg),
+                            ctypes.POINTER(Densify), ctypes.c_void_p], ctypes.c_int),
     "sdgs_server_create": ([ctypes.POINTER(ServerCfg), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "sdgs_server_add_scene": ([ctypes.c_void_p, ctypes.POINTER(Scene), ctypes.POINTER(ctypes.c_int32)],
                               ctypes.c_int),
@@ -147,14 +159,16 @@ def _stream(stream) -> int | None:
 # Struct builders
 # ------------------------------------------------------------------------------------------
 
-def scene_struct(t: dict, lambda_t: float, lambda_d: float) -> Scene:
-    """t: dict of CUDA float32 tensors mean7 [N,7], L28 [N,28], opacity [N], sh [N,16,3]."""
+def scene_struct(t: dict, lambda_t: float, lambda_d: float, dir_mode: int = 0) -> Scene:
+    """t: dict of CUDA float32 tensors mean7 [N,7], L28 [N,28], opacity [N], sh [N,16,3].
+    dir_mode 0 conditions on the view's direction d, 1 on each Gaussian's direction from the
+    camera centre."""
     n = t["mean7"].shape[0]
     for k, w in (("mean7", 7), ("L28", 28), ("opacity", 1), ("sh", 48)):
         if t[k].dtype != torch.float32 or t[k].numel() != n * w:
             raise ValueError(f"scene tensor {k} must be float32 with {w} values per Gaussian")
     return Scene(_ptr(t["mean7"]), _ptr(t["L28"]), _ptr(t["opacity"]), _ptr(t["sh"]), n, 3,
-                 float(lambda_t), float(lambda_d))
+                 float(lambda_t), float(lambda_d), int(dir_mode))
 
 
 def view_struct(cam) -> View:
@@ -288,10 +302,28 @@ def bwd_workspace_size(n: int) -> int:
 def render_bwd(scene: Scene, view: View, proj: ProjectedBuffers, bins: BinBuffers, final_T: torch.Tensor,
                n_contrib: torch.Tensor, dL_dimage: torch.Tensor, workspace: torch.Tensor, grads: dict,
                stream=None):
-    g = Grads(_ptr(grads["mean7"]), _ptr(grads["L28"]), _ptr(grads["opacity"]), _ptr(grads["sh"]))
+    g = Grads(_ptr(grads["mean7"]), _ptr(grads["L28"]), _ptr(grads["opacity"]), _ptr(grads["sh"]),
+              _ptr(grads.get("lam")))
     _check(lib().sdgs_render_bwd(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(proj.struct()),
                                  ctypes.byref(bins.struct()), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
                                  _ptr(workspace), workspace.numel(), ctypes.byref(g), _stream(stream)))
+
+
+def densify_stats(scene: Scene, view: View, n: int, extent: float, split_pt: float = 0.05, split_t: float = 0.25,
+                  prune_alpha: float = 0.01, stream=None) -> dict:
+    """sdgs_densify_stats into fresh device tensors: scale [n,3], rot [n,3,3], pt_norm, t_scale [n],
+    split, prune [n] (bool)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = dict(scale=torch.empty(n, 3, device=dev), rot=torch.empty(n, 3, 3, device=dev),
+               pt_norm=torch.empty(n, device=dev), t_scale=torch.empty(n, device=dev),
+               split=torch.empty(n, dtype=torch.uint8, device=dev), prune=torch.empty(n, dtype=torch.uint8, device=dev))
+    o = Densify(*(_ptr(out[k]) for k in ("scale", "rot", "pt_norm", "t_scale", "split", "prune")))
+    cfg = DensifyCfg(float(extent), float(split_pt), float(split_t), float(prune_alpha))
+    _check(lib().sdgs_densify_stats(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(cfg), ctypes.byref(o),
+                                    _stream(stream)))
+    out["split"] = out["split"].bool()
+    out["prune"] = out["prune"].bool()
+    return out
 
 
 class Server:

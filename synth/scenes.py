@@ -34,6 +34,7 @@ class Scene:
     lambda_t: float
     lambda_d: float
     bg: tuple = (0.0, 0.0, 0.0)
+    dir_mode: int = 0  # conditioning direction: 0 the request's, 1 camera centre -> mu_p per Gaussian
 
     @property
     def n(self) -> int:
@@ -41,7 +42,7 @@ class Scene:
 
     def subset(self, idx) -> "Scene":
         return Scene(self.mean7[idx].copy(), self.L28[idx].copy(), self.opacity[idx].copy(),
-                     self.sh[idx].copy(), self.lambda_t, self.lambda_d, self.bg)
+                     self.sh[idx].copy(), self.lambda_t, self.lambda_d, self.bg, self.dir_mode)
 
 
 @dataclasses.dataclass
@@ -218,7 +219,7 @@ def perturb_scene(scene: Scene, seed: int = 2000, mean_sigma: float = 0.01,
         k = _packed_index(i, i)
         L28[:, k] = np.maximum(L28[:, k], diag_floor)
     return Scene(mean7.astype(np.float32), L28.astype(np.float32), scene.opacity.copy(),
-                 scene.sh.copy(), scene.lambda_t, scene.lambda_d, scene.bg)
+                 scene.sh.copy(), scene.lambda_t, scene.lambda_d, scene.bg, scene.dir_mode)
 
 
 def serving_scenes() -> list[Scene]:

@@ -11,7 +11,7 @@ from paper_2503_07946_gb300 import sdgs
 def gpu_project(scene, cam):
     """sdgs_slice_project on a synth.Scene; returns host copies of the projected record."""
     dev = prender.scene_to_device(scene)
-    st = sdgs.scene_struct(dev, scene.lambda_t, scene.lambda_d)
+    st = sdgs.scene_struct(dev, scene.lambda_t, scene.lambda_d, scene.dir_mode)
     view = sdgs.view_struct(cam)
     proj = sdgs.ProjectedBuffers(scene.n)
     sdgs.slice_project(st, view, proj)

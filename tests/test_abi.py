@@ -47,6 +47,7 @@ def test_struct_layout_matches_c(tmp_path):
         " sizeof(sdgs_bins), sizeof(sdgs_grads));\n"
         '  printf("%zu %zu %zu %zu\\n", offsetof(sdgs_view, width), offsetof(sdgs_view, d),'
         " offsetof(sdgs_scene, lambda_d), offsetof(sdgs_bins, capacity));\n"
+        '  printf("%zu %zu\\n", offsetof(sdgs_scene, dir_mode), offsetof(sdgs_grads, dlambda));\n'
         "  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
@@ -55,7 +56,7 @@ def test_struct_layout_matches_c(tmp_path):
     assert sizes[:5] == [ctypes.sizeof(sdgs.Scene), ctypes.sizeof(sdgs.View), ctypes.sizeof(sdgs.Projected),
                          ctypes.sizeof(sdgs.Bins), ctypes.sizeof(sdgs.Grads)]
     assert sizes[5:] == [sdgs.View.width.offset, sdgs.View.d.offset, sdgs.Scene.lambda_d.offset,
-                         sdgs.Bins.capacity.offset]
+                         sdgs.Bins.capacity.offset, sdgs.Scene.dir_mode.offset, sdgs.Grads.dlambda.offset]
 
 
 def test_version_and_workspace_size(lib):

@@ -19,11 +19,14 @@ GRAD_TOL = 1e-3  # per tensor: max|g - g_ref| <= 1e-3 max|g_ref|
 def _gpu_grads(scene, cam, dL):
     dev = prender.scene_to_device(scene)
     params = {k: v.clone().requires_grad_(True) for k, v in dev.items()}
+    lam = torch.tensor([scene.lambda_t, scene.lambda_d], dtype=torch.float32, device="cuda", requires_grad=True)
     r = prender.Renderer(scene.n, cam.width, cam.height)
     img = prender.render_image(params["mean7"], params["L28"], params["opacity"], params["sh"],
-                               sdgs.view_struct(cam), scene.lambda_t, scene.lambda_d, r)
+                               sdgs.view_struct(cam), lam[0], lam[1], r, scene.dir_mode)
     (img * torch.as_tensor(dL, dtype=torch.float32, device="cuda")).sum().backward()
-    return {k: v.grad.cpu().numpy() for k, v in params.items()}, img.detach().cpu().numpy()
+    out = {k: v.grad.cpu().numpy() for k, v in params.items()}
+    out["lam"] = lam.grad.cpu().numpy()
+    return out, img.detach().cpu().numpy()
 
 
 def _check(scene, cam, seed):
@@ -32,23 +35,32 @@ def _check(scene, cam, seed):
     got, img = _gpu_grads(scene, cam, dL)
     ref = orender.vjp(scene, cam, dL)
     report = {}
-    for k in ("mean7", "L28", "opacity", "sh"):
-        g, r = got[k].reshape(scene.n, -1), ref[k].reshape(scene.n, -1)
+    for k in ("mean7", "L28", "opacity", "sh", "lam"):
+        g, r = got[k].reshape(-1), ref[k].reshape(-1)
         scale = np.abs(r).max()
         report[k] = float(np.abs(g - r).max() / scale)
     return report
 
 
-@pytest.mark.parametrize("case", ["config0", "rotated", "small"])
-def test_gradients_match_oracle(case):
+def _case(case):
     if case == "config0":
-        scene, cam = synth.config_scene(0), synth.config_cameras(0)[0]
-    elif case == "rotated":
+        return synth.config_scene(0), synth.config_cameras(0)[0]
+    if case == "rotated":
         scene = synth.config_scene(0, n=2048)
-        cam = synth.make_camera((1.2, -0.8, -2.6), 141, 97, 55.0, 0.3, bg=(0.2, 0.4, 0.6))
-    else:
+        return scene, synth.make_camera((1.2, -0.8, -2.6), 141, 97, 55.0, 0.3, bg=(0.2, 0.4, 0.6))
+    if case == "small":
         scene = synth.make_scene(64, seed=16, box=0.6)
-        cam = synth.make_camera((0.0, 0.0, -3.0), 32, 32, 60.0, 0.5, bg=(0.3, 0.3, 0.3))
+        return scene, synth.make_camera((0.0, 0.0, -3.0), 32, 32, 60.0, 0.5, bg=(0.3, 0.3, 0.3))
+    # per-Gaussian conditioning direction, broad direction blocks so most Gaussians stay visible
+    scene = synth.make_scene(2048, seed=31, box=1.0, diag=(0.05, 0.4), lambda_t=0.1, lambda_d=0.2)
+    scene.dir_mode = 1
+    return scene, synth.make_camera((0.9, -0.4, -2.8), 120, 90, 55.0, 0.6, bg=(0.1, 0.2, 0.3))
+
+
+@pytest.mark.parametrize("case", ["config0", "rotated", "small", "gaussian_dir"])
+def test_gradients_match_oracle(case):
+    """Gradients of all parameter tensors and of (lambda_t, lambda_d)."""
+    scene, cam = _case(case)
     rep = _check(scene, cam, seed=3)
     for k, v in rep.items():
         assert v <= GRAD_TOL, (k, rep)

@@ -27,11 +27,13 @@ def scene0():
     return synth.config_scene(0)
 
 
-@pytest.mark.parametrize("ci", [0, 1, 2])
-def test_slice_project_records(scene0, ci):
+@pytest.mark.parametrize("ci,dir_mode", [(0, 0), (1, 0), (2, 0), (1, 1)])
+def test_slice_project_records(scene0, ci, dir_mode):
     cam = _cams()[ci]
+    scene0 = scene0.subset(np.arange(scene0.n))
+    scene0.dir_mode = dir_mode
     got, _ = U.gpu_project(scene0, cam)
-    g = render.gaussians(render.params_from_scene(scene0), cam, scene0.lambda_t, scene0.lambda_d)
+    g = render.gaussians(render.params_from_scene(scene0), cam, scene0.lambda_t, scene0.lambda_d, dir_mode)
     vis_o = g["visible"].numpy()
     vis_g = (got["rect"][:, 2] > got["rect"][:, 0]) & (got["rect"][:, 3] > got["rect"][:, 1])
     border = U.boundary_gaussians(g)

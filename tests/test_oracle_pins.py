@@ -515,3 +515,124 @@ def test_reachability_drops_a_large_share_of_rectangle_tiles_on_a_scene():
     full, _ = binning.instances(rect, cam.tiles_x)
     kept, _ = binning.instances(rect, cam.tiles_x, render.cull_inputs(g["mean2d"], g["conic"], g["alpha_cond"]))
     assert 0 < len(kept) < 0.8 * len(full)
+
+
+# ----------------------------------------------------------------------------------------------
+# Per-Gaussian conditioning direction and lambda gradients
+# ----------------------------------------------------------------------------------------------
+
+def test_per_gaussian_direction_is_unit_vector_from_camera_centre_to_mu_p():
+    """dir_mode = 1 conditions Gaussian i on (mu_p,i - c) / |mu_p,i - c|: the same as the request
+    path with that single direction; and a Gaussian whose mu_d is that direction has f_dir = 1."""
+    rng = np.random.default_rng(21)
+    n = 12
+    L28 = torch.tensor(_pack(_random_L(rng, n)))
+    mean7 = torch.tensor(rng.normal(size=(n, 7)))
+    centre = np.array([0.3, -0.2, -3.0])
+    w = mean7[:, :3].numpy() - centre
+    unit = w / np.linalg.norm(w, axis=1, keepdims=True)
+    mean7[::2, 4:7] = torch.tensor(unit[::2])  # even Gaussians look exactly along their direction
+    op = torch.full((n,), 0.7, dtype=F64)
+    per = slicing.slice_gaussians(mean7, L28, op, 0.4, None, 0.05, 0.3, dir_mode=1, center=centre)
+    np.testing.assert_allclose(per["f_dir"].numpy()[::2], 1.0, rtol=0, atol=1e-14)
+    for i in range(n):
+        one = slicing.slice_gaussians(mean7[i:i + 1], L28[i:i + 1], op[i:i + 1], 0.4, unit[i], 0.05, 0.3)
+        for k in ("mu_cond", "Sigma_cond", "alpha_cond"):
+            np.testing.assert_allclose(per[k].numpy()[i], one[k].numpy()[0], rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("dir_mode", [0, 1])
+def test_oracle_lambda_and_mean_gradients_match_central_differences(dir_mode):
+    scene = synth.make_scene(48, seed=23, box=0.6, lambda_t=0.1, lambda_d=0.15, diag=(0.2, 0.6))
+    scene.dir_mode = dir_mode
+    cam = synth.make_camera((0.2, -0.1, -3.0), 32, 32, 60.0, 0.35, bg=(0.3, 0.3, 0.3))
+    rng = np.random.default_rng(29)
+    dL = rng.normal(size=(32, 32, 3))
+    grads = render.vjp(scene, cam, dL)
+    base_dec, _ = _decisions(scene, cam)
+
+    def run(lam_t, lam_d, mean7):
+        sc = synth.Scene(mean7, scene.L28.astype(np.float64), scene.opacity.astype(np.float64),
+                         scene.sh.astype(np.float64), lam_t, lam_d, scene.bg, dir_mode)
+        dec, out = _decisions(sc, cam)
+        return dec, float((out["image"].numpy() * dL).sum())
+
+    m64 = scene.mean7.astype(np.float64)
+    for k, (lt, ld) in enumerate([(1e-6, 0.0), (0.0, 1e-6)]):
+        (dp, vp), (dm, vm) = run(scene.lambda_t + lt, scene.lambda_d + ld, m64), \
+            run(scene.lambda_t - lt, scene.lambda_d - ld, m64)
+        assert all(np.array_equal(a, b) for d in (dp, dm) for a, b in zip(d, base_dec))
+        fd = (vp - vm) / 2e-6
+        assert abs(fd - grads["lam"][k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, grads["lam"][k])
+    assert np.any(grads["lam"] != 0)
+    checked = 0
+    vis = np.nonzero(base_dec[0])[0]
+    for g in rng.choice(vis, size=8, replace=False):
+        for c in range(3):  # mu_p: with dir_mode = 1 it also moves the conditioning direction
+            h = 1e-6
+            mp, mm = m64.copy(), m64.copy()
+            mp[g, c] += h
+            mm[g, c] -= h
+            (dp, vp), (dm, vm) = run(scene.lambda_t, scene.lambda_d, mp), run(scene.lambda_t, scene.lambda_d, mm)
+            if not all(np.array_equal(a, b) for d in (dp, dm) for a, b in zip(d, base_dec)):
+                continue
+            fd = (vp - vm) / (2 * h)
+            an = grads["mean7"][g, c]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-7, (g, c, fd, an)
+            checked += 1
+    assert checked >= 18
+
+
+# ----------------------------------------------------------------------------------------------
+# Densification statistics (Algorithm 1 step 7, Sec. 4.4)
+# ----------------------------------------------------------------------------------------------
+
+def _rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_scale_rotation_recovers_a_known_rotation_and_scales():
+    """Sigma_cond = R0 diag(s0^2) R0^T with distinct s0: S = sorted s0, R = R0's columns in that
+    order up to sign, det R = +1."""
+    from oracle import densify
+    rng = np.random.default_rng(41)
+    n = 20
+    R0 = np.stack([_rotation(rng) for _ in range(n)])
+    s0 = rng.uniform(0.05, 1.0, size=(n, 3))
+    Sig = np.einsum("nij,nj,nkj->nik", R0, s0 ** 2, R0)
+    S, R = densify.scale_rotation(torch.tensor(Sig))
+    order = np.argsort(-s0, axis=1)
+    np.testing.assert_allclose(S, np.take_along_axis(s0, order, axis=1), rtol=1e-12)
+    for i in range(n):
+        for j in range(3):
+            c = abs(float(R[i, :, j] @ R0[i, :, order[i, j]]))
+            assert abs(c - 1.0) < 1e-10
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-12)
+
+
+def test_split_statistics_closed_form():
+    """With L built so that row t of L is (0, 0, 0, st, 0, 0, 0) plus a chosen coupling to x:
+    Sigma_t = st^2 + c^2 and Sigma_pt = (c * L_xx, 0, 0)."""
+    from oracle import densify
+    n = 3
+    L = np.zeros((n, 7, 7))
+    for i in range(7):
+        L[:, i, i] = 0.3
+    st = np.array([0.1, 0.3, 0.5])
+    c = np.array([0.0, 0.4, 0.2])
+    L[:, 3, 3] = st
+    L[:, 3, 0] = c
+    mean7 = np.zeros((n, 7))
+    mean7[:, 4:] = [0.0, 0.0, 1.0]
+    out = densify.densify_stats(mean7, _pack(L), np.array([0.5, 0.005, 0.02]), 0.0, [0, 0, 1], 0.05, 0.05,
+                                extent=2.0)
+    np.testing.assert_allclose(out["t_scale"], np.sqrt(st ** 2 + c ** 2), rtol=1e-14)
+    np.testing.assert_allclose(out["pt_norm"], c * 0.3, rtol=1e-14, atol=1e-16)
+    # split: |Sigma_pt| > 0.05 * 2.0 = 0.1 and t_scale > 0.25
+    np.testing.assert_array_equal(out["split"], [False, True, False])
+    np.testing.assert_array_equal(out["prune"], [False, True, False])
