@@ -257,6 +257,50 @@ typedef struct sdgs_densify {
 int sdgs_densify_stats(const sdgs_scene* scene, const sdgs_view* view, const sdgs_densify_cfg* cfg,
                        const sdgs_densify* out, void* stream);
 
+/* Adaptive Gaussian Refinement (Sec. 4.3, Algorithm 1 steps 1-2).  Four two-layer MLPs
+ * Linear(27, 64) -> ReLU -> Linear(64, C_out), C_out = 3, 1, 3, 28, read
+ *   f = mu_p (+) mu_t (+) mu_d (+) gamma(t),
+ *   gamma(t) = (sin(2^0 pi t), cos(2^0 pi t), ..., sin(2^9 pi t), cos(2^9 pi t)),
+ * and add their outputs to mu_p, mu_t, mu_d and the packed L (same packing as L28).  The paper
+ * prints the feature, the encoding and the layer sizes; ReLU and the biases are our reading.
+ * Weights (device float32, C-contiguous):
+ *   w1 [4][64][27], b1 [4][64]   first layers of the MLPs for mu_p, mu_t, mu_d, l (in that order)
+ *   w2 [35][64], b2 [35]         output rows 0-2 -> mu_p, 3 -> mu_t, 4-6 -> mu_d, 7-34 -> l; each
+ *                                row reads the 64 hidden units of its own MLP */
+typedef struct sdgs_agr {
+  const float* w1;
+  const float* b1;
+  const float* w2;
+  const float* b2;
+} sdgs_agr;
+
+/* Weight gradients, same shapes as sdgs_agr, accumulated (+=). */
+typedef struct sdgs_agr_grads {
+  float* dw1;
+  float* db1;
+  float* dw2;
+  float* db2;
+} sdgs_agr_grads;
+
+/* Refined parameters of every Gaussian at time t: mean7_out [n][7], L28_out [n][28] (device
+ * float32, caller-allocated; may not alias the scene's arrays).  The refined scene is then
+ * rendered like any other (sdgs_scene pointing at mean7_out / L28_out).
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_CUDA. */
+int sdgs_agr_refine(const sdgs_scene* scene, const sdgs_agr* agr, float t, float* mean7_out, float* L28_out,
+                    void* stream);
+
+/* Bytes of device workspace sdgs_agr_refine_bwd needs for n Gaussians. */
+int sdgs_agr_bwd_workspace_size(int64_t n, size_t* bytes);
+
+/* Adjoint of sdgs_agr_refine: given dmean7_hat [n][7] and dL28_hat [n][28] (gradients w.r.t. the
+ * refined parameters, e.g. from sdgs_render_bwd on the refined scene), accumulates
+ * dmean7 += dmean7_hat + (d phi / d mu)^T (...), dL28 += dL28_hat, and the weight gradients.
+ * The weight gradients are summed per block and then across blocks in a fixed order, so repeated
+ * calls give identical results.  Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_CUDA. */
+int sdgs_agr_refine_bwd(const sdgs_scene* scene, const sdgs_agr* agr, float t, const float* dmean7_hat,
+                        const float* dL28_hat, float* dmean7, float* dL28, const sdgs_agr_grads* dagr,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Render server.  The paper has no serving component; this realises "render requests over
  * resident scenes" on one GPU.  Scenes stay resident (caller-owned device arrays).  Requests --

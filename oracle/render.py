@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import binning, composite, projection, sh, slicing
+from . import agr, binning, composite, projection, sh, slicing
 
 F64 = torch.float64
 TILE = 16
@@ -164,27 +164,47 @@ def render_projected(rec: dict, width: int, height: int, bg, tiles=None) -> dict
                          torch.as_tensor(bg, dtype=F64), tiles)
 
 
-def vjp(scene, cam, dL_dimage: np.ndarray, tiles=None) -> dict:
+def refined_params(scene, agr_weights: dict | None, t, requires_grad: bool = False):
+    """Scene parameters as float64 tensors, refined by the adaptive refinement MLPs (Sec. 4.3)
+    at time t when agr_weights (float32 arrays) are given.  Returns (leaves, params, weights)."""
+    leaf = params_from_scene(scene, requires_grad=requires_grad)
+    if agr_weights is None:
+        return leaf, leaf, None
+    w = agr.weights_to_torch(agr_weights, requires_grad=requires_grad)
+    m, l = agr.refine(leaf["mean7"], leaf["L28"], t, w)
+    return leaf, dict(leaf, mean7=m, L28=l), w
+
+
+def render_agr(scene, cam, agr_weights: dict, tiles=None) -> dict:
+    """render() of the scene refined at the camera's time t."""
+    _, p, _ = refined_params(scene, agr_weights, cam.t)
+    return render(scene, cam, tiles, params={k: v.detach() for k, v in p.items()})
+
+
+def vjp(scene, cam, dL_dimage: np.ndarray, tiles=None, agr_weights: dict | None = None) -> dict:
     """Gradients of sum(dL_dimage * image) w.r.t. mean7, L28, opacity, sh and (lambda_t,
-    lambda_d), in float64.
+    lambda_d) -- and, with agr_weights, w.r.t. the refinement weights -- in float64.
 
     The visible set is found first without gradients; the forward is then re-run on the
     visible Gaussians only, so culled Gaussians receive exactly zero gradient.  With `tiles`,
     only those tiles are composited: exact when dL_dimage is zero outside them.
     """
-    p0 = params_from_scene(scene)
     with torch.no_grad():
+        _, p0, _ = refined_params(scene, agr_weights, cam.t)
         vis = gaussians(p0, cam, scene.lambda_t, scene.lambda_d, scene.dir_mode)["visible"]
     idx = torch.nonzero(vis).reshape(-1)
-    leaf = params_from_scene(scene, requires_grad=True)
+    leaf, p, w = refined_params(scene, agr_weights, cam.t, requires_grad=True)
     lam = torch.tensor([scene.lambda_t, scene.lambda_d], dtype=F64, requires_grad=True)
-    sub = {k: v[idx] for k, v in leaf.items()}
+    sub = {k: v[idx] for k, v in p.items()}
     g = gaussians(sub, cam, lam[0], lam[1], scene.dir_mode)
     bg = torch.as_tensor(cam.bg, dtype=F64)
     out = composite_all(g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], g["depth"], g["rect"],
                         cam, bg, tiles)
     loss = (out["image"] * torch.as_tensor(dL_dimage, dtype=F64)).sum()
     loss.backward()
-    return dict(mean7=leaf["mean7"].grad.numpy(), L28=leaf["L28"].grad.numpy(),
-                opacity=leaf["opacity"].grad.numpy(), sh=leaf["sh"].grad.numpy(),
-                lam=lam.grad.numpy(), image=out["image"].detach().numpy(), loss=float(loss.detach()))
+    res = dict(mean7=leaf["mean7"].grad.numpy(), L28=leaf["L28"].grad.numpy(),
+               opacity=leaf["opacity"].grad.numpy(), sh=leaf["sh"].grad.numpy(),
+               lam=lam.grad.numpy(), image=out["image"].detach().numpy(), loss=float(loss.detach()))
+    if w is not None:
+        res.update({k: v.grad.numpy() for k, v in w.items()})
+    return res

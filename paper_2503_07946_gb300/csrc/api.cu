@@ -268,6 +268,63 @@ int sdgs_densify_stats(const sdgs_scene* scene, const sdgs_view* view, const sdg
   return cuda_status(launch_densify(*scene, *view, *cfg, *out, (cudaStream_t)stream), "densify launch");
 }
 
+static int check_agr(const sdgs_agr* a) {
+  if (a == nullptr || !a->w1 || !a->b1 || !a->w2 || !a->b2) { set_error("AGR weights are NULL"); return SDGS_ERR_INVALID_ARG; }
+  if (!aligned(a->w1, 4) || !aligned(a->b1, 4) || !aligned(a->w2, 4) || !aligned(a->b2, 4)) {
+    set_error("AGR weights misaligned");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  return SDGS_OK;
+}
+
+int sdgs_agr_refine(const sdgs_scene* scene, const sdgs_agr* agr, float t, float* mean7_out, float* L28_out,
+                    void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_scene(scene));
+  SDGS_TRY(check_agr(agr));
+  if (!std::isfinite(t)) { set_error("t is not finite"); return SDGS_ERR_INVALID_ARG; }
+  if (scene->n > 0 && (!mean7_out || !L28_out || !aligned(mean7_out, 4) || !aligned(L28_out, 16))) {
+    set_error("refined outputs NULL or misaligned (L28_out to 16 bytes)");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (scene->n > 0 && ((const float*)mean7_out == scene->mean7 || (const float*)L28_out == scene->L28)) {
+    set_error("refined outputs alias the scene");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  return cuda_status(launch_agr_refine(*scene, *agr, t, mean7_out, L28_out, (cudaStream_t)stream), "agr launch");
+}
+
+int sdgs_agr_bwd_workspace_size(int64_t n, size_t* bytes) {
+  if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 31)) { set_error("bad arguments to sdgs_agr_bwd_workspace_size"); return SDGS_ERR_INVALID_ARG; }
+  *bytes = agr_bwd_workspace_bytes(n);
+  return SDGS_OK;
+}
+
+int sdgs_agr_refine_bwd(const sdgs_scene* scene, const sdgs_agr* agr, float t, const float* dmean7_hat,
+                        const float* dL28_hat, float* dmean7, float* dL28, const sdgs_agr_grads* dagr,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  g_error[0] = 0;
+  SDGS_TRY(check_scene(scene));
+  SDGS_TRY(check_agr(agr));
+  if (!std::isfinite(t)) { set_error("t is not finite"); return SDGS_ERR_INVALID_ARG; }
+  if (dagr == nullptr || !dagr->dw1 || !dagr->db1 || !dagr->dw2 || !dagr->db2) {
+    set_error("AGR gradient pointers are NULL");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (scene->n > 0 && (!dmean7_hat || !dL28_hat || !dmean7 || !dL28)) {
+    set_error("AGR backward input / output pointer is NULL");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  const size_t need = agr_bwd_workspace_bytes(scene->n);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) {
+    set_error("AGR backward workspace needs %zu bytes, 256-byte aligned", need);
+    return SDGS_ERR_WORKSPACE;
+  }
+  return cuda_status(launch_agr_refine_bwd(*scene, *agr, t, dmean7_hat, dL28_hat, dmean7, dL28, *dagr,
+                                           (char*)workspace, (cudaStream_t)stream),
+                     "agr backward launch");
+}
+
 int sdgs_bwd_workspace_size(int64_t n, size_t* bytes) {
   g_error[0] = 0;
   if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 31)) { set_error("bad arguments to sdgs_bwd_workspace_size"); return SDGS_ERR_INVALID_ARG; }

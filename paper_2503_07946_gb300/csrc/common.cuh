@@ -59,6 +59,12 @@ cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const
 size_t bwd_workspace_bytes(int64_t n);
 cudaError_t launch_densify(const sdgs_scene& s, const sdgs_view& v, const sdgs_densify_cfg& cfg,
                            const sdgs_densify& out, cudaStream_t st);
+size_t agr_bwd_workspace_bytes(int64_t n);
+cudaError_t launch_agr_refine(const sdgs_scene& s, const sdgs_agr& a, float t, float* mean7_out, float* L28_out,
+                              cudaStream_t st);
+cudaError_t launch_agr_refine_bwd(const sdgs_scene& s, const sdgs_agr& a, float t, const float* dmean7_hat,
+                                  const float* dL28_hat, float* dmean7, float* dL28, const sdgs_agr_grads& g,
+                                  char* ws, cudaStream_t st);
 cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& p,
                               const sdgs_bins& b, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, char* ws, const sdgs_grads& g,

@@ -108,3 +108,43 @@ def render_image(mean7, L28, opacity, sh, view: sdgs.View, lambda_t, lambda_d, r
     lam = torch.stack([torch.as_tensor(lambda_t, dtype=torch.float32, device=dev).reshape(()),
                        torch.as_tensor(lambda_d, dtype=torch.float32, device=dev).reshape(())])
     return Render7DGS.apply(mean7, L28, opacity, sh, lam, view, renderer, dir_mode)
+
+
+class AGRRefine(torch.autograd.Function):
+    """(mean7^, L28^) = adaptive refinement of (mean7, L28) at time t by the four MLPs (w1, b1, w2,
+    b2); backward is the CUDA adjoint (input and weight gradients)."""
+
+    @staticmethod
+    def forward(ctx, mean7, L28, w1, b1, w2, b2, t: float):
+        w = dict(w1=w1.contiguous(), b1=b1.contiguous(), w2=w2.contiguous(), b2=b2.contiguous())
+        m7, l28 = mean7.contiguous(), L28.contiguous()
+        n = m7.shape[0]
+        opacity = torch.zeros(n, device=m7.device)
+        sh = torch.zeros(n, 16, 3, device=m7.device)
+        scene = sdgs.scene_struct(dict(mean7=m7, L28=l28, opacity=opacity, sh=sh), 0.0, 0.0)
+        m_out, l_out = torch.empty_like(m7), torch.empty_like(l28)
+        sdgs.agr_refine(scene, w, t, m_out, l_out)
+        ctx.t = float(t)
+        ctx.save_for_backward(m7, l28, w["w1"], w["b1"], w["w2"], w["b2"])
+        return m_out, l_out
+
+    @staticmethod
+    def backward(ctx, d_m, d_l):
+        m7, l28, w1, b1, w2, b2 = ctx.saved_tensors
+        n = m7.shape[0]
+        w = dict(w1=w1, b1=b1, w2=w2, b2=b2)
+        opacity = torch.zeros(n, device=m7.device)
+        sh = torch.zeros(n, 16, 3, device=m7.device)
+        scene = sdgs.scene_struct(dict(mean7=m7, L28=l28, opacity=opacity, sh=sh), 0.0, 0.0)
+        d_m = torch.zeros_like(m7) if d_m is None else d_m.contiguous()
+        d_l = torch.zeros_like(l28) if d_l is None else d_l.contiguous()
+        gm, gl = torch.zeros_like(m7), torch.zeros_like(l28)
+        dw = {k: torch.zeros_like(v) for k, v in w.items()}
+        ws = torch.empty(max(sdgs.agr_bwd_workspace_size(n), 256), dtype=torch.uint8, device=m7.device)
+        sdgs.agr_refine_bwd(scene, w, ctx.t, d_m, d_l, gm, gl, dw, ws)
+        return gm, gl, dw["w1"], dw["b1"], dw["w2"], dw["b2"], None
+
+
+def agr_refine(mean7, L28, weights: dict, t: float):
+    """Differentiable adaptive refinement: returns (mean7^, L28^)."""
+    return AGRRefine.apply(mean7, L28, weights["w1"], weights["b1"], weights["w2"], weights["b2"], float(t))

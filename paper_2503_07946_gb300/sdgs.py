@@ -56,6 +56,14 @@ class Grads(ctypes.Structure):
                 ("dsh", ctypes.c_void_p), ("dlambda", ctypes.c_void_p)]
 
 
+class Agr(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p)]
+
+
+class AgrGrads(ctypes.Structure):
+    _fields_ = [("dw1", ctypes.c_void_p), ("db1", ctypes.c_void_p), ("dw2", ctypes.c_void_p), ("db2", ctypes.c_void_p)]
+
+
 class DensifyCfg(ctypes.Structure):
     _fields_ = [("extent", ctypes.c_float), ("split_pt", ctypes.c_float), ("split_t", ctypes.c_float),
                 ("prune_alpha", ctypes.c_float)]
@@ -102,6 +110,12 @@ SIGNATURES = {
                          ctypes.POINTER(Bins), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(Grads), ctypes.c_void_p],
                         ctypes.c_int),
+    "sdgs_agr_refine": ([ctypes.POINTER(Scene), ctypes.POINTER(Agr), ctypes.c_float, ctypes.c_void_p,
+                         ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "sdgs_agr_bwd_workspace_size": ([ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sdgs_agr_refine_bwd": ([ctypes.POINTER(Scene), ctypes.POINTER(Agr), ctypes.c_float, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(AgrGrads),
+                             ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p], ctypes.c_int),
     "sdgs_densify_stats": ([ctypes.POINTER(Scene), ctypes.POINTER(View), ctypes.POINTER(DensifyCfg),
                             ctypes.POINTER(Densify), ctypes.c_void_p], ctypes.c_int),
     "sdgs_server_create": ([ctypes.POINTER(ServerCfg), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -307,6 +321,38 @@ def render_bwd(scene: Scene, view: View, proj: ProjectedBuffers, bins: BinBuffer
     _check(lib().sdgs_render_bwd(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(proj.struct()),
                                  ctypes.byref(bins.struct()), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
                                  _ptr(workspace), workspace.numel(), ctypes.byref(g), _stream(stream)))
+
+
+AGR_SHAPES = dict(w1=(4, 64, 27), b1=(4, 64), w2=(35, 64), b2=(35,))
+
+
+def agr_struct(w: dict) -> Agr:
+    """w: dict of CUDA float32 tensors w1 [4,64,27], b1 [4,64], w2 [35,64], b2 [35] (contiguous)."""
+    for k, shape in AGR_SHAPES.items():
+        if w[k].dtype != torch.float32 or tuple(w[k].shape) != shape or not w[k].is_contiguous():
+            raise ValueError(f"AGR weight {k} must be contiguous float32 of shape {shape}")
+    return Agr(_ptr(w["w1"]), _ptr(w["b1"]), _ptr(w["w2"]), _ptr(w["b2"]))
+
+
+def agr_refine(scene: Scene, w: dict, t: float, mean7_out: torch.Tensor, L28_out: torch.Tensor, stream=None):
+    a = agr_struct(w)
+    _check(lib().sdgs_agr_refine(ctypes.byref(scene), ctypes.byref(a), float(t), _ptr(mean7_out), _ptr(L28_out),
+                                 _stream(stream)))
+
+
+def agr_bwd_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().sdgs_agr_bwd_workspace_size(n, ctypes.byref(b)))
+    return int(b.value)
+
+
+def agr_refine_bwd(scene: Scene, w: dict, t: float, dmean7_hat, dL28_hat, dmean7, dL28, dw: dict,
+                   workspace: torch.Tensor, stream=None):
+    a = agr_struct(w)
+    g = AgrGrads(_ptr(dw["w1"]), _ptr(dw["b1"]), _ptr(dw["w2"]), _ptr(dw["b2"]))
+    _check(lib().sdgs_agr_refine_bwd(ctypes.byref(scene), ctypes.byref(a), float(t), _ptr(dmean7_hat),
+                                     _ptr(dL28_hat), _ptr(dmean7), _ptr(dL28), ctypes.byref(g), _ptr(workspace),
+                                     workspace.numel(), _stream(stream)))
 
 
 def densify_stats(scene: Scene, view: View, n: int, extent: float, split_pt: float = 0.05, split_t: float = 0.25,

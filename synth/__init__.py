@@ -16,6 +16,7 @@ from .scenes import (  # noqa: F401
     perturb_scene,
     random_projected,
     serving_scenes,
+    make_agr_weights,
     WHITE,
     BLACK,
 )

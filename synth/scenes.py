@@ -269,3 +269,16 @@ def random_projected(n: int, width: int, height: int, seed: int, *, empty_frac: 
     rgb = rng.uniform(0.0, 1.0, size=(n, 3)).astype(np.float32)
     return dict(mean2d=mean2d, conic=conic, opacity=opacity, rgb=rgb, depth=depth, rect=rect,
                 width=width, height=height)
+
+
+def make_agr_weights(seed: int = 3000, scale: float = 0.1) -> dict:
+    """Random weights of the four refinement MLPs (27 -> 64 -> 3, 1, 3, 28): uniform
+    +-1/sqrt(fan_in) as a freshly initialised linear layer, times `scale` so that the residuals
+    stay small next to the parameters.  float32 arrays w1 [4, 64, 27], b1 [4, 64], w2 [35, 64],
+    b2 [35]."""
+    rng = np.random.default_rng(seed)
+    a1, a2 = 1.0 / np.sqrt(27.0), 1.0 / np.sqrt(64.0)
+    return dict(w1=(rng.uniform(-a1, a1, size=(4, 64, 27)) * scale).astype(np.float32),
+                b1=(rng.uniform(-a1, a1, size=(4, 64)) * scale).astype(np.float32),
+                w2=(rng.uniform(-a2, a2, size=(35, 64)) * scale).astype(np.float32),
+                b2=(rng.uniform(-a2, a2, size=(35,)) * scale).astype(np.float32))

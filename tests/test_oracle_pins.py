@@ -636,3 +636,88 @@ def test_split_statistics_closed_form():
     # split: |Sigma_pt| > 0.05 * 2.0 = 0.1 and t_scale > 0.25
     np.testing.assert_array_equal(out["split"], [False, True, False])
     np.testing.assert_array_equal(out["prune"], [False, True, False])
+
+
+# ----------------------------------------------------------------------------------------------
+# Adaptive Gaussian Refinement (Sec. 4.3, Algorithm 1 steps 1-2)
+# ----------------------------------------------------------------------------------------------
+
+def test_temporal_encoding_closed_form():
+    from oracle import agr
+    g0 = agr.temporal_encoding(0.0).numpy()
+    np.testing.assert_array_equal(g0, np.tile([0.0, 1.0], 10))
+    # t = 1/2: sin(2^k pi / 2) = 1, 0, 0, ...; cos(2^k pi / 2) = 0, -1, 1, 1, ...
+    g = agr.temporal_encoding(0.5).numpy()
+    np.testing.assert_allclose(g[0::2], [1.0] + [0.0] * 9, atol=1e-12)
+    np.testing.assert_allclose(g[1::2], [0.0, -1.0] + [1.0] * 8, atol=1e-12)
+    assert g.shape == (20,)
+
+
+def _zero_weights():
+    return dict(w1=torch.zeros(4, 64, 27, dtype=F64), b1=torch.zeros(4, 64, dtype=F64),
+                w2=torch.zeros(35, 64, dtype=F64), b2=torch.zeros(35, dtype=F64))
+
+
+def test_refinement_routes_each_mlp_to_its_parameters():
+    """Zero weights give the identity; one hidden unit feeding one output row gives
+    relu(f_c + beta) on exactly the parameter that row refines."""
+    from oracle import agr
+    rng = np.random.default_rng(51)
+    n = 9
+    mean7 = torch.tensor(rng.normal(size=(n, 7)))
+    L28 = torch.tensor(rng.normal(size=(n, 28)))
+    t = 0.3
+    m0, l0 = agr.refine(mean7, L28, t, _zero_weights())
+    assert torch.equal(m0, mean7) and torch.equal(l0, L28)
+    f = agr.features(mean7, t).numpy()
+    cases = [(0, 0, 0, -0.2, "mean7", 0), (1, 5, 3, 0.1, "mean7", 3), (2, 9, 6, 0.0, "mean7", 6),
+             (3, 7, 10, 0.4, "L28", 3), (3, 26, 34, -0.7, "L28", 27), (0, 12, 2, 0.25, "mean7", 2)]
+    for m, c, row, beta, which, col in cases:
+        w = _zero_weights()
+        w["w1"][m, 17, c] = 1.0
+        w["b1"][m, 17] = beta
+        w["w2"][row, 17] = 1.0
+        mh, lh = agr.refine(mean7, L28, t, w)
+        want = np.maximum(f[:, c] + beta, 0.0)
+        got_m, got_l = (mh - mean7).numpy(), (lh - L28).numpy()
+        target, other = (got_m, got_l) if which == "mean7" else (got_l, got_m)
+        np.testing.assert_allclose(target[:, col], want, rtol=0, atol=1e-15)
+        target[:, col] = 0.0
+        assert not target.any() and not other.any(), (m, c, row)
+    # features: mu_p, mu_t, mu_d, then gamma(t)
+    np.testing.assert_array_equal(f[:, :7], mean7.numpy())
+    np.testing.assert_allclose(f[:, 7], math.sin(math.pi * t), rtol=1e-15)
+    np.testing.assert_allclose(f[:, 26], math.cos(2 ** 9 * math.pi * t), rtol=1e-12)
+
+
+def test_refinement_gradients_match_central_differences():
+    from oracle import agr
+    rng = np.random.default_rng(53)
+    n = 6
+    mean7 = torch.tensor(rng.normal(size=(n, 7)), requires_grad=True)
+    L28 = torch.tensor(rng.normal(size=(n, 28)), requires_grad=True)
+    w = agr.weights_to_torch(synth.make_agr_weights(seed=5, scale=1.0), requires_grad=True)
+    cm, cl = torch.tensor(rng.normal(size=(n, 7))), torch.tensor(rng.normal(size=(n, 28)))
+
+    def loss(m7, l28, ww):
+        mh, lh = agr.refine(m7, l28, 0.37, ww)
+        return (mh * cm).sum() + (lh * cl).sum()
+
+    loss(mean7, L28, w).backward()
+    checked = 0
+    for name in ("mean7", "L28", "w1", "b1", "w2", "b2"):
+        base = {"mean7": mean7, "L28": L28, **w}
+        for _ in range(6):
+            arr = base[name].detach()
+            k = int(rng.integers(0, arr.numel()))
+            vals = []
+            for sgn in (1, -1):
+                cur = {kk: v.detach().clone() for kk, v in base.items()}
+                cur[name].reshape(-1)[k] += sgn * 1e-6
+                with torch.no_grad():
+                    vals.append(float(loss(cur["mean7"], cur["L28"], {q: cur[q] for q in ("w1", "b1", "w2", "b2")})))
+            fd = (vals[0] - vals[1]) / 2e-6
+            an = float(base[name].grad.reshape(-1)[k])
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, k, fd, an)
+            checked += 1
+    assert checked == 36
