@@ -180,16 +180,14 @@ def run_reference(args, rank: int, world: int):
 # ---------------------------------------------------------------------------------------------
 
 def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
-    """Kernels libsdgs launches for one render: slice_project; depth keys; 4 depth radix passes over
-    the n Gaussians; the tested rectangles; the kept-tile counts and their 3-kernel scan; the
-    duplication into depth order; ceil(tile bits / 8) tile radix passes over `capacity` slots;
-    tile ranges; the rasteriser.  A radix pass is an upsweep and a downsweep, plus a 3-kernel
-    histogram scan above 128 radix blocks of 4096 keys."""
-    def per_pass(m):
-        return 2 if (m + 4095) // 4096 <= 128 else 5
+    """Kernels libsdgs launches for one render: slice_project; the depth keys (with the depth
+    digit histograms); 4 depth radix passes; the tested rectangles; the 3-kernel scan of the
+    bitmask words; the tile test; the 3-kernel scan of the kept counts; the emit (with the tile
+    digit histograms); ceil(tile bits / 8) tile radix passes; tile ranges; the rasteriser."""
     tiles = ((width + 15) // 16) * ((height + 15) // 16)
     bits = max(0, (tiles - 1).bit_length())
-    return 1 + 1 + 4 * per_pass(n) + 1 + 1 + 3 + 1 + ((bits + 7) // 8) * per_pass(capacity) + 1 + 1
+    tile_passes = (bits + 7) // 8 if capacity > 0 else 0
+    return 1 + 1 + 4 + 1 + 3 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
 
 
 def cpu_baseline(scene, cam) -> dict:
@@ -305,6 +303,9 @@ def run_ours(args, rank: int, world: int):
 
     # ---- fwd + bwd (L2 loss against a target from perturbed parameters, camera 0) ----
     fb = fwd_bwd_its(scene, cams[0], steps, warm, dev)
+    fb_agr = fwd_bwd_its(scene, cams[0], min(steps, 200), warm, dev, agr=True)
+    agr = agr_frames(scene, t_scene, views, flush, min(steps, 300), warm, dev)
+    dens = densify_ms(t_scene, scene, views[0], flush, 20, dev)
     serving = None if args.no_serving else serving_bench(dev)
 
     pix = W * H
@@ -327,6 +328,9 @@ def run_ours(args, rank: int, world: int):
                       "render_fwd": raster_ms},
         "workload_stats": {"instances": k_inst, "visible": visible, "evaluations_per_frame": evals // steps},
         "fwd_bwd_it_s": fb,
+        "fwd_bwd_agr_it_s": fb_agr,
+        "agr_frames": agr,
+        "densify_stats": dens,
         "serving": serving,
         "e2e": {"value": world * pix / e2e_s / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
                 "d2h_bytes_per_step": pix * 3 * 4 + 8},
@@ -441,7 +445,77 @@ def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: i
     return result
 
 
-def fwd_bwd_its(scene, cam, steps: int, warm: int, dev) -> dict:
+def agr_weights_dev(dev) -> dict:
+    return {k: torch.as_tensor(v, device=dev).contiguous() for k, v in synth.make_agr_weights(scale=0.1).items()}
+
+
+def agr_frames(scene, t_scene, views, flush, steps: int, warm: int, dev) -> dict:
+    """Forward frames with adaptive refinement: refine (at each view's t) -> slice -> bin -> render."""
+    from paper_2503_07946_gb300 import render as prender
+    from paper_2503_07946_gb300 import sdgs
+    w = agr_weights_dev(dev)
+    m_out, l_out = torch.empty_like(t_scene["mean7"]), torch.empty_like(t_scene["L28"])
+    st_raw = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
+    st_ref = sdgs.scene_struct(dict(t_scene, mean7=m_out, L28=l_out), scene.lambda_t, scene.lambda_d)
+    W, H = views[0].width, views[0].height
+    sizing = prender.Renderer(scene.n, W, H, capacity=4096)
+    kmax = 0
+    for v in views[: min(len(views), 100)]:
+        sdgs.agr_refine(st_raw, w, v.t, m_out, l_out)
+        sdgs.slice_project(st_ref, v, sizing.proj)
+        kmax = max(kmax, sizing.bin(v))
+    del sizing
+    r = prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096)
+    stream = torch.cuda.current_stream()
+
+    def step(v, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        sdgs.agr_refine(st_raw, w, v.t, m_out, l_out, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        sdgs.slice_project(st_ref, v, r.proj, stream)
+        sdgs.bin_sort(r.proj, v, r.bins, sync=False, stream=stream)
+        sdgs.render_fwd(r.proj, r.bins, v, r.image, r.final_T, r.n_contrib, None, stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for i in range(warm):
+        step(views[i])
+        flush.zero_()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        step(views[warm + i], evs[i])
+        flush.zero_()
+    torch.cuda.synchronize()
+    ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])] for e in evs])
+    ms = float(ph.sum(1).mean())
+    return {"value": W * H / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_frame": ms,
+            "agr_refine_ms": float(ph[:, 0].mean()), "steps": steps,
+            "workload": "config 1 frames with adaptive refinement (random weights, scale 0.1) before slicing"}
+
+
+def densify_ms(t_scene, scene, view, flush, steps: int, dev) -> dict:
+    from paper_2503_07946_gb300 import sdgs
+    st = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
+    for _ in range(3):
+        sdgs.densify_stats(st, view, scene.n, 3.0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    outs = []
+    for e in evs:
+        flush.zero_()
+        e[0].record()
+        outs.append(sdgs.densify_stats(st, view, scene.n, 3.0))
+        e[1].record()
+        outs.clear()
+    torch.cuda.synchronize()
+    return {"ms": float(np.mean([a.elapsed_time(b) for a, b in evs])), "n": scene.n,
+            "note": "scale/rotation (Jacobi), |Sigma_pt|, sqrt(Sigma_t), split and prune flags; includes the "
+                    "output allocations from the caching allocator"}
+
+
+def fwd_bwd_its(scene, cam, steps: int, warm: int, dev, agr: bool = False) -> dict:
     from paper_2503_07946_gb300 import render as prender
     from paper_2503_07946_gb300 import sdgs
     target_scene = synth.perturb_scene(scene)
@@ -451,13 +525,17 @@ def fwd_bwd_its(scene, cam, steps: int, warm: int, dev) -> dict:
     with torch.no_grad():
         target = r.forward(sdgs.scene_struct(tt, scene.lambda_t, scene.lambda_d), view).clone()
     params = {k: v.clone().requires_grad_(True) for k, v in prender.scene_to_device(scene).items()}
+    weights = {k: v.clone().requires_grad_(True) for k, v in agr_weights_dev(dev).items()} if agr else None
 
     def it():
-        img = prender.render_image(params["mean7"], params["L28"], params["opacity"], params["sh"], view,
+        m7, l28 = params["mean7"], params["L28"]
+        if weights is not None:
+            m7, l28 = prender.agr_refine(m7, l28, weights, cam.t)
+        img = prender.render_image(m7, l28, params["opacity"], params["sh"], view,
                                    scene.lambda_t, scene.lambda_d, r)
         loss = ((img - target) ** 2).mean()
         loss.backward()
-        for p in params.values():
+        for p in list(params.values()) + (list(weights.values()) if weights else []):
             p.grad = None
         return loss
 
@@ -472,7 +550,8 @@ def fwd_bwd_its(scene, cam, steps: int, warm: int, dev) -> dict:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     return {"value": 1000.0 / ms, "unit": "it/s", "ms_per_it": ms,
-            "workload": "config 3: 300k Gaussians, 800x800, camera 0, L2 loss vs a perturbed-parameter target"}
+            "workload": "config 3: 300k Gaussians, 800x800, camera 0, L2 loss vs a perturbed-parameter target"
+                        + (", with adaptive refinement (weights trained too)" if agr else "")}
 
 
 def main():
