@@ -35,10 +35,10 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # exponent (8), opacity clamp (2), tests (2), transmittance (2), weight (1), colour FMAs (6) = 23
 # FLOP (an FMA counts 2) plus one exp2 on the MUFU pipe.
 FLOP_PER_EVAL = 23
-# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture summarised in
-# profiles/render_fwd_config1_800x800_300k.md.  Set to None whenever render_fwd_kernel changes
+# DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one
+# `ncu --set full` capture of render_fwd_kernel.  Set to None whenever render_fwd_kernel changes
 # until it is captured again.
-RENDER_FWD_TRAFFIC_BYTES = None
+RENDER_FWD_TRAFFIC_BYTES = 12.805632e6
 
 
 def load_peaks() -> dict:
