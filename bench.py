@@ -181,13 +181,13 @@ def run_reference(args, rank: int, world: int):
 
 def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
     """Kernels libsdgs launches for one render: slice_project; the depth keys (with the depth
-    digit histograms); 4 depth radix passes; the tested rectangles; the 3-kernel scan of the
-    bitmask words; the tile test; the 3-kernel scan of the kept counts; the emit (with the tile
-    digit histograms); ceil(tile bits / 8) tile radix passes; tile ranges; the rasteriser."""
+    digit histograms); 4 depth radix passes; the kept-tile count per Gaussian; its 3-kernel scan;
+    the emit (with the tile digit histograms); ceil(tile bits / 8) tile radix passes; tile
+    ranges; the rasteriser."""
     tiles = ((width + 15) // 16) * ((height + 15) // 16)
     bits = max(0, (tiles - 1).bit_length())
     tile_passes = (bits + 7) // 8 if capacity > 0 else 0
-    return 1 + 1 + 4 + 1 + 3 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
+    return 1 + 1 + 4 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
 
 
 def cpu_baseline(scene, cam) -> dict:

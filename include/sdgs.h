@@ -159,18 +159,23 @@ int sdgs_slice_project(const sdgs_scene* scene, const sdgs_view* view, const sdg
 int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height,
                             size_t* bytes);
 
-/* Tile binning (Sec. 3.3 and the 3DGS tile rasteriser it builds on).  Sorts the Gaussians by
+/* Tile binning (the 3DGS tile rasteriser of Sec. 3 that Sec. 4.4 renders with).  Sorts the Gaussians by
  * float32 depth (stable, so equal depths keep ascending id), emits in that order one instance per
  * tile of each visible Gaussian's rectangle that the Gaussian may reach, stably sorts the
  * instances by tile id, and writes the per-tile ranges: the result is the stable sort of the
  * 64-bit keys tile_id << 32 | bits(depth) over the kept instances.
- * A tile of the rectangle is dropped only when, with conic (a, b, c) and opacity alpha, every
- * pixel centre of the tile has alpha exp(-q/2) < 1/255 by a margin far above float32 error:
- *   q_min = min of a dx^2 + 2 b dx dy + c dy^2 over the tile's pixel-centre box (0 if the mean
- *           lies inside; else the least of the one or two edges facing the mean, each at its
- *           clamped stationary point dy = clamp((-b / c) dx) or dx = clamp((-b / a) dy)),
- *   thr   = 512 (sqrt^8(255 alpha) - 1),  m = 1e-4 + 2^-18 (ac + b^2) / (ac - b^2),
- *   drop iff ac - b^2 > 0 and m < 1/2 and q_min (1 - m) > thr + 1e-3,
+ * A tile of the rectangle is dropped only when every pixel centre of the tile has
+ * alpha exp(-q/2) < 1/255 by a margin above float32 error; the kept tiles of each tile row form
+ * one span.  With conic (a, b, c), opacity alpha and mean (u, v):
+ *   det = ac - b^2,  m = 1e-4 + 2^-18 (ac + b^2) / det,  lim = 512 (sqrt^8(255 alpha) - 1) + 1e-3,
+ *   Q = lim (1 + 8m) / (1 - m),  hx = sqrt(Q c / det),  hy = sqrt(Q a / det),  dy_r = (-b / c) hx;
+ *   row ty is empty when its pixel-centre band [ey0, ey1] = [16 ty + 0.5 - v, 16 ty + 15.5 - v]
+ *   misses [-(hy + 0.05 + 2e-3 hy), +(...)]; otherwise, with pad = 0.05 + 2e-3 hx,
+ *     x_max = (-b d1 + sqrt(max(aQ - det d1^2, 0))) / a + pad,  d1 = clamp(dy_r, ey0, ey1),
+ *     x_min = (-b d2 - sqrt(max(aQ - det d2^2, 0))) / a - pad,  d2 = clamp(-dy_r, ey0, ey1),
+ *   and the row keeps ceil((u + x_min - 15.5) / 16) <= tx <= floor((u + x_max - 0.5) / 16);
+ *   alpha < 1/255 (lim < 0) drops every tile; det <= 0, m >= 1/2, a <= 0 or a NaN keeps every
+ *   tile (a NaN bound keeps the row),
  * every operation a correctly rounded float32 operation in that order, so the kept set is a
  * function of the float32 inputs alone.  Such tiles would composite to the same image.
  * `workspace` is device memory of at least sdgs_bin_workspace_size() bytes, 256-byte aligned.

@@ -6,11 +6,11 @@ keys keep ascending Gaussian id (the 3DGS tile sort the paper's rasteriser relie
 tile_id = ty * Tx + tx.  Tile ranges are the [start, end) spans of each tile in the sorted list.
 
 Tiles of the rectangle where the Gaussian cannot reach alpha >= 1/255 at any pixel are dropped
-(`tile_reachable`).  The rule is a conservative bound: a dropped tile's pixels would all skip the
-Gaussian, so the image is the same with or without it.  It decides which (tile, Gaussian)
-instances exist, an integer outcome, so it is evaluated in float32 with correctly rounded
-operations only (+ - * / sqrt, no fused multiply-add), in the order written below, exactly as the
-CUDA binning evaluates it.
+(`tile_reachable`, a span of tiles per row).  The rule is conservative: a dropped tile's pixels
+would all skip the Gaussian, so the image is the same with or without it.  It decides which
+(tile, Gaussian) instances exist, an integer outcome, so it is evaluated in float32 with
+correctly rounded operations only (+ - * / sqrt, no fused multiply-add), in the order written
+below, exactly as the CUDA binning evaluates it.
 """
 from __future__ import annotations
 
@@ -30,51 +30,59 @@ def alpha_exponent_bound(alpha: np.ndarray) -> np.ndarray:
     return F32(512.0) * (y - F32(1.0))
 
 
-def _q(a, b, c, dx, dy):
-    """a dx^2 + 2 b dx dy + c dy^2, float32, in this rounding order."""
-    return ((a * dx) * dx + ((F32(2.0) * b) * dx) * dy) + (c * dy) * dy
-
-
 def tile_reachable(mean2d, conic, alpha, tx, ty) -> np.ndarray:
-    """Whether a pixel of tile (tx, ty) may see alpha >= 1/255 from each Gaussian (vectorised).
+    """Whether tile (tx, ty) of a Gaussian's rectangle is kept (vectorised over any shape).
 
-    q_min = min over the box of pixel centres [16 tx + 0.5, 16 tx + 15.5] x [...] of
-    a dx^2 + 2b dx dy + c dy^2.  It is 0 when the mean is inside the box.  Otherwise the minimum of
-    this convex form lies on an edge that faces the mean (the segment from the mean to any point
-    of the box first crosses such an edge, and the form grows along it), so only the facing x edge
-    (left if u < x0, right if u > x1) and the facing y edge are evaluated, each at its clamped
-    stationary point dy = clamp((-b / c) dx) or dx = clamp((-b / a) dy).  The tile is dropped when
-    q_min (1 - m) > 2 ln(255 alpha)_bound + 1e-3, m = 1e-4 + 64 * 2^-24 (ac + b^2) / (ac - b^2)
-    (the relative FP32 error of the quadratic form grows with that ratio), unless ac - b^2 <= 0 or
-    m >= 1/2 (never dropped).
+    The row span rule.  With ac - b^2 = det, m = 1e-4 + 2^-18 (ac + b^2) / det (a bound on the
+    relative float32 error of the conic's quadratic form) and lim = 2 ln(255 alpha)_bound + 1e-3,
+    the ellipse {a dx^2 + 2b dx dy + c dy^2 <= Q}, Q = lim (1 + 8m) / (1 - m), contains every
+    pixel centre where alpha_cond exp(-q/2) >= 1/255.  For the tile row ty, whose pixel centres
+    span dy in [ey0, ey1] (relative to the mean), the ellipse's x-extent over that band is
+    attained at the clamped dy of its rightmost and leftmost points (the extent is concave in dy):
+        hx = sqrt(Q c / det), hy = sqrt(Q a / det), dy_r = (-b / c) hx
+        d1 = clamp(dy_r, ey0, ey1),  x_max = (-b d1 + sqrt(max(aQ - det d1^2, 0))) / a + pad_x
+        d2 = clamp(-dy_r, ey0, ey1), x_min = (-b d2 - sqrt(max(aQ - det d2^2, 0))) / a - pad_x
+    with pad_x = 0.05 + 2e-3 hx covering the float32 error of the square roots near the
+    ellipse's top and bottom.  The row is empty when the band misses [-hy - pad_y, hy + pad_y]
+    (pad_y = 0.05 + 2e-3 hy) and everything is dropped when lim < 0 (alpha < 1/255); otherwise
+    the kept tiles are those whose pixel-centre x-range [16 tx + 0.5, 16 tx + 15.5] meets
+    [u + x_min, u + x_max]:  ceil((u + x_min - 15.5) / 16) <= tx <= floor((u + x_max - 0.5) / 16).
+    Nothing is dropped when det <= 0, m >= 1/2, a <= 0 or lim is NaN.  A NaN bound keeps the row.
     """
     u = np.asarray(mean2d[..., 0], F32)
     v = np.asarray(mean2d[..., 1], F32)
     a = np.asarray(conic[..., 0], F32)
     b = np.asarray(conic[..., 1], F32)
     c = np.asarray(conic[..., 2], F32)
-    x0 = (np.asarray(tx, np.int64) * 16).astype(F32) + F32(0.5)
-    x1 = x0 + F32(15.0)
-    y0 = (np.asarray(ty, np.int64) * 16).astype(F32) + F32(0.5)
-    y1 = y0 + F32(15.0)
     with np.errstate(all="ignore"):
-        lo_x, hi_x, lo_y, hi_y = u < x0, u > x1, v < y0, v > y1
-        facing_x, facing_y = lo_x | hi_x, lo_y | hi_y
-        ex0, ex1, ey0, ey1 = x0 - u, x1 - u, y0 - v, y1 - v
-        sx, sy = (-b) / c, (-b) / a  # slopes of the stationary points: dy* = sx dx, dx* = sy dy
-        dx = np.where(lo_x, ex0, ex1)
-        qx = _q(a, b, c, dx, np.fmin(ey1, np.fmax(ey0, sx * dx)))
-        dy = np.where(lo_y, ey0, ey1)
-        qy = _q(a, b, c, np.fmin(ex1, np.fmax(ex0, sy * dy)), dy)
-        best = np.fmin(np.where(facing_x, qx, F32(np.inf)), np.where(facing_y, qy, F32(np.inf)))
-        qmin = np.where(facing_x | facing_y, np.fmax(best, F32(0.0)), F32(0.0))
         ac = a * c
         bb = b * b
         det = ac - bb
-        m = F32(1e-4) + F32(64.0 * 2.0 ** -24) * ((ac + bb) / det)
-        thr = alpha_exponent_bound(alpha)
-        drop = (det > F32(0.0)) & (m < F32(0.5)) & (qmin * (F32(1.0) - m) > thr + F32(1e-3))
-    return ~drop
+        m = F32(1e-4) + F32(2.0 ** -18) * ((ac + bb) / det)
+        lim = alpha_exponent_bound(alpha) + F32(1e-3)
+        never = ~(det > F32(0.0)) | ~(m < F32(0.5)) | ~(a > F32(0.0)) | (lim != lim)
+        Q = (lim * (F32(1.0) + F32(8.0) * m)) / (F32(1.0) - m)
+        hx = np.sqrt((Q * c) / det)
+        hy = np.sqrt((Q * a) / det)
+        dyr = ((-b) / c) * hx
+        padx = F32(0.05) + F32(2e-3) * hx
+        pady = F32(0.05) + F32(2e-3) * hy
+        aQ = a * Q
+        y0 = (np.asarray(ty, np.int64) * 16).astype(F32) + F32(0.5)
+        ey0 = y0 - v
+        ey1 = (y0 + F32(15.0)) - v
+        reach_y = hy + pady
+        row_hit = ~(ey0 > reach_y) & ~(ey1 < -reach_y)
+        d1 = np.fmin(ey1, np.fmax(ey0, dyr))
+        x_max = ((-(b * d1)) + np.sqrt(np.fmax(aQ - (det * d1) * d1, F32(0.0)))) / a + padx
+        d2 = np.fmin(ey1, np.fmax(ey0, -dyr))
+        x_min = ((-(b * d2)) - np.sqrt(np.fmax(aQ - (det * d2) * d2, F32(0.0)))) / a - padx
+        lo = np.ceil(((u + x_min) - F32(15.5)) / F32(16.0))
+        hi = np.floor(((u + x_max) - F32(0.5)) / F32(16.0))
+        txf = np.asarray(tx, np.int64).astype(F32)
+        in_span = ~(txf < lo) & ~(txf > hi)
+        keep = never | (~(lim < F32(0.0)) & row_hit & in_span)
+    return keep
 
 
 def instances(rect: np.ndarray, tiles_x: int, cull=None, block: int = 65536) -> tuple[np.ndarray, np.ndarray]:

@@ -8,14 +8,12 @@
 // followed by emission in that order.  That sort runs over n keys, not K.
 //
 // Tile digit: the instances, emitted in depth order, are radix-sorted stably by tile id
-// (ceil(log2 tiles) bits, 8 per pass).  Instances exist only for the tiles of a Gaussian's
-// rectangle that it may reach (tile_reach.cuh).
+// (ceil(log2 tiles) bits, in passes of equal width <= 8 bits).  Instances exist only inside the
+// per-row spans of tiles a Gaussian may reach (tile_reach.cuh).
 //
-// Each radix pass is reduce-then-scan with no inter-block waiting: an upsweep writes a per-block
-// digit histogram, a device-wide exclusive scan (or, for few blocks, each downsweep block itself)
-// turns it into block offsets, and a downsweep ranks the block's keys stably (warp match +
-// per-warp counters) and scatters them through shared memory so that runs of one digit are
-// written contiguously.
+// Each radix pass is one kernel (digit histograms of all passes are accumulated while the keys are
+// produced): a block ranks its tile of keys stably, finds the keys of each digit in earlier tiles
+// by a decoupled look-back (bounded waits), and writes each digit's run contiguously.
 #include <algorithm>
 
 #include "common.cuh"
@@ -477,12 +475,11 @@ depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ r
 // ------------------------------------------------------------------------------------------
 // Instances in depth order, then a stable sort on the tile digit.
 //
-// Each visible Gaussian (in depth order) tests the tiles of its rectangle clipped to
-// reach_bounds with the exact reachability rule (tile_reach.cuh); one warp handles one Gaussian,
-// 32 tiles per step, so a huge rectangle costs steps, not imbalance.  A first pass counts the kept
-// tiles, an exclusive scan gives each Gaussian its first instance, and a second pass writes the
-// (tile id, Gaussian id) pairs -- each Gaussian's contiguously, in row-major tile order.  The LSD
-// radix passes over the tile id then make the order (tile, depth, id).
+// Each depth-ordered Gaussian walks the rows of its rectangle and takes one span of tiles per row
+// from the reachability rule (tile_reach.cuh): a first pass counts the kept tiles, an exclusive
+// scan gives each Gaussian its first instance, and a second pass writes its (tile id, Gaussian
+// id) pairs contiguously, row-major.  The radix passes over the tile id then make the order
+// (tile, depth, id).
 // ------------------------------------------------------------------------------------------
 
 // Rectangles are clipped to the tile grid, so records that come from the caller rather than
@@ -498,193 +495,142 @@ __device__ __forceinline__ ushort4 clip_rect(ushort4 r, int tiles_x, int tiles_y
 // The tested tiles of a block of kWalkThreads consecutive depth-ordered Gaussians form one
 // sequence -- Gaussian-major, each tested rectangle row-major -- cut into 32-tile words that the
 // block's warps share, so a few large rectangles do not leave one warp with all the work.
-constexpr int kWalkThreads = 256;
-constexpr int kWalkWarps = kWalkThreads / 32;
-constexpr int kEmitChunk = 4 * kWalkThreads;  // bitmask words a block scans at a time
+constexpr int kSpanThreads = 256;
 
-struct BlockWalk {
-  uint32_t incl[kWalkThreads];    // tested tiles of Gaussians 0 .. i of the block
-  uint32_t origin[kWalkThreads];  // tile (x0 | y0 << 16) of Gaussian i's tested rectangle
-  uint32_t width[kWalkThreads];   // its width in tiles
-  Reach reach[kWalkThreads];
+// Kept tiles of each depth-ordered Gaussian (one thread each): its rectangle (clipped to the grid)
+// row by row, each row's span from the reachability rule (tile_reach.cuh).
+__global__ void __launch_bounds__(kSpanThreads)
+span_count_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
+                  int tiles_x, int tiles_y, uint32_t* __restrict__ counts) {
+  const int64_t s = (int64_t)blockIdx.x * kSpanThreads + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t g = order[s];
+  const ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
+  uint32_t c = 0;
+  if (r.z > r.x && r.w > r.y) {
+    const SpanRule rule = span_setup(mean2d[g], conic_opacity[g]);
+    int y0, y1;
+    span_rows(rule, r.y, r.w, &y0, &y1);
+    for (int ty = y0; ty < y1; ++ty) {
+      int x0, x1;
+      span_cols(rule, ty, r.x, r.z, &x0, &x1);
+      c += (uint32_t)(x1 - x0);
+    }
+  }
+  counts[s] = c;
+}
+
+// Digit histograms of the tile ids of a row span id0 .. id0 + len - 1 for the tile sort.  Pass 0
+// (the low digit) cycles through its 2^width values along consecutive ids, so each value gets
+// floor(len / 2^width) plus one over a cyclic range: a per-block constant and a cyclic difference
+// array (at most four adds instead of len).  Higher passes are constant along runs of 2^(p width)
+// ids: one add per run.
+struct DigitAcc {
+  uint32_t (*hist)[kBins];  // passes >= 1
+  int32_t* diff0;           // [kBins + 1] difference array of pass 0
+  uint32_t* all0;           // added to every pass-0 digit
 };
 
-__device__ __forceinline__ uint32_t rect_area(ushort4 r) {
-  return (r.z > r.x && r.w > r.y) ? (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y) : 0u;
-}
-
-// Fills bw from the walk rectangles (and, with want_reach, the reachability parameters) of
-// Gaussians base .. base + kWalkThreads - 1; returns the block's tested-tile count.
-__device__ __forceinline__ uint32_t block_walk_load(BlockWalk& bw, const ushort4* __restrict__ walk,
-                                                    const Reach* __restrict__ reach, int64_t base, int64_t n,
-                                                    bool want_reach) {
-  const int t = threadIdx.x;
-  const int64_t s = base + t;
-  const ushort4 r = s < n ? walk[s] : make_ushort4(0, 0, 0, 0);
-  const uint32_t area = rect_area(r);
-  if (want_reach && area > 0) bw.reach[t] = reach[s];
-  uint32_t total;
-  bw.incl[t] = block_inclusive_scan<uint32_t, kWalkThreads>(area, &total);
-  bw.origin[t] = (uint32_t)r.x | ((uint32_t)r.y << 16);
-  bw.width[t] = (uint32_t)(r.z - r.x);
-  __syncthreads();
-  return total;
-}
-
-// Position f (< total) of the block's sequence -> Gaussian i of the block and its tile (tx, ty).
-__device__ __forceinline__ int block_locate(const BlockWalk& bw, uint32_t f, int* tx, int* ty) {
-  int i = 0;
-#pragma unroll
-  for (int step = kWalkThreads / 2; step >= 1; step >>= 1)
-    if (bw.incl[i + step - 1] <= f) i += step;
-  const uint32_t local = f - (i > 0 ? bw.incl[i - 1] : 0u);
-  const uint32_t w = bw.width[i], o = bw.origin[i];
-  const uint32_t dy = local / w;
-  *tx = (int)((o & 0xffffu) + (local - dy * w));
-  *ty = (int)((o >> 16) + dy);
-  return i;
-}
-
-// Kept bits of word k of the block's sequence (32 tested tiles), computed by the calling warp.
-__device__ __forceinline__ unsigned test_word(const BlockWalk& bw, uint32_t total, uint32_t k) {
-  const uint32_t f = 32u * k + (threadIdx.x & 31);
-  bool kept = false;
-  if (f < total) {
-    int tx, ty;
-    const int i = block_locate(bw, f, &tx, &ty);
-    kept = reach_tile(bw.reach[i], tx, ty);
+__device__ __forceinline__ void count_span_digits(const DigitAcc& acc, uint32_t id0, uint32_t len, int passes,
+                                                  int width) {
+  if (passes == 0 || len == 0) return;
+  const uint32_t period = 1u << width, dmask = period - 1u;
+  const uint32_t full = len >> width, rem = len & dmask;
+  if (full) atomicAdd(acc.all0, full);
+  if (rem) {
+    const uint32_t d0 = id0 & dmask, d1 = d0 + rem;
+    atomicAdd(&acc.diff0[d0], 1);
+    if (d1 <= period) {
+      atomicAdd(&acc.diff0[d1], -1);
+    } else {
+      atomicAdd(&acc.diff0[period], -1);
+      atomicAdd(&acc.diff0[0], 1);
+      atomicAdd(&acc.diff0[d1 - period], -1);
+    }
   }
-  return __ballot_sync(0xffffffffu, kept);
+  for (int p = 1; p < passes; ++p) {
+    const int sh = p * width;
+    uint32_t id = id0;
+    const uint32_t end = id0 + len;
+    while (id < end) {
+      const uint32_t d = (id >> sh) & dmask;
+      const uint32_t next = min(end, ((id >> sh) + 1u) << sh);  // first id with the next digit value
+      atomicAdd(&acc.hist[p][d], next - id);
+      id = next;
+    }
+  }
 }
 
-// Per depth-ordered Gaussian: the rectangle it tests (its rectangle clipped to reach_bounds) and
-// its reachability parameters; per block of kWalkThreads Gaussians: the bitmask words its tested
-// tiles take.
-__global__ void __launch_bounds__(kWalkThreads)
-walk_setup_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
-                  int tiles_x, int tiles_y, ushort4* __restrict__ walk, Reach* __restrict__ reach,
-                  uint32_t* __restrict__ block_words) {
-  const int64_t s = (int64_t)blockIdx.x * kWalkThreads + threadIdx.x;
-  uint32_t area = 0;
+// Writes each depth-ordered Gaussian's (tile id, Gaussian id) pairs from its first instance (one
+// thread each), row-major over its spans, and accumulates the tile-digit histograms of what it
+// writes.  With vec, keys and vals are 16-byte aligned and runs are stored four at a time.
+// Positions >= cap are dropped.
+__global__ void __launch_bounds__(kSpanThreads)
+span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+                 const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
+                 int tiles_x, int tiles_y, const uint64_t* __restrict__ first, int64_t cap,
+                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, bool vec, int passes, int width,
+                 uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[kMaxPasses][kBins];
+  __shared__ int32_t s_diff0[kBins + 1];
+  __shared__ uint32_t s_all0;
+  for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kSpanThreads) (&s_hist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i <= kBins; i += kSpanThreads) s_diff0[i] = 0;
+  if (threadIdx.x == 0) s_all0 = 0;
+  __syncthreads();
+  const DigitAcc acc{s_hist, s_diff0, &s_all0};
+  const int64_t s = (int64_t)blockIdx.x * kSpanThreads + threadIdx.x;
   if (s < n) {
     const uint32_t g = order[s];
-    ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
-    if (r.z > r.x && r.w > r.y) {
-      const Reach rc = reach_setup(mean2d[g], conic_opacity[g]);
-      reach[s] = rc;
-      r = reach_bounds(rc, r);
-      area = rect_area(r);
-    }
-    walk[s] = r;
-  }
-  uint32_t total;
-  block_inclusive_scan<uint32_t, kWalkThreads>(area, &total);
-  if (threadIdx.x == 0) block_words[blockIdx.x] = (total + 31u) / 32u;
-}
-
-// Tests every tested tile once: kept count per block and, where the block's words fit in
-// `bits_cap`, its kept bitmask (bit l of word k: position 32 k + l of the block's sequence).
-__global__ void __launch_bounds__(kWalkThreads)
-test_tiles_kernel(const ushort4* __restrict__ walk, const Reach* __restrict__ reach, int64_t n,
-                  const uint64_t* __restrict__ block_word_first, uint64_t bits_cap, uint32_t* __restrict__ bits,
-                  uint32_t* __restrict__ block_kept) {
-  __shared__ BlockWalk bw;
-  __shared__ uint32_t s_kept[kWalkWarps];
-  const uint32_t total = block_walk_load(bw, walk, reach, (int64_t)blockIdx.x * kWalkThreads, n, true);
-  const uint32_t words = (total + 31u) / 32u;
-  const uint64_t w0 = block_word_first[blockIdx.x];
-  const bool store = w0 + words <= bits_cap;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t c = 0;
-  for (uint32_t k = warp; k < words; k += kWalkWarps) {
-    const unsigned b = test_word(bw, total, k);
-    if (store && lane == 0) bits[w0 + k] = b;
-    c += __popc(b);
-  }
-  if (lane == 0) s_kept[warp] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t sum = 0;
-#pragma unroll
-    for (int w = 0; w < kWalkWarps; ++w) sum += s_kept[w];
-    block_kept[blockIdx.x] = sum;
-  }
-}
-
-// Writes each block's (tile id, Gaussian id) pairs from the block's first instance in sequence
-// order (Gaussian-major in depth order, row-major within a rectangle), from the bitmask of
-// test_tiles_kernel or, for blocks whose words did not fit, by testing again with the same
-// decisions.  Positions >= cap are dropped.
-__global__ void __launch_bounds__(kWalkThreads)
-emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ walk,
-            const Reach* __restrict__ reach, int64_t n, const uint64_t* __restrict__ block_word_first,
-            uint64_t bits_cap, const uint32_t* __restrict__ bits, const uint64_t* __restrict__ block_first,
-            int tiles_x, int64_t cap, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int passes,
-            int width, uint32_t* __restrict__ hist) {
-  __shared__ BlockWalk bw;
-  __shared__ uint32_t s_hist[kMaxPasses][kBins];
-  __shared__ uint32_t s_gid[kWalkThreads];
-  __shared__ uint32_t s_words[kEmitChunk];
-  __shared__ uint32_t s_before[kEmitChunk];
-  const int64_t base = (int64_t)blockIdx.x * kWalkThreads;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const uint64_t w0 = block_word_first[blockIdx.x];
-  s_gid[t] = base + t < n ? order[base + t] : 0u;
-  for (int i = t; i < kMaxPasses * kBins; i += kWalkThreads) (&s_hist[0][0])[i] = 0;
-  const uint32_t total = block_walk_load(bw, walk, reach, base, n, true);
-  const uint32_t words = (total + 31u) / 32u;
-  const bool stored = w0 + words <= bits_cap;
-  uint64_t pos = block_first[blockIdx.x];
-  const unsigned lt = lanemask_lt();
-  for (uint32_t c0 = 0; c0 < words; c0 += kEmitChunk) {
-    const uint32_t cw = min((uint32_t)kEmitChunk, words - c0);
-    if (stored) {
-      for (uint32_t i = t; i < cw; i += kWalkThreads) s_words[i] = bits[w0 + c0 + i];
-    } else {
-      for (uint32_t i = warp; i < cw; i += kWalkWarps) {
-        const unsigned b = test_word(bw, total, c0 + i);
-        if (lane == 0) s_words[i] = b;
-      }
-    }
-    __syncthreads();
-    // kept instances before each word of the chunk (4 consecutive words per thread)
-    uint32_t cnt[4], run = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t i = 4u * t + q;
-      cnt[q] = i < cw ? __popc(s_words[i]) : 0u;
-      run += cnt[q];
-    }
-    uint32_t chunk_total;
-    const uint32_t incl = block_inclusive_scan<uint32_t, kWalkThreads>(run, &chunk_total);
-    uint32_t acc = incl - run;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t i = 4u * t + q;
-      if (i < cw) s_before[i] = acc;
-      acc += cnt[q];
-    }
-    __syncthreads();
-    for (uint32_t i = warp; i < cw; i += kWalkWarps) {
-      const unsigned b = s_words[i];
-      if (b == 0u) continue;  // uniform over the warp
-      uint32_t key = 0;
-      bool put = false;
-      if ((b >> lane) & 1u) {
-        int tx, ty;
-        const int gi = block_locate(bw, 32u * (c0 + i) + lane, &tx, &ty);
-        const uint64_t p = pos + s_before[i] + __popc(b & lt);
-        if (p < (uint64_t)cap) {
-          key = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx;
-          keys[p] = key;
-          vals[p] = s_gid[gi];
-          put = true;
+    const ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
+    uint64_t pos = first[s];
+    if (r.z > r.x && r.w > r.y && pos < (uint64_t)cap) {
+      const SpanRule rule = span_setup(mean2d[g], conic_opacity[g]);
+      int y0, y1;
+      span_rows(rule, r.y, r.w, &y0, &y1);
+      const uint4 g4 = make_uint4(g, g, g, g);
+      for (int ty = y0; ty < y1 && pos < (uint64_t)cap; ++ty) {
+        int x0, x1;
+        span_cols(rule, ty, r.x, r.z, &x0, &x1);
+        const int64_t room = cap - (int64_t)pos;
+        const uint32_t len = (uint32_t)((int64_t)(x1 - x0) < room ? (int64_t)(x1 - x0) : room);
+        const uint32_t id0 = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0;
+        uint32_t k = 0;
+        if (vec) {
+          for (; k < len && ((pos + k) & 3u); ++k) {
+            keys[pos + k] = id0 + k;
+            vals[pos + k] = g;
+          }
+          for (; k + 4 <= len; k += 4) {
+            const uint32_t id = id0 + k;
+            *reinterpret_cast<uint4*>(keys + pos + k) = make_uint4(id, id + 1, id + 2, id + 3);
+            *reinterpret_cast<uint4*>(vals + pos + k) = g4;
+          }
         }
+        for (; k < len; ++k) {
+          keys[pos + k] = id0 + k;
+          vals[pos + k] = g;
+        }
+        count_span_digits(acc, id0, len, passes, width);
+        pos += len;
       }
-      count_digits(s_hist, key, put, passes, width);
     }
-    pos += chunk_total;
+  }
+  __syncthreads();
+  if (passes > 0) {  // pass 0 from the difference array: a running sum over the digits
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int period = 1 << width;
+      int carry = 0;
+      for (int d0 = 0; d0 < period; d0 += 32) {
+        const int d = d0 + lane;
+        const int v = d < period ? s_diff0[d] : 0;
+        const int incl = warp_inclusive_scan(v) + carry;
+        if (d < period) s_hist[0][d] = (uint32_t)incl + s_all0;
+        carry = __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
     __syncthreads();
   }
   flush_digits(s_hist, passes, hist);
@@ -712,22 +658,11 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   int bits = 0;
   while ((int64_t(1) << bits) < p.num_tiles) ++bits;
   p.tile_bits = bits;
-  p.chunk = 0;
-  p.chunks = 0;
-  const int64_t groups = (n + 31) / 32;
-  p.hist_blocks = 0;
-  p.partial_cap = (groups + kScanChunk - 1) / kScanChunk + 1;
+  p.partial_cap = (n + kScanChunk - 1) / kScanChunk + 1;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) { p.off_dkeys[k] = off; off += align256(sizeof(uint32_t) * n); }
   for (int k = 0; k < 2; ++k) { p.off_dvals[k] = off; off += align256(sizeof(uint32_t) * n); }
-  p.bits_cap = (uint64_t)(capacity / 4 + groups + 1);
-  p.off_gwords = off; off += align256(sizeof(uint32_t) * groups);
-  p.off_gwfirst = off; off += align256(sizeof(uint64_t) * groups);
-  p.off_gkept = off; off += align256(sizeof(uint32_t) * groups);
-  p.off_gfirst = off; off += align256(sizeof(uint64_t) * groups);
-  p.off_bits = off; off += align256(sizeof(uint32_t) * p.bits_cap);
-  p.off_walk = off; off += align256(sizeof(uint64_t) * n);
-  p.off_reach = off; off += align256(sizeof(Reach) * n);
+  p.off_first = off; off += align256(sizeof(uint64_t) * n);
   p.off_ikeys[0] = off; off += align256(sizeof(uint32_t) * capacity);
   p.off_ikeys[1] = off; off += align256(sizeof(uint32_t) * capacity);
   p.off_ivals = off; off += align256(sizeof(uint32_t) * capacity);
@@ -746,13 +681,7 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
                         reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[1])};
   uint32_t* dvals[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dvals[0]),
                         reinterpret_cast<uint32_t*>(ws + plan.off_dvals[1])};
-  uint32_t* gwords = reinterpret_cast<uint32_t*>(ws + plan.off_gwords);
-  uint64_t* gwfirst = reinterpret_cast<uint64_t*>(ws + plan.off_gwfirst);
-  uint32_t* gkept = reinterpret_cast<uint32_t*>(ws + plan.off_gkept);
-  uint64_t* gfirst = reinterpret_cast<uint64_t*>(ws + plan.off_gfirst);
-  uint32_t* bits = reinterpret_cast<uint32_t*>(ws + plan.off_bits);
-  ushort4* walk = reinterpret_cast<ushort4*>(ws + plan.off_walk);
-  Reach* reach = reinterpret_cast<Reach*>(ws + plan.off_reach);
+  uint64_t* first = reinterpret_cast<uint64_t*>(ws + plan.off_first);
   uint32_t* sort_scratch = reinterpret_cast<uint32_t*>(ws + plan.off_sort);
   uint32_t* err = reinterpret_cast<uint32_t*>(ws + plan.off_err);
   uint64_t* partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
@@ -765,23 +694,18 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   if (n == 0) return cudaMemsetAsync(out.num_instances, 0, sizeof(int64_t), st);
-  const int tb = 256;
-  const unsigned gb = (unsigned)((n + tb - 1) / tb);
+  const unsigned gb = (unsigned)((n + kRadixThreads - 1) / kRadixThreads);
   // 1. Gaussians by float32 depth (stable; culled ones last).
   e = sort_clear(sort_scratch, n, 32, st);
   if (e != cudaSuccess) return e;
   depth_keys_kernel<<<gb, kRadixThreads, 0, st>>>(proj.depth, rect, n, dkeys[0], dvals[0], sort_scratch);
   const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_scratch, err, true, st);
   const uint32_t* order = dvals[dcur];
-  // 2. Tiles to test; each tested once (kept bitmask + kept count per block of kWalkThreads
-  //    Gaussians); first instance of each block; K.
-  const int64_t wblocks = (n + kWalkThreads - 1) / kWalkThreads;
-  walk_setup_kernel<<<(unsigned)wblocks, kWalkThreads, 0, st>>>(order, rect, m2, co, n, tiles_x, tiles_y, walk,
-                                                                reach, gwords);
-  e = exclusive_scan<uint32_t, uint64_t>(gwords, wblocks, gwfirst, partials, nullptr, st);
-  if (e != cudaSuccess) return e;
-  test_tiles_kernel<<<(unsigned)wblocks, kWalkThreads, 0, st>>>(walk, reach, n, gwfirst, plan.bits_cap, bits, gkept);
-  e = exclusive_scan<uint32_t, uint64_t>(gkept, wblocks, gfirst, partials, out.num_instances, st);
+  // 2. Kept tiles per Gaussian (row spans); first instance of each; K.
+  uint32_t* counts = dkeys[dcur ^ 1];
+  const unsigned gs = (unsigned)((n + kSpanThreads - 1) / kSpanThreads);
+  span_count_kernel<<<gs, kSpanThreads, 0, st>>>(order, rect, m2, co, n, tiles_x, tiles_y, counts);
+  e = exclusive_scan<uint32_t, uint64_t>(counts, n, first, partials, out.num_instances, st);
   if (e != cudaSuccess) return e;
   // 3. Instances in depth order, into the buffer that makes the tile passes end in `out`.
   const int passes = radix_pass_count(plan.tile_bits);
@@ -797,15 +721,16 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   }
   e = sort_clear(sort_scratch, plan.capacity, plan.tile_bits, st);
   if (e != cudaSuccess) return e;
-  emit_kernel<<<(unsigned)wblocks, kWalkThreads, 0, st>>>(order, walk, reach, n, gwfirst, plan.bits_cap, bits,
-                                                          gfirst, tiles_x, plan.capacity, ikeys[0], ivals[0], passes,
-                                                          radix_digit_width(plan.tile_bits), sort_scratch);
+  const bool vec = ((reinterpret_cast<uintptr_t>(ikeys[0]) | reinterpret_cast<uintptr_t>(ivals[0])) & 15u) == 0;
+  span_emit_kernel<<<gs, kSpanThreads, 0, st>>>(order, rect, m2, co, n, tiles_x, tiles_y, first, plan.capacity,
+                                                ikeys[0], ivals[0], vec, passes, radix_digit_width(plan.tile_bits),
+                                                sort_scratch);
   // 4. Stable sort by tile id; 5. tile ranges.
   radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_scratch, err, true, st);
   if (plan.capacity > 0) {
-    const unsigned gr = (unsigned)((plan.capacity + tb - 1) / tb);
-    ranges_kernel<<<gr, tb, 0, st>>>(out_keys, out.num_instances, plan.capacity,
-                                     reinterpret_cast<uint2*>(out.ranges));
+    const unsigned gr = (unsigned)((plan.capacity + 255) / 256);
+    ranges_kernel<<<gr, 256, 0, st>>>(out_keys, out.num_instances, plan.capacity,
+                                      reinterpret_cast<uint2*>(out.ranges));
   }
   return cudaGetLastError();
 }

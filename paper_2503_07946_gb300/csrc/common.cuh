@@ -39,13 +39,8 @@ struct BinPlan {
   int64_t capacity;
   int num_tiles;
   int tile_bits;
-  int chunk;       // unused
-  int64_t chunks;  // unused
   // workspace carve-up (byte offsets)
-  size_t off_dkeys[2], off_dvals[2], off_gwords, off_gwfirst, off_gkept, off_gfirst, off_bits, off_walk,
-      off_reach, off_ikeys[2], off_ivals, off_err, off_sort, off_partials, total;
-  uint64_t bits_cap;  // 32-bit words of kept-tile bitmask available
-  int64_t hist_blocks;  // unused
+  size_t off_dkeys[2], off_dvals[2], off_first, off_ikeys[2], off_ivals, off_err, off_sort, off_partials, total;
   int64_t partial_cap;  // entries available for scan partials
 };
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);

@@ -484,28 +484,68 @@ def test_alpha_exponent_bound_is_an_upper_bound_within_1p1_percent():
     assert np.all(bound <= exact * 1.011 + 2e-4)
 
 
-def test_dropped_tiles_have_no_pixel_at_or_above_the_alpha_threshold():
-    """Brute force over all 256 pixel centres of every tested tile, in float64."""
-    rng = np.random.default_rng(21)
-    n = 4000
-    mean2d = rng.uniform(-20, 84, size=(n, 2)).astype(np.float32)
-    sx, sy = rng.uniform(0.6, 30, n), rng.uniform(0.6, 30, n)
-    rho = rng.uniform(-0.99, 0.99, n)
+def _stress_gaussians(rng, n):
+    """Screen-space Gaussians spanning the shapes the rule must survive: tiny (0.3 px), huge
+    (300 px), needle-thin (aspect 1e-3), correlation up to 0.99999, alpha just above 1/255."""
+    mean2d = rng.uniform(-40, 140, size=(n, 2)).astype(np.float32)
+    kind = rng.integers(0, 4, n)
+    sx = np.where(kind == 0, rng.uniform(0.3, 3, n), np.where(kind == 1, rng.uniform(3, 40, n),
+                  np.where(kind == 2, rng.uniform(40, 300, n), rng.uniform(0.5, 60, n))))
+    sy = np.where(kind == 3, sx * rng.uniform(0.001, 0.05, n), rng.uniform(0.3, 60, n))
+    rho = np.where(rng.random(n) < 0.3, rng.choice([-1, 1], n) * rng.uniform(0.99, 0.99999, n),
+                   rng.uniform(-0.99, 0.99, n))
     cov = np.stack([sx * sx, rho * sx * sy, sy * sy], 1)
     det = cov[:, 0] * cov[:, 2] - cov[:, 1] ** 2
     conic = np.stack([cov[:, 2] / det, -cov[:, 1] / det, cov[:, 0] / det], 1).astype(np.float32)
-    alpha = rng.uniform(1 / 255, 1.0, n).astype(np.float32)
-    tx, ty = rng.integers(0, 4, n), rng.integers(0, 4, n)
-    keep = binning.tile_reachable(mean2d, conic, alpha, tx, ty)
-    dropped = np.nonzero(~keep)[0]
-    assert 0.2 * n < len(dropped) < 0.95 * n
+    alpha = np.where(rng.random(n) < 0.3, (1 / 255) * (1 + rng.uniform(0, 0.05, n)),
+                     rng.uniform(1 / 255, 1.0, n)).astype(np.float32)
+    return mean2d, conic, alpha
+
+
+def test_dropped_tiles_have_no_pixel_at_or_above_the_alpha_threshold():
+    """Brute force, in float64, over all 256 pixel centres of each of the 64 tiles of an 8 x 8 grid
+    for 3000 stress Gaussians: every tile holding a pixel with alpha >= 1/255 is kept, and the
+    rule keeps at most 6% more tiles than that exact set."""
+    rng = np.random.default_rng(5)
+    n, T = 3000, 8
+    mean2d, conic, alpha = _stress_gaussians(rng, n)
+    tx, ty = np.meshgrid(np.arange(T), np.arange(T), indexing="xy")
+    G = np.repeat(np.arange(n), T * T)
+    TX, TY = np.tile(tx.ravel(), n), np.tile(ty.ravel(), n)
+    keep = binning.tile_reachable(mean2d[G], conic[G], alpha[G], TX, TY)
     px, py = np.meshgrid(np.arange(16) + 0.5, np.arange(16) + 0.5, indexing="xy")
-    for i in dropped:
-        dx = tx[i] * 16 + px - float(mean2d[i, 0])
-        dy = ty[i] * 16 + py - float(mean2d[i, 1])
-        a, b, c = conic[i].astype(np.float64)
-        al = float(alpha[i]) * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
-        assert al.max() < 1 / 255, (i, al.max())
+    px, py = px.ravel(), py.ravel()
+    reach = np.zeros(len(G), bool)
+    for s0 in range(0, len(G), 20000):
+        g = G[s0:s0 + 20000]
+        dx = TX[s0:s0 + 20000, None] * 16 + px[None] - mean2d[g, 0:1].astype(np.float64)
+        dy = TY[s0:s0 + 20000, None] * 16 + py[None] - mean2d[g, 1:2].astype(np.float64)
+        a, b, c = (conic[g, k:k + 1].astype(np.float64) for k in range(3))
+        al = alpha[g, None].astype(np.float64) * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+        reach[s0:s0 + 20000] = al.max(1) >= 1 / 255
+    assert not np.any(reach & ~keep), np.nonzero(reach & ~keep)[0][:5]
+    assert reach.sum() > 10000 and keep.sum() <= 1.06 * reach.sum()
+
+
+def test_row_span_rule_keeps_contiguous_spans_and_special_cases():
+    """Kept tiles of a row form one contiguous run; alpha < 1/255 drops everything; a conic that
+    is not positive definite keeps everything."""
+    rng = np.random.default_rng(7)
+    n = 500
+    mean2d, conic, alpha = _stress_gaussians(rng, n)
+    tx = np.arange(-4, 14)
+    for i in range(n):
+        for row in range(-2, 10):
+            k = binning.tile_reachable(mean2d[i:i + 1], conic[i:i + 1], alpha[i:i + 1], tx, np.full_like(tx, row))
+            idx = np.nonzero(k)[0]
+            assert len(idx) == 0 or idx[-1] - idx[0] + 1 == len(idx)
+    low = binning.tile_reachable(mean2d[:20], conic[:20], np.full(20, 0.5 / 255, np.float32), np.zeros(20, int),
+                                 np.zeros(20, int))
+    assert not low.any()
+    bad = conic[:20].copy()
+    bad[:, 1] = np.sqrt(bad[:, 0] * bad[:, 2]) * 1.01  # det < 0
+    far = np.full((20, 2), 1e4, np.float32)
+    assert binning.tile_reachable(far, bad, alpha[:20], np.zeros(20, int), np.zeros(20, int)).all()
 
 
 def test_reachability_drops_a_large_share_of_rectangle_tiles_on_a_scene():
