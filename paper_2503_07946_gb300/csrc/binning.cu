@@ -217,7 +217,7 @@ __device__ __forceinline__ void store_status(uint32_t* p, uint32_t v) {
 }
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kRadixThreads, 4)
+__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 16 ? 4 : 6)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* nptr,
                 int64_t n_static, int64_t cap, int shift, int width, const uint32_t* __restrict__ digit_hist,

@@ -27,33 +27,46 @@ struct FwdArgs {
   unsigned long long* n_evaluated;  // optional work counter
 };
 
-struct Pixel {
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  uint32_t last = 0, evaluated = 0;
-  bool done;
+// The two pixels of a thread (rows r and r + 8 of one column) as pairs, so that the arithmetic
+// they share runs as paired FP32 operations (each element correctly rounded, identical to the
+// scalar operations the backward uses).
+struct PixelPair {
+  float2 T = make_float2(1.f, 1.f), c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f),
+         c2 = make_float2(0.f, 0.f);
+  uint32_t last0 = 0, last1 = 0, evaluated = 0;
+  bool done0, done1;
 };
 
-// One (pixel, Gaussian) evaluation written without branches, so that a thread's two pixels
-// interleave: the pixel takes the Gaussian iff it is still running, the exponent is <= 0 and
-// alpha >= 1/255; if that would take T below 1e-4 the pixel stops instead (without blending).
+// One Gaussian evaluated at both pixels, without branches: a pixel takes the Gaussian iff it is
+// still running, the exponent is <= 0 and alpha >= 1/255; if that would take T below 1e-4 the
+// pixel stops instead (without blending).  The exponent is qa dx^2 + dy (qc dy + qb dx), as in
+// splat_power2.
 template <bool kCount>
-__device__ __forceinline__ void blend(Pixel& px, const float4& q, const float4& c, float dx, float dy,
-                                      uint32_t pos1) {
-  const float p2 = splat_power2(q, dx, dy);
-  const float al = fminf(kAlphaMax, __fmul_rn(q.w, ex2_approx(p2)));
-  const float Tn = __fmul_rn(px.T, __fsub_rn(1.f, al));
-  const bool live = !px.done;
-  const bool hit = live && p2 <= 0.f && al >= kAlphaMin;
-  const bool stop = hit && Tn < kTMin;
-  const bool take = hit && !stop;
-  const float w = take ? al * px.T : 0.f;
-  if (kCount) px.evaluated += live ? 1u : 0u;
-  px.c0 += c.x * w;
-  px.c1 += c.y * w;
-  px.c2 += c.z * w;
-  px.T = take ? Tn : px.T;
-  px.last = take ? pos1 : px.last;
-  px.done = px.done || stop;
+__device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const float4& c, float dx, float2 dy,
+                                       uint32_t pos1) {
+  const float a = __fmul_rn(__fmul_rn(q.x, dx), dx);
+  const float bx = __fmul_rn(q.y, dx);
+  const float2 t = __ffma2_rn(make_float2(q.z, q.z), dy, make_float2(bx, bx));
+  const float2 p2 = __ffma2_rn(dy, t, make_float2(a, a));
+  const float2 e = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+  const float2 m = __fmul2_rn(make_float2(q.w, q.w), e);
+  const float2 al = make_float2(fminf(kAlphaMax, m.x), fminf(kAlphaMax, m.y));
+  const float2 Tn = __fmul2_rn(px.T, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-al.x, -al.y)));
+  const float2 aT = __fmul2_rn(al, px.T);
+  const bool hit0 = !px.done0 && p2.x <= 0.f && al.x >= kAlphaMin;
+  const bool hit1 = !px.done1 && p2.y <= 0.f && al.y >= kAlphaMin;
+  const bool stop0 = hit0 && Tn.x < kTMin, stop1 = hit1 && Tn.y < kTMin;
+  const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
+  if (kCount) px.evaluated += (px.done0 ? 0u : 1u) + (px.done1 ? 0u : 1u);
+  const float2 w = make_float2(take0 ? aT.x : 0.f, take1 ? aT.y : 0.f);
+  px.c0 = __ffma2_rn(make_float2(c.x, c.x), w, px.c0);
+  px.c1 = __ffma2_rn(make_float2(c.y, c.y), w, px.c1);
+  px.c2 = __ffma2_rn(make_float2(c.z, c.z), w, px.c2);
+  px.T = make_float2(take0 ? Tn.x : px.T.x, take1 ? Tn.y : px.T.y);
+  px.last0 = take0 ? pos1 : px.last0;
+  px.last1 = take1 ? pos1 : px.last1;
+  px.done0 = px.done0 || stop0;
+  px.done1 = px.done1 || stop1;
 }
 
 template <bool kCount>
@@ -72,11 +85,12 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
   const uint2 range = a.ranges[tile];
   const int n = (int)(range.y - range.x);
 
-  Pixel p0, p1;
-  p0.done = !(px < a.width && py0 < a.height);
-  p1.done = !(px < a.width && py1 < a.height);
+  PixelPair pp;
+  pp.done0 = !(px < a.width && py0 < a.height);
+  pp.done1 = !(px < a.width && py1 < a.height);
+  const float2 fy = make_float2(fy0, fy1);
   for (int base = 0; base < n; base += kThreads) {
-    if (__syncthreads_count(p0.done && p1.done) == kThreads) break;
+    if (__syncthreads_count(pp.done0 && pp.done1) == kThreads) break;
     // stage the next 128 instances of the tile's list
     const int j = base + threadIdx.x;
     if (j < n) {
@@ -87,9 +101,9 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
     }
     const int cnt = min(kThreads, n - base);
     __syncthreads();
-    if (!(p0.done && p1.done)) {
+    if (!(pp.done0 && pp.done1)) {
       // Entries past cnt are never read: the batch is padded by predication.  The stop test runs
-      // every 4 Gaussians; a stopped pixel ignores the rest (blend is a no-op once done).
+      // every 4 Gaussians; a stopped pixel ignores the rest (blend2 is a no-op for it).
       for (int k0 = 0; k0 < cnt; k0 += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -101,32 +115,32 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
             const uint32_t pos1 = (uint32_t)(base + k) + 1u;
             // offsets exactly as the backward forms them, so both passes take the same decisions
             const float dx = fx - m.x;
-            blend<kCount>(p0, q, c, dx, fy0 - m.y, pos1);
-            blend<kCount>(p1, q, c, dx, fy1 - m.y, pos1);
+            blend2<kCount>(pp, q, c, dx, __fadd2_rn(fy, make_float2(-m.y, -m.y)), pos1);
           }
         }
-        if (p0.done && p1.done) break;
+        if (pp.done0 && pp.done1) break;
       }
     }
   }
   if (kCount) {
-    unsigned long long e = (unsigned long long)p0.evaluated + p1.evaluated;
+    unsigned long long e = (unsigned long long)pp.evaluated;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
     if (lane == 0 && e) atomicAdd(a.n_evaluated, e);
   }
-  const Pixel* pp[2] = {&p0, &p1};
+  const float Ts[2] = {pp.T.x, pp.T.y};
+  const float C0[2] = {pp.c0.x, pp.c0.y}, C1[2] = {pp.c1.x, pp.c1.y}, C2[2] = {pp.c2.x, pp.c2.y};
+  const uint32_t lasts[2] = {pp.last0, pp.last1};
   const int rows[2] = {py0, py1};
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     if (px < a.width && rows[r] < a.height) {
       const int pix = rows[r] * a.width + px;
-      const Pixel& q = *pp[r];
-      a.image[3 * pix + 0] = q.c0 + q.T * a.bg[0];
-      a.image[3 * pix + 1] = q.c1 + q.T * a.bg[1];
-      a.image[3 * pix + 2] = q.c2 + q.T * a.bg[2];
-      a.final_T[pix] = q.T;
-      a.n_contrib[pix] = q.last;
+      a.image[3 * pix + 0] = C0[r] + Ts[r] * a.bg[0];
+      a.image[3 * pix + 1] = C1[r] + Ts[r] * a.bg[1];
+      a.image[3 * pix + 2] = C2[r] + Ts[r] * a.bg[2];
+      a.final_T[pix] = Ts[r];
+      a.n_contrib[pix] = lasts[r];
     }
   }
 }
