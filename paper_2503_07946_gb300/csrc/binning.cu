@@ -85,6 +85,7 @@ __device__ __forceinline__ T block_inclusive_scan(T x, T* total) {
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const TIn* in, int64_t n,
                                                                     TOut* partials) {
+  griddep_wait();
   const int64_t base = (int64_t)blockIdx.x * kScanChunk;
   TOut sum = 0;
 #pragma unroll
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const TIn* in
 
 template <typename T>
 __global__ void __launch_bounds__(1024) scan_partials_kernel(T* partials, int64_t nb, int64_t* total_out) {
+  griddep_wait();
   T carry = 0;
   for (int64_t base = 0; base < nb; base += 1024) {
     const int64_t i = base + threadIdx.x;
@@ -114,6 +116,7 @@ __global__ void __launch_bounds__(1024) scan_partials_kernel(T* partials, int64_
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const TIn* in, int64_t n,
                                                                   const TOut* partials, TOut* out) {
+  griddep_wait();
   __shared__ TOut s[kScanChunk];
   const int64_t base = (int64_t)blockIdx.x * kScanChunk;
 #pragma unroll
@@ -147,10 +150,12 @@ cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partia
                            int64_t* total_out, cudaStream_t st) {
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
   TOut* part = reinterpret_cast<TOut*>(partials);
-  if (nb > 0) scan_reduce_kernel<TIn, TOut><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, part);
-  scan_partials_kernel<TOut><<<1, 1024, 0, st>>>(part, nb, total_out);
-  if (nb > 0) scan_down_kernel<TIn, TOut><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, part, out);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (nb > 0) e = launch_pdl(scan_reduce_kernel<TIn, TOut>, dim3((unsigned)nb), dim3(kScanThreads), 0, st, in, n, part);
+  if (e == cudaSuccess) e = launch_pdl(scan_partials_kernel<TOut>, dim3(1), dim3(1024), 0, st, part, nb, total_out);
+  if (e == cudaSuccess && nb > 0)
+    e = launch_pdl(scan_down_kernel<TIn, TOut>, dim3((unsigned)nb), dim3(kScanThreads), 0, st, in, n, part, out);
+  return e;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -192,6 +197,7 @@ constexpr int kMaxPasses = 4;
 __global__ void __launch_bounds__(kRadixThreads)
 digit_hist_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t n_static, int64_t cap,
                   int passes, int width, uint32_t* __restrict__ hist) {
+  griddep_wait();
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
@@ -222,6 +228,7 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* nptr,
                 int64_t n_static, int64_t cap, int shift, int width, const uint32_t* __restrict__ digit_hist,
                 uint32_t* status, uint32_t* ticket, uint32_t* err) {
+  griddep_wait();
   constexpr int TILE = kRadixThreads * ITEMS;
   __shared__ uint32_t s_keys[TILE];
   __shared__ uint32_t s_vals[TILE];
@@ -430,18 +437,9 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
   for (int p = 0; p < passes; ++p) {
     uint32_t* stp = status + (size_t)p * nblocks * kBins;
     const int shift = p * width;
-    if (items == 16)
-      onesweep_kernel<16><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
-          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, width,
-          hist + p * kBins, stp, tickets + p, err);
-    else if (items == 8)
-      onesweep_kernel<8><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
-          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, width,
-          hist + p * kBins, stp, tickets + p, err);
-    else
-      onesweep_kernel<4><<<(unsigned)nblocks, kRadixThreads, 0, st>>>(
-          keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], nptr, n_static, cap, shift, width,
-          hist + p * kBins, stp, tickets + p, err);
+    auto* kern = items == 16 ? onesweep_kernel<16> : items == 8 ? onesweep_kernel<8> : onesweep_kernel<4>;
+    launch_pdl(kern, dim3((unsigned)nblocks), dim3(kRadixThreads), 0, st, keys[cur], vals[cur], keys[cur ^ 1],
+               vals[cur ^ 1], nptr, n_static, cap, shift, width, hist + p * kBins, stp, tickets + p, err);
     cur ^= 1;
   }
   return cur;
@@ -451,10 +449,29 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
 // Binning-specific kernels.
 // ------------------------------------------------------------------------------------------
 
+// Zeroes the words binning accumulates into or reads before writing: the tile ranges, the error
+// word, the instance count (when there are no Gaussians) and both sorts' scratch.  One kernel
+// instead of several memsets keeps the render's launches a chain of kernels.
+struct ClearJob {
+  uint32_t* ptr[5];
+  size_t words[5];
+};
+
+__global__ void __launch_bounds__(256) clear_kernel(const ClearJob job) {
+  griddep_wait();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int k = 0; k < 5; ++k) {
+    uint32_t* p = job.ptr[k];
+    if (p == nullptr) continue;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < job.words[k]; i += stride) p[i] = 0u;
+  }
+}
+
 // Depth keys of the Gaussians (culled ones last) and their digit histograms for the depth sort.
 __global__ void __launch_bounds__(kRadixThreads)
 depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ rect, int64_t n,
                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ hist) {
+  griddep_wait();
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
@@ -503,6 +520,7 @@ __global__ void __launch_bounds__(kSpanThreads)
 span_count_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
                   const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
                   int tiles_x, int tiles_y, uint32_t* __restrict__ counts) {
+  griddep_wait();
   const int64_t s = (int64_t)blockIdx.x * kSpanThreads + threadIdx.x;
   if (s >= n) return;
   const uint32_t g = order[s];
@@ -572,6 +590,7 @@ span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__
                  int tiles_x, int tiles_y, const uint64_t* __restrict__ first, int64_t cap,
                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, bool vec, int passes, int width,
                  uint32_t* __restrict__ hist) {
+  griddep_wait();
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   __shared__ int32_t s_diff0[kBins + 1];
   __shared__ uint32_t s_all0;
@@ -638,6 +657,7 @@ span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t cap,
                               uint2* __restrict__ ranges) {
+  griddep_wait();
   const int64_t n = element_count(nptr, 0, cap);
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -667,7 +687,8 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   p.off_ikeys[1] = off; off += align256(sizeof(uint32_t) * capacity);
   p.off_ivals = off; off += align256(sizeof(uint32_t) * capacity);
   p.off_err = off; off += 256;
-  p.off_sort = off; off += align256(std::max(sort_scratch_bytes(n, 32), sort_scratch_bytes(capacity, bits)));
+  p.off_sort_d = off; off += align256(sort_scratch_bytes(n, 32));
+  p.off_sort_t = off; off += align256(sort_scratch_bytes(capacity, bits));
   p.off_partials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
   p.total = off;
   return p;
@@ -682,29 +703,38 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   uint32_t* dvals[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dvals[0]),
                         reinterpret_cast<uint32_t*>(ws + plan.off_dvals[1])};
   uint64_t* first = reinterpret_cast<uint64_t*>(ws + plan.off_first);
-  uint32_t* sort_scratch = reinterpret_cast<uint32_t*>(ws + plan.off_sort);
+  uint32_t* sort_d = reinterpret_cast<uint32_t*>(ws + plan.off_sort_d);
+  uint32_t* sort_t = reinterpret_cast<uint32_t*>(ws + plan.off_sort_t);
   uint32_t* err = reinterpret_cast<uint32_t*>(ws + plan.off_err);
   uint64_t* partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
   const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
   const float2* m2 = reinterpret_cast<const float2*>(proj.mean2d);
   const float4* co = reinterpret_cast<const float4*>(proj.conic_opacity);
 
-  cudaError_t e = cudaMemsetAsync(out.ranges, 0, sizeof(uint32_t) * 2 * (size_t)plan.num_tiles, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  if (n == 0) return cudaMemsetAsync(out.num_instances, 0, sizeof(int64_t), st);
+  ClearJob clear;
+  clear.ptr[0] = out.ranges; clear.words[0] = 2 * (size_t)plan.num_tiles;
+  clear.ptr[1] = err; clear.words[1] = 1;
+  clear.ptr[2] = n == 0 ? reinterpret_cast<uint32_t*>(out.num_instances) : nullptr; clear.words[2] = 2;
+  clear.ptr[3] = n > 0 ? sort_d : nullptr; clear.words[3] = sort_scratch_bytes(n, 32) / 4;
+  clear.ptr[4] = n > 0 ? sort_t : nullptr; clear.words[4] = sort_scratch_bytes(plan.capacity, plan.tile_bits) / 4;
+  size_t most = 0;
+  for (int k = 0; k < 5; ++k) most = std::max(most, clear.ptr[k] ? clear.words[k] : 0);
+  const unsigned gc = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * 152));
+  cudaError_t e = launch_pdl(clear_kernel, dim3(gc), dim3(256), 0, st, clear);
+  if (e != cudaSuccess || n == 0) return e;
   const unsigned gb = (unsigned)((n + kRadixThreads - 1) / kRadixThreads);
   // 1. Gaussians by float32 depth (stable; culled ones last).
-  e = sort_clear(sort_scratch, n, 32, st);
+  e = launch_pdl(depth_keys_kernel, dim3(gb), dim3(kRadixThreads), 0, st, proj.depth, rect, n, dkeys[0], dvals[0],
+                 sort_d);
   if (e != cudaSuccess) return e;
-  depth_keys_kernel<<<gb, kRadixThreads, 0, st>>>(proj.depth, rect, n, dkeys[0], dvals[0], sort_scratch);
-  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_scratch, err, true, st);
+  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_d, err, true, st);
   const uint32_t* order = dvals[dcur];
   // 2. Kept tiles per Gaussian (row spans); first instance of each; K.
   uint32_t* counts = dkeys[dcur ^ 1];
   const unsigned gs = (unsigned)((n + kSpanThreads - 1) / kSpanThreads);
-  span_count_kernel<<<gs, kSpanThreads, 0, st>>>(order, rect, m2, co, n, tiles_x, tiles_y, counts);
+  e = launch_pdl(span_count_kernel, dim3(gs), dim3(kSpanThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
+                 counts);
+  if (e != cudaSuccess) return e;
   e = exclusive_scan<uint32_t, uint64_t>(counts, n, first, partials, out.num_instances, st);
   if (e != cudaSuccess) return e;
   // 3. Instances in depth order, into the buffer that makes the tile passes end in `out`.
@@ -719,18 +749,18 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   } else {
     ikeys[0] = wk0; ivals[0] = wv0; ikeys[1] = out_keys; ivals[1] = out.point_list;
   }
-  e = sort_clear(sort_scratch, plan.capacity, plan.tile_bits, st);
-  if (e != cudaSuccess) return e;
   const bool vec = ((reinterpret_cast<uintptr_t>(ikeys[0]) | reinterpret_cast<uintptr_t>(ivals[0])) & 15u) == 0;
-  span_emit_kernel<<<gs, kSpanThreads, 0, st>>>(order, rect, m2, co, n, tiles_x, tiles_y, first, plan.capacity,
-                                                ikeys[0], ivals[0], vec, passes, radix_digit_width(plan.tile_bits),
-                                                sort_scratch);
+  e = launch_pdl(span_emit_kernel, dim3(gs), dim3(kSpanThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
+                 (const uint64_t*)first, plan.capacity, ikeys[0], ivals[0], vec, passes,
+                 radix_digit_width(plan.tile_bits), sort_t);
+  if (e != cudaSuccess) return e;
   // 4. Stable sort by tile id; 5. tile ranges.
-  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_scratch, err, true, st);
+  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_t, err, true, st);
   if (plan.capacity > 0) {
     const unsigned gr = (unsigned)((plan.capacity + 255) / 256);
-    ranges_kernel<<<gr, 256, 0, st>>>(out_keys, out.num_instances, plan.capacity,
-                                      reinterpret_cast<uint2*>(out.ranges));
+    e = launch_pdl(ranges_kernel, dim3(gr), dim3(256), 0, st, (const uint32_t*)out_keys,
+                   (const int64_t*)out.num_instances, plan.capacity, reinterpret_cast<uint2*>(out.ranges));
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

@@ -9,6 +9,29 @@
 
 namespace sdgs {
 
+// Programmatic dependent launch.  A kernel started by launch_pdl may be scheduled while the
+// kernel before it in the stream is still finishing; it calls griddep_wait() before it touches
+// global memory, which returns once that kernel has completed and its writes are visible (and is
+// a no-op after an ordinary launch).  This hides the launch gap between the dependent kernels of
+// one render.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr int kTile = 16;
 constexpr int kTilePixels = kTile * kTile;
 constexpr float kAlphaMin = 1.0f / 255.0f;  // compositing skip threshold and cull threshold
@@ -40,7 +63,8 @@ struct BinPlan {
   int num_tiles;
   int tile_bits;
   // workspace carve-up (byte offsets)
-  size_t off_dkeys[2], off_dvals[2], off_first, off_ikeys[2], off_ivals, off_err, off_sort, off_partials, total;
+  size_t off_dkeys[2], off_dvals[2], off_first, off_ikeys[2], off_ivals, off_err, off_sort_d, off_sort_t,
+      off_partials, total;
   int64_t partial_cap;  // entries available for scan partials
 };
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);

@@ -71,6 +71,7 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
 
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
+  griddep_wait();
   __shared__ float2 s_xy[kThreads];
   __shared__ float4 s_q[kThreads];
   __shared__ float4 s_rgb[kThreads];
@@ -166,11 +167,8 @@ cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const
   a.n_evaluated = reinterpret_cast<unsigned long long*>(n_evaluated);
   const int tiles = a.tiles_x * tiles_of(v.height);
   if (tiles == 0) return cudaSuccess;
-  if (n_evaluated != nullptr)
-    render_fwd_kernel<true><<<tiles, kThreads, 0, st>>>(a);
-  else
-    render_fwd_kernel<false><<<tiles, kThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(n_evaluated != nullptr ? render_fwd_kernel<true> : render_fwd_kernel<false>, dim3(tiles),
+                    dim3(kThreads), 0, st, a);
 }
 
 }  // namespace sdgs

@@ -29,6 +29,7 @@ constexpr int kThreads = 128;
 __device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i);
 
 __global__ void __launch_bounds__(kThreads) slice_project_kernel(const SliceArgs a) {
+  griddep_wait();
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;
   slice_project_one(a, i);
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) slice_project_kernel(const SliceArgs
 
 // Several requests in one launch: blockIdx.y selects the request's argument block.
 __global__ void __launch_bounds__(kThreads) slice_project_batched_kernel(const SliceArgs* __restrict__ jobs) {
+  griddep_wait();
   const SliceArgs& a = jobs[blockIdx.y];
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;
@@ -153,8 +155,7 @@ cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const 
   if (s.n == 0) return cudaSuccess;
   const SliceArgs a = make_args(s, v, o);
   const int64_t blocks = (s.n + kThreads - 1) / kThreads;
-  slice_project_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(slice_project_kernel, dim3((unsigned)blocks), dim3(kThreads), 0, st, a);
 }
 
 size_t slice_job_bytes() { return sizeof(SliceArgs); }
