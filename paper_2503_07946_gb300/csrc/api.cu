@@ -348,6 +348,10 @@ int sdgs_render_bwd(const sdgs_scene* scene, const sdgs_view* view, const sdgs_p
     return SDGS_ERR_INVALID_ARG;
   }
   if (grads->dlambda != nullptr && !aligned(grads->dlambda, 4)) { set_error("dlambda misaligned"); return SDGS_ERR_INVALID_ARG; }
+  if (!aligned(grads->dL28, 16) || !aligned(grads->dsh, 16) || !aligned(grads->dmean7, 4) || !aligned(grads->dopacity, 4)) {
+    set_error("gradient arrays misaligned (dL28 and dsh to 16 bytes)");
+    return SDGS_ERR_INVALID_ARG;
+  }
   const size_t need = bwd_workspace_bytes(scene->n);
   if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) {
     set_error("backward workspace needs %zu bytes, 256-byte aligned", need);

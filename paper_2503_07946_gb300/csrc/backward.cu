@@ -26,10 +26,27 @@ struct RasterBwdArgs {
   float* g2;  // [n][12]
 };
 
-__device__ __forceinline__ float warp_sum(float x) {
+// Sums g[0..8] over the warp by recursive halving: at each level a lane keeps one half of its
+// values and adds its partner's copy of that half, so 16 exchanges replace 9 full butterflies.
+// Afterwards lanes 2v and 2v + 1 hold the warp total of g[v] (v < 9); the result is returned
+// for those lanes (and 0 for lanes whose v >= 9).
+__device__ __forceinline__ float warp_sum9(const float g[9]) {
+  const int lane = threadIdx.x & 31;
+  float v[16];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
+  for (int i = 0; i < 16; ++i) v[i] = i < 9 ? g[i] : 0.f;
+  // level k keeps the half of v selected by lane bit (4 - k) and folds the other half in
+#pragma unroll
+  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+    const bool upper = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = upper ? v[i] : v[i + half];
+      const float keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // Per-pixel state of the back-to-front replay.
@@ -51,7 +68,7 @@ __device__ __forceinline__ bool unblend(BwdPixel& px, const float4& co, const fl
   const float raw = __fmul_rn(co.w, G);
   const float al = fminf(kAlphaMax, raw);
   if (!(al >= kAlphaMin)) return false;
-  px.T = px.T / (1.f - al);
+  px.T = __fdividef(px.T, 1.f - al);
   const float w = al * px.T;
   g[6] += px.d0 * w;
   g[7] += px.d1 * w;
@@ -81,6 +98,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
   __shared__ float4 s_co[kThreads];
   __shared__ float4 s_rgb[kThreads];
   __shared__ uint32_t s_id[kThreads];
+  __shared__ float s_g[kThreads][9];  // this batch's per-Gaussian gradient, summed over the warps
   __shared__ uint32_t s_max;
 
   const int tile = blockIdx.x;
@@ -115,6 +133,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
   __syncthreads();
   const int end = (int)s_max;  // positions >= end were blended at no pixel of the tile
 
+  for (int i = threadIdx.x; i < kThreads * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
   for (int top = end; top > 0; top -= kThreads) {
     const int lo = max(0, top - kThreads);
     const int j = lo + threadIdx.x;
@@ -139,13 +158,20 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
       const bool b0 = unblend(pxs[0], co_k, q, c, dx, fy[0] - m.y, pos, g);
       const bool b1 = unblend(pxs[1], co_k, q, c, dx, fy[1] - m.y, pos, g);
       if (__any_sync(0xffffffffu, b0 || b1)) {
+        const float tot = warp_sum9(g);
+        const int v = lane >> 1;
+        if ((lane & 1) == 0 && v < 9) atomicAdd(&s_g[k][v], tot);
+      }
+    }
+    __syncthreads();
+    // one set of global atomics per Gaussian and block
+    if (threadIdx.x < cnt) {
+      float* out = a.g2 + (size_t)kG2 * s_id[threadIdx.x];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = warp_sum(g[i]);
-        if (lane == 0) {
-          float* out = a.g2 + (size_t)kG2 * s_id[k];
-#pragma unroll
-          for (int i = 0; i < 9; ++i) atomicAdd(out + i, g[i]);
-        }
+      for (int i = 0; i < 9; ++i) {
+        const float x = s_g[threadIdx.x][i];
+        if (x != 0.f) atomicAdd(out + i, x);
+        s_g[threadIdx.x][i] = 0.f;
       }
     }
   }
@@ -183,7 +209,7 @@ __device__ __forceinline__ void solve_upper_T(const float Lw[N][N], const float 
 // One visible Gaussian's adjoint; returns its d/d(lambda_t, lambda_d) in *dlt, *dld.
 __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, float* dlt, float* dld);
 
-__global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
+__global__ void __launch_bounds__(128, 3) geom_bwd_kernel(const GeomBwdArgs a) {
   const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
   float dlt = 0.f, dld = 0.f;
   if (i < a.n) {
@@ -205,11 +231,15 @@ __global__ void __launch_bounds__(128) geom_bwd_kernel(const GeomBwdArgs a) {
 __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, float* dlt, float* dld) {
 
   float L[28];
+  const float4* Lp = reinterpret_cast<const float4*>(a.L28 + 28 * i);  // 112-byte rows: aligned
 #pragma unroll
-  for (int k = 0; k < 28; ++k) L[k] = a.L28[28 * i + k];
+  for (int k = 0; k < 7; ++k) {
+    const float4 v = __ldg(Lp + k);
+    L[4 * k] = v.x; L[4 * k + 1] = v.y; L[4 * k + 2] = v.z; L[4 * k + 3] = v.w;
+  }
   float m[7];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) m[k] = a.mean7[7 * i + k];
+  for (int k = 0; k < 7; ++k) m[k] = __ldg(a.mean7 + 7 * i + k);
   const float alpha = a.opacity[i];
   const float* gp = a.g2 + (size_t)kG2 * i;
   const float du = gp[0], dv = gp[1], dA_ = gp[2], dB_ = gp[3], dC_ = gp[4], dalc = gp[5];
@@ -236,25 +266,37 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
     const float x = w0 * rn, y = w1 * rn, z = w2 * rn;
     float Y[16];
     sh_basis(x, y, z, Y);
-    const float* shp = a.sh + 48 * i;
+    // 192-byte SH rows (and their gradients) as 12 float4: flat index f = 3 k + c
+    const float4* shp = reinterpret_cast<const float4*>(a.sh + 48 * i);
     float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) raw[c] += Y[k] * shp[3 * k + c];
+    for (int q = 0; q < 12; ++q) {
+      const float4 v = __ldg(shp + q);
+      raw[(4 * q) % 3] += Y[(4 * q) / 3] * v.x;
+      raw[(4 * q + 1) % 3] += Y[(4 * q + 1) / 3] * v.y;
+      raw[(4 * q + 2) % 3] += Y[(4 * q + 2) / 3] * v.z;
+      raw[(4 * q + 3) % 3] += Y[(4 * q + 3) / 3] * v.w;
+    }
     float dc[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) dc[c] = raw[c] > 0.f ? drgb[c] : 0.f;
     float dY[16];
-    float* dshp = a.dsh + 48 * i;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      dY[k] = 0.f;
+    for (int k = 0; k < 16; ++k) dY[k] = 0.f;
+    float4* dshp = reinterpret_cast<float4*>(a.dsh + 48 * i);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        dshp[3 * k + c] += Y[k] * dc[c];
-        dY[k] += shp[3 * k + c] * dc[c];
-      }
+    for (int q = 0; q < 12; ++q) {
+      const float4 v = __ldg(shp + q);  // second read: L1
+      dY[(4 * q) / 3] += v.x * dc[(4 * q) % 3];
+      dY[(4 * q + 1) / 3] += v.y * dc[(4 * q + 1) % 3];
+      dY[(4 * q + 2) / 3] += v.z * dc[(4 * q + 2) % 3];
+      dY[(4 * q + 3) / 3] += v.w * dc[(4 * q + 3) % 3];
+      float4 d = dshp[q];
+      d.x += Y[(4 * q) / 3] * dc[(4 * q) % 3];
+      d.y += Y[(4 * q + 1) / 3] * dc[(4 * q + 1) % 3];
+      d.z += Y[(4 * q + 2) / 3] * dc[(4 * q + 2) % 3];
+      d.w += Y[(4 * q + 3) / 3] * dc[(4 * q + 3) % 3];
+      dshp[q] = d;
     }
     const float xx = x * x, yy = y * y, zz = z * z;
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -437,8 +479,13 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
     for (int k = 0; k < 3; ++k) dm[k] += (ded[k] - dot * q.d[k]) * rnd;
   }
 
+  float4* dLp = reinterpret_cast<float4*>(a.dL28 + 28 * i);
 #pragma unroll
-  for (int k = 0; k < 28; ++k) a.dL28[28 * i + k] += dLg[k];
+  for (int q = 0; q < 7; ++q) {
+    float4 d = dLp[q];
+    d.x += dLg[4 * q]; d.y += dLg[4 * q + 1]; d.z += dLg[4 * q + 2]; d.w += dLg[4 * q + 3];
+    dLp[q] = d;
+  }
 #pragma unroll
   for (int k = 0; k < 7; ++k) a.dmean7[7 * i + k] += dm[k];
 }
