@@ -94,6 +94,7 @@ __device__ __forceinline__ bool unblend(BwdPixel& px, const float4& co, const fl
 // over the thread's pixels, then over the warp, and added to the per-Gaussian buffer with one
 // atomic per component and warp.
 __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArgs a) {
+  griddep_wait();
   __shared__ float2 s_xy[kThreads];
   __shared__ float4 s_co[kThreads];
   __shared__ float4 s_rgb[kThreads];
