@@ -61,13 +61,52 @@ __device__ __forceinline__ float hidden_pre(const AgrWeights& W, int u, const fl
   return z;
 }
 
+// The forward's shared-memory layout, arranged for 16-byte broadcast reads: unit u's first-layer
+// row (7 weights, then its bias) is two float4; hidden unit j of MLP m has its output weights
+// contiguous (rows padded to a multiple of 4).
+struct AgrFwdWeights {
+  float4 w1[kUnits][2];
+  float4 w2p[kHidden];      // rows 0-2 (phi_p), padded
+  float4 w2t[kHidden];      // row 3 (phi_t), padded
+  float4 w2d[kHidden];      // rows 4-6 (phi_d), padded
+  float4 w2l[kHidden][7];   // rows 7-34 (phi_l)
+  float b2[kOut];
+};
+
+__device__ __forceinline__ void load_fwd_weights(AgrFwdWeights& F, AgrWeights& W, const sdgs_agr& a, float t) {
+  load_weights(W, a, t);  // gamma folded into W.bias
+  for (int u = threadIdx.x; u < kUnits; u += blockDim.x) {
+    F.w1[u][0] = make_float4(W.w1x[u][0], W.w1x[u][1], W.w1x[u][2], W.w1x[u][3]);
+    F.w1[u][1] = make_float4(W.w1x[u][4], W.w1x[u][5], W.w1x[u][6], W.bias[u]);
+  }
+  for (int j = threadIdx.x; j < kHidden; j += blockDim.x) {
+    F.w2p[j] = make_float4(W.w2[0][j], W.w2[1][j], W.w2[2][j], 0.f);
+    F.w2t[j] = make_float4(W.w2[3][j], 0.f, 0.f, 0.f);
+    F.w2d[j] = make_float4(W.w2[4][j], W.w2[5][j], W.w2[6][j], 0.f);
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+      F.w2l[j][q] = make_float4(W.w2[7 + 4 * q][j], W.w2[8 + 4 * q][j], W.w2[9 + 4 * q][j], W.w2[10 + 4 * q][j]);
+  }
+  for (int r = threadIdx.x; r < kOut; r += blockDim.x) F.b2[r] = W.b2[r];
+  __syncthreads();
+}
+
+__device__ __forceinline__ float fwd_hidden(const AgrFwdWeights& F, int u, const float x[kX]) {
+  const float4 a = F.w1[u][0], b = F.w1[u][1];
+  float z = b.w;  // same order as hidden_pre: bias, then columns 0..6
+  z += a.x * x[0]; z += a.y * x[1]; z += a.z * x[2]; z += a.w * x[3];
+  z += b.x * x[4]; z += b.y * x[5]; z += b.z * x[6];
+  return fmaxf(z, 0.f);
+}
+
 __global__ void __launch_bounds__(kAgrThreads) agr_refine_kernel(const float* __restrict__ mean7,
                                                                  const float* __restrict__ L28, int64_t n,
                                                                  sdgs_agr agr, float t,
                                                                  float* __restrict__ mean7_out,
                                                                  float* __restrict__ L28_out) {
   __shared__ AgrWeights W;
-  load_weights(W, agr, t);
+  __shared__ AgrFwdWeights F;
+  load_fwd_weights(F, W, agr, t);
   const int64_t i = (int64_t)blockIdx.x * kAgrThreads + threadIdx.x;
   if (i >= n) return;
   float x[kX];
@@ -75,20 +114,43 @@ __global__ void __launch_bounds__(kAgrThreads) agr_refine_kernel(const float* __
   for (int c = 0; c < kX; ++c) x[c] = mean7[kX * i + c];
   float out[kOut];
 #pragma unroll
-  for (int r = 0; r < kOut; ++r) out[r] = W.b2[r];
-#pragma unroll
-  for (int m = 0; m < kMlps; ++m) {
+  for (int r = 0; r < kOut; ++r) out[r] = F.b2[r];
 #pragma unroll 4
-    for (int j = 0; j < kHidden; ++j) {
-      const float h = fmaxf(hidden_pre(W, m * kHidden + j, x), 0.f);
+  for (int j = 0; j < kHidden; ++j) {  // phi_p
+    const float h = fwd_hidden(F, j, x);
+    const float4 w = F.w2p[j];
+    out[0] += w.x * h; out[1] += w.y * h; out[2] += w.z * h;
+  }
+#pragma unroll 4
+  for (int j = 0; j < kHidden; ++j) {  // phi_t
+    const float h = fwd_hidden(F, kHidden + j, x);
+    out[3] += F.w2t[j].x * h;
+  }
+#pragma unroll 4
+  for (int j = 0; j < kHidden; ++j) {  // phi_d
+    const float h = fwd_hidden(F, 2 * kHidden + j, x);
+    const float4 w = F.w2d[j];
+    out[4] += w.x * h; out[5] += w.y * h; out[6] += w.z * h;
+  }
+#pragma unroll 2
+  for (int j = 0; j < kHidden; ++j) {  // phi_l
+    const float h = fwd_hidden(F, 3 * kHidden + j, x);
 #pragma unroll
-      for (int r = row_begin(m); r < row_end(m); ++r) out[r] += W.w2[r][j] * h;
+    for (int q = 0; q < 7; ++q) {
+      const float4 w = F.w2l[j][q];
+      out[7 + 4 * q] += w.x * h; out[8 + 4 * q] += w.y * h; out[9 + 4 * q] += w.z * h; out[10 + 4 * q] += w.w * h;
     }
   }
 #pragma unroll
   for (int c = 0; c < kX; ++c) mean7_out[kX * i + c] = x[c] + out[c];
+  const float4* Lin = reinterpret_cast<const float4*>(L28 + 28 * i);
+  float4* Lout = reinterpret_cast<float4*>(L28_out + 28 * i);
 #pragma unroll
-  for (int k = 0; k < 28; ++k) L28_out[28 * i + k] = L28[28 * i + k] + out[kX + k];
+  for (int q = 0; q < 7; ++q) {
+    float4 l = Lin[q];
+    l.x += out[kX + 4 * q]; l.y += out[kX + 4 * q + 1]; l.z += out[kX + 4 * q + 2]; l.w += out[kX + 4 * q + 3];
+    Lout[q] = l;
+  }
 }
 
 // Weight-gradient sums owned by the block: O1 = per unit (7 x-columns, then db1), O2 = per output
