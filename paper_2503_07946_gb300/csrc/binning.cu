@@ -580,16 +580,37 @@ __device__ __forceinline__ void count_span_digits(const DigitAcc& acc, uint32_t 
   }
 }
 
-// Writes each depth-ordered Gaussian's (tile id, Gaussian id) pairs from its first instance (one
-// thread each), row-major over its spans, and accumulates the tile-digit histograms of what it
-// writes.  With vec, keys and vals are 16-byte aligned and runs are stored four at a time.
+constexpr uint32_t kBigInstances = 32;  // above this a Gaussian is written by its whole warp
+
+__device__ __forceinline__ SpanRule shfl_rule(const SpanRule& q, int src) {
+  SpanRule o;
+  o.u = __shfl_sync(0xffffffffu, q.u, src);
+  o.v = __shfl_sync(0xffffffffu, q.v, src);
+  o.a = __shfl_sync(0xffffffffu, q.a, src);
+  o.b = __shfl_sync(0xffffffffu, q.b, src);
+  o.det = __shfl_sync(0xffffffffu, q.det, src);
+  o.aQ = __shfl_sync(0xffffffffu, q.aQ, src);
+  o.hx = 0.f;  // not used past setup
+  o.reach_y = __shfl_sync(0xffffffffu, q.reach_y, src);
+  o.dyr = __shfl_sync(0xffffffffu, q.dyr, src);
+  o.padx = __shfl_sync(0xffffffffu, q.padx, src);
+  o.mode = __shfl_sync(0xffffffffu, q.mode, src);
+  return o;
+}
+
+// Writes each depth-ordered Gaussian's (tile id, Gaussian id) pairs from its first instance,
+// row-major over its spans, and accumulates the tile-digit histograms of what it writes.  A
+// Gaussian with at most kBigInstances instances is written by its own thread (runs stored four
+// at a time when keys and vals are 16-byte aligned, `vec`); larger ones are then written by the
+// whole warp one at a time -- lanes take 32 rows, a warp scan places their spans, and the lanes
+// store consecutive instances -- so that one large Gaussian does not hold up its warp.
 // Positions >= cap are dropped.
 __global__ void __launch_bounds__(kSpanThreads)
 span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
-                 int tiles_x, int tiles_y, const uint64_t* __restrict__ first, int64_t cap,
-                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, bool vec, int passes, int width,
-                 uint32_t* __restrict__ hist) {
+                 int tiles_x, int tiles_y, const uint64_t* __restrict__ first, const uint32_t* __restrict__ counts,
+                 int64_t cap, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, bool vec, int passes,
+                 int width, uint32_t* __restrict__ hist) {
   griddep_wait();
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   __shared__ int32_t s_diff0[kBins + 1];
@@ -600,46 +621,95 @@ span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__
   __syncthreads();
   const DigitAcc acc{s_hist, s_diff0, &s_all0};
   const int64_t s = (int64_t)blockIdx.x * kSpanThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t g = 0;
+  ushort4 r = make_ushort4(0, 0, 0, 0);
+  SpanRule rule;
+  rule.mode = 2;
+  int y0 = 0, y1 = 0;
+  uint64_t pos = 0;
+  bool live = false, big = false;
   if (s < n) {
-    const uint32_t g = order[s];
-    const ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
-    uint64_t pos = first[s];
-    if (r.z > r.x && r.w > r.y && pos < (uint64_t)cap) {
-      const SpanRule rule = span_setup(mean2d[g], conic_opacity[g]);
-      int y0, y1;
+    pos = first[s];
+    const uint32_t cnt = counts[s];
+    if (cnt > 0 && pos < (uint64_t)cap) {
+      g = order[s];
+      r = clip_rect(rect[g], tiles_x, tiles_y);
+      rule = span_setup(mean2d[g], conic_opacity[g]);
       span_rows(rule, r.y, r.w, &y0, &y1);
-      const uint4 g4 = make_uint4(g, g, g, g);
-      for (int ty = y0; ty < y1 && pos < (uint64_t)cap; ++ty) {
-        int x0, x1;
-        span_cols(rule, ty, r.x, r.z, &x0, &x1);
-        const int64_t room = cap - (int64_t)pos;
-        const uint32_t len = (uint32_t)((int64_t)(x1 - x0) < room ? (int64_t)(x1 - x0) : room);
-        const uint32_t id0 = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0;
-        uint32_t k = 0;
-        if (vec) {
-          for (; k < len && ((pos + k) & 3u); ++k) {
-            keys[pos + k] = id0 + k;
-            vals[pos + k] = g;
-          }
-          for (; k + 4 <= len; k += 4) {
-            const uint32_t id = id0 + k;
-            *reinterpret_cast<uint4*>(keys + pos + k) = make_uint4(id, id + 1, id + 2, id + 3);
-            *reinterpret_cast<uint4*>(vals + pos + k) = g4;
-          }
-        }
-        for (; k < len; ++k) {
+      live = true;
+      big = cnt > kBigInstances;
+    }
+  }
+  if (live && !big) {
+    const uint4 g4 = make_uint4(g, g, g, g);
+    for (int ty = y0; ty < y1 && pos < (uint64_t)cap; ++ty) {
+      int x0, x1;
+      span_cols(rule, ty, r.x, r.z, &x0, &x1);
+      const int64_t room = cap - (int64_t)pos;
+      const uint32_t len = (uint32_t)((int64_t)(x1 - x0) < room ? (int64_t)(x1 - x0) : room);
+      const uint32_t id0 = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0;
+      uint32_t k = 0;
+      if (vec) {
+        for (; k < len && ((pos + k) & 3u); ++k) {
           keys[pos + k] = id0 + k;
           vals[pos + k] = g;
         }
-        count_span_digits(acc, id0, len, passes, width);
-        pos += len;
+        for (; k + 4 <= len; k += 4) {
+          const uint32_t id = id0 + k;
+          *reinterpret_cast<uint4*>(keys + pos + k) = make_uint4(id, id + 1, id + 2, id + 3);
+          *reinterpret_cast<uint4*>(vals + pos + k) = g4;
+        }
       }
+      for (; k < len; ++k) {
+        keys[pos + k] = id0 + k;
+        vals[pos + k] = g;
+      }
+      count_span_digits(acc, id0, len, passes, width);
+      pos += len;
+    }
+  }
+  for (unsigned bigs = __ballot_sync(0xffffffffu, big); bigs != 0u; bigs &= bigs - 1u) {  // uniform
+    const int i = __ffs(bigs) - 1;
+    const SpanRule q = shfl_rule(rule, i);
+    const uint32_t qg = __shfl_sync(0xffffffffu, g, i);
+    const int qx0 = __shfl_sync(0xffffffffu, (int)r.x, i), qx1 = __shfl_sync(0xffffffffu, (int)r.z, i);
+    const int qy0 = __shfl_sync(0xffffffffu, y0, i), qy1 = __shfl_sync(0xffffffffu, y1, i);
+    uint64_t qpos = __shfl_sync(0xffffffffu, pos, i);
+    for (int rb = qy0; rb < qy1; rb += 32) {
+      const int ty = rb + lane;
+      int x0 = 0, x1 = 0;
+      if (ty < qy1) span_cols(q, ty, qx0, qx1, &x0, &x1);
+      const uint32_t len = (uint32_t)(x1 - x0);
+      const uint32_t incl = warp_inclusive_scan(len);
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const int64_t rstart = (int64_t)qpos + (int64_t)(incl - len);
+      const int64_t room = cap - rstart;
+      const uint32_t written = room <= 0 ? 0u : (room < (int64_t)len ? (uint32_t)room : len);
+      count_span_digits(acc, (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0, written, passes, width);
+      for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        int rl = 0;  // the row lane holding instance j: the first lane whose inclusive count exceeds j
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const uint32_t v = __shfl_sync(0xffffffffu, incl, rl + step - 1);
+          if (v <= j) rl += step;
+        }
+        const uint32_t r_excl = __shfl_sync(0xffffffffu, incl - len, rl);
+        const int r_x0 = __shfl_sync(0xffffffffu, x0, rl);
+        const uint64_t p = qpos + j;
+        if (j < total && p < (uint64_t)cap) {
+          keys[p] = (uint32_t)(rb + rl) * (uint32_t)tiles_x + (uint32_t)(r_x0 + (int)(j - r_excl));
+          vals[p] = qg;
+        }
+      }
+      qpos += total;
+      if (qpos >= (uint64_t)cap) break;  // uniform
     }
   }
   __syncthreads();
   if (passes > 0) {  // pass 0 from the difference array: a running sum over the digits
     if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
       const int period = 1 << width;
       int carry = 0;
       for (int d0 = 0; d0 < period; d0 += 32) {
@@ -751,7 +821,7 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   }
   const bool vec = ((reinterpret_cast<uintptr_t>(ikeys[0]) | reinterpret_cast<uintptr_t>(ivals[0])) & 15u) == 0;
   e = launch_pdl(span_emit_kernel, dim3(gs), dim3(kSpanThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
-                 (const uint64_t*)first, plan.capacity, ikeys[0], ivals[0], vec, passes,
+                 (const uint64_t*)first, (const uint32_t*)counts, plan.capacity, ikeys[0], ivals[0], vec, passes,
                  radix_digit_width(plan.tile_bits), sort_t);
   if (e != cudaSuccess) return e;
   // 4. Stable sort by tile id; 5. tile ranges.
