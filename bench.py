@@ -180,14 +180,14 @@ def run_reference(args, rank: int, world: int):
 # ---------------------------------------------------------------------------------------------
 
 def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
-    """Kernels libsdgs launches for one render: slice_project; the depth keys (with the depth
-    digit histograms); 4 depth radix passes; the kept-tile count per Gaussian; its 3-kernel scan;
-    the emit (with the tile digit histograms); ceil(tile bits / 8) tile radix passes; tile
-    ranges; the rasteriser."""
+    """Kernels libsdgs launches for one render: slice_project; the binning clear kernel; the
+    depth keys (with the depth digit histograms); 4 depth radix passes; the kept-tile count per
+    Gaussian; its 3-kernel scan; the emit (with the tile digit histograms); ceil(tile bits / 8)
+    tile radix passes; tile ranges; the rasteriser."""
     tiles = ((width + 15) // 16) * ((height + 15) // 16)
     bits = max(0, (tiles - 1).bit_length())
     tile_passes = (bits + 7) // 8 if capacity > 0 else 0
-    return 1 + 1 + 4 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
+    return 1 + 1 + 1 + 4 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
 
 
 def cpu_baseline(scene, cam) -> dict:
@@ -302,6 +302,12 @@ def run_ours(args, rank: int, world: int):
     e2e_s = (time.perf_counter() - t0) / steps
 
     # ---- fwd + bwd (L2 loss against a target from perturbed parameters, camera 0) ----
+    big_scene = synth.config_scene(2)
+    large = frames_on(big_scene, synth.config_cameras(2), min(steps, 200), warm, dev, flush)
+    large["workload"] = ("config 2: 1.5M 7D Gaussians in 64 clusters, 1352x1014, forward-facing arc cameras, "
+                         "black background, lambda_t = lambda_d = 0.1")
+    del big_scene
+    pipe = pipelined_frames(scene, t_scene, views, min(steps, 1000), warm, dev)
     fb = fwd_bwd_its(scene, cams[0], steps, warm, dev)
     fb_agr = fwd_bwd_its(scene, cams[0], min(steps, 200), warm, dev, agr=True)
     agr = agr_frames(scene, t_scene, views, flush, min(steps, 300), warm, dev)
@@ -327,6 +333,8 @@ def run_ours(args, rank: int, world: int):
         "phases_ms": {"slice_project": float(phase[:, 0].mean()), "bin_sort": float(phase[:, 1].mean()),
                       "render_fwd": raster_ms},
         "workload_stats": {"instances": k_inst, "visible": visible, "evaluations_per_frame": evals // steps},
+        "large_scene_frames": large,
+        "pipelined_frames": pipe,
         "fwd_bwd_it_s": fb,
         "fwd_bwd_agr_it_s": fb_agr,
         "agr_frames": agr,
@@ -443,6 +451,90 @@ def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: i
                                   "mpix_s": pix / (finish - trace[0][0]) / 1e6}}
         result["server_stats"] = srv.stats()
     return result
+
+
+def frames_on(scene, cams, steps: int, warm: int, dev, flush) -> dict:
+    """Forward frames of another scene (slice -> bin -> render), timed per frame with L2 flushes
+    between frames, like the headline measurement."""
+    from paper_2503_07946_gb300 import render as prender
+    from paper_2503_07946_gb300 import sdgs
+    t_scene = prender.scene_to_device(scene)
+    st = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
+    views = [sdgs.view_struct(cams[i % len(cams)]) for i in range(steps + warm)]
+    W, H = views[0].width, views[0].height
+    sizing = prender.Renderer(scene.n, W, H, capacity=4096)
+    kmax = 0
+    for v in views[: min(len(views), 60)]:
+        sdgs.slice_project(st, v, sizing.proj)
+        kmax = max(kmax, sizing.bin(v))
+    del sizing
+    r = prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096)
+    stream = torch.cuda.current_stream()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(warm + steps):
+        ev = evs[i - warm] if i >= warm else None
+        if ev:
+            ev[0].record(stream)
+        sdgs.slice_project(st, views[i], r.proj, stream)
+        if ev:
+            ev[1].record(stream)
+        sdgs.bin_sort(r.proj, views[i], r.bins, sync=False, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        sdgs.render_fwd(r.proj, r.bins, views[i], r.image, r.final_T, r.n_contrib, None, stream)
+        if ev:
+            ev[3].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    ph = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
+    ms = float(ph.sum(1).mean())
+    return {"value": W * H / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_frame": ms, "fps": 1000.0 / ms,
+            "phases_ms": {"slice_project": float(ph[:, 0].mean()), "bin_sort": float(ph[:, 1].mean()),
+                          "render_fwd": float(ph[:, 2].mean())},
+            "instances": int(r.bins.num_instances.item()), "steps": steps}
+
+
+def pipelined_frames(scene, t_scene, views, steps: int, warm: int, dev) -> dict:
+    """Throughput with two frames in flight: independent views alternate between two streams with
+    their own buffers, so one frame's latency-bound binning overlaps the other's compositing.  No
+    L2 flush between frames (scene, records and lists together exceed the 129 MB L2)."""
+    from paper_2503_07946_gb300 import render as prender
+    from paper_2503_07946_gb300 import sdgs
+    st = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
+    W, H = views[0].width, views[0].height
+    sizing = prender.Renderer(scene.n, W, H, capacity=4096)
+    kmax = 0
+    for v in views[: min(len(views), 100)]:
+        sdgs.slice_project(st, v, sizing.proj)
+        kmax = max(kmax, sizing.bin(v))
+    del sizing
+    rs = [prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096) for _ in range(2)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+
+    def run(lo, hi):
+        for i in range(lo, hi):
+            r, s = rs[i % 2], streams[i % 2]
+            sdgs.slice_project(st, views[i], r.proj, s)
+            sdgs.bin_sort(r.proj, views[i], r.bins, sync=False, stream=s)
+            sdgs.render_fwd(r.proj, r.bins, views[i], r.image, r.final_T, r.n_contrib, None, s)
+
+    run(0, warm)
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for s in streams:
+        s.wait_event(e0)
+    run(warm, warm + steps)
+    for s in streams:
+        ev = torch.cuda.Event()
+        ev.record(s)
+        cur.wait_event(ev)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": W * H / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_frame": ms, "fps": 1000.0 / ms,
+            "frames_in_flight": 2, "steps": steps}
 
 
 def agr_weights_dev(dev) -> dict:
