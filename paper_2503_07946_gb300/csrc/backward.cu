@@ -57,36 +57,54 @@ struct BwdPixel {
   uint32_t last;           // positions >= last were not blended in the forward
 };
 
-// Adjoint of one (pixel, Gaussian) blend, accumulated into g[9] = d(u, v, a, b, c, alpha_cond,
-// r, g, b).  Replays exactly the forward's decisions (same exponent, alpha and thresholds).
-__device__ __forceinline__ bool unblend(BwdPixel& px, const float4& co, const float4& q, const float4& c,
-                                        float dx, float dy, uint32_t pos, float g[9]) {
-  if (pos >= px.last) return false;
-  const float p2 = splat_power2(q, dx, dy);
-  if (!(p2 <= 0.f)) return false;
-  const float G = ex2_approx(p2);
-  const float raw = __fmul_rn(co.w, G);
-  const float al = fminf(kAlphaMax, raw);
-  if (!(al >= kAlphaMin)) return false;
-  px.T = __fdividef(px.T, 1.f - al);
-  const float w = al * px.T;
-  g[6] += px.d0 * w;
-  g[7] += px.d1 * w;
-  g[8] += px.d2 * w;
-  const float dal = px.T * (px.d0 * (c.x - px.R0) + px.d1 * (c.y - px.R1) + px.d2 * (c.z - px.R2));
-  px.R0 = c.x * al + (1.f - al) * px.R0;
-  px.R1 = c.y * al + (1.f - al) * px.R1;
-  px.R2 = c.z * al + (1.f - al) * px.R2;
-  if (raw < kAlphaMax) {  // no derivative through the 0.99 clamp
-    g[5] += dal * G;
-    const float dp = dal * al;  // d alpha / d(power) = alpha
-    g[0] += dp * (co.x * dx + co.y * dy);
-    g[1] += dp * (co.y * dx + co.z * dy);
-    g[2] += -0.5f * dp * dx * dx;
-    g[3] += -dp * dx * dy;
-    g[4] += -0.5f * dp * dy * dy;
-  }
-  return true;
+// Adjoint of one (pixel, Gaussian) blend for the thread's two pixels at once (rows r and r + 8:
+// same dx, dy as a pair), without branches, accumulated into g[9] = d(u, v, a, b, c, alpha_cond,
+// r, g, b).  A pixel that does not take the Gaussian gets alpha 0, which leaves its T, R and the
+// gradient unchanged exactly; the decisions are those of the forward (same exponent, alpha and
+// thresholds).  The gradient is accumulated per pixel in g2[9] (x: first pixel, y: second).
+struct BwdPair {
+  float2 T, R0, R1, R2, d0, d1, d2;
+  uint32_t last0, last1;
+};
+
+__device__ __forceinline__ bool unblend2(BwdPair& px, const float4& co, const float4& q, const float4& c,
+                                         float dx, float2 dy, uint32_t pos, float2 g[9]) {
+  const float a = __fmul_rn(__fmul_rn(q.x, dx), dx);
+  const float bx = __fmul_rn(q.y, dx);
+  const float2 t = __ffma2_rn(make_float2(q.z, q.z), dy, make_float2(bx, bx));
+  const float2 p2 = __ffma2_rn(dy, t, make_float2(a, a));
+  const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+  const float2 raw = __fmul2_rn(make_float2(co.w, co.w), G);
+  const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
+  const bool h0 = pos < px.last0 && p2.x <= 0.f && al.x >= kAlphaMin;
+  const bool h1 = pos < px.last1 && p2.y <= 0.f && al.y >= kAlphaMin;
+  const float2 ae = make_float2(h0 ? al.x : 0.f, h1 ? al.y : 0.f);  // alpha taken (0: skipped)
+  const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
+  px.T = make_float2(__fdividef(px.T.x, om.x), __fdividef(px.T.y, om.y));
+  const float2 w = __fmul2_rn(ae, px.T);
+  g[6] = __ffma2_rn(px.d0, w, g[6]);
+  g[7] = __ffma2_rn(px.d1, w, g[7]);
+  g[8] = __ffma2_rn(px.d2, w, g[8]);
+  float2 s = __fmul2_rn(px.d0, __fadd2_rn(make_float2(c.x, c.x), make_float2(-px.R0.x, -px.R0.y)));
+  s = __ffma2_rn(px.d1, __fadd2_rn(make_float2(c.y, c.y), make_float2(-px.R1.x, -px.R1.y)), s);
+  s = __ffma2_rn(px.d2, __fadd2_rn(make_float2(c.z, c.z), make_float2(-px.R2.x, -px.R2.y)), s);
+  const float2 dal = __fmul2_rn(px.T, s);
+  px.R0 = __ffma2_rn(om, px.R0, __fmul2_rn(make_float2(c.x, c.x), ae));
+  px.R1 = __ffma2_rn(om, px.R1, __fmul2_rn(make_float2(c.y, c.y), ae));
+  px.R2 = __ffma2_rn(om, px.R2, __fmul2_rn(make_float2(c.z, c.z), ae));
+  // no derivative through the 0.99 clamp
+  const float2 dl = make_float2(h0 && raw.x < kAlphaMax ? dal.x : 0.f, h1 && raw.y < kAlphaMax ? dal.y : 0.f);
+  g[5] = __ffma2_rn(dl, make_float2(fminf(G.x, 1.f), fminf(G.y, 1.f)), g[5]);  // G <= 1 where taken
+  const float2 dp = __fmul2_rn(dl, al);  // d alpha / d(power) = alpha
+  const float2 ddx = __ffma2_rn(make_float2(co.y, co.y), dy, make_float2(co.x * dx, co.x * dx));
+  const float2 ddy = __ffma2_rn(make_float2(co.z, co.z), dy, make_float2(co.y * dx, co.y * dx));
+  g[0] = __ffma2_rn(dp, ddx, g[0]);
+  g[1] = __ffma2_rn(dp, ddy, g[1]);
+  const float hdx2 = -0.5f * dx * dx;
+  g[2] = __ffma2_rn(dp, make_float2(hdx2, hdx2), g[2]);
+  g[3] = __ffma2_rn(dp, __fmul2_rn(make_float2(-dx, -dx), dy), g[3]);
+  g[4] = __ffma2_rn(dp, __fmul2_rn(make_float2(-0.5f, -0.5f), __fmul2_rn(dy, dy)), g[4]);
+  return h0 || h1;
 }
 
 // Back-to-front replay per 16x16 tile, 128 threads with two pixels each (rows r and r + 8).
@@ -104,30 +122,42 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
   const int py[2] = {ty * kTile + (int)(threadIdx.x / kTile), ty * kTile + (int)(threadIdx.x / kTile) + kTile / 2};
   const float fx = (float)px + 0.5f;
   const float fy[2] = {(float)py[0] + 0.5f, (float)py[1] + 0.5f};
   const uint2 range = a.ranges[tile];
 
-  BwdPixel pxs[2];
-  uint32_t mylast = 0;
+  BwdPair pp;
+  {
+    BwdPixel pxs[2];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    BwdPixel& p = pxs[r];
-    p.T = 1.f; p.last = 0; p.d0 = p.d1 = p.d2 = 0.f;
-    p.R0 = a.bg[0]; p.R1 = a.bg[1]; p.R2 = a.bg[2];
-    if (px < a.width && py[r] < a.height) {
-      const int pix = py[r] * a.width + px;
-      p.T = a.final_T[pix];
-      p.last = a.n_contrib[pix];
-      p.d0 = a.dL_dimage[3 * pix + 0];
-      p.d1 = a.dL_dimage[3 * pix + 1];
-      p.d2 = a.dL_dimage[3 * pix + 2];
+    for (int r = 0; r < 2; ++r) {
+      BwdPixel& p = pxs[r];
+      p.T = 1.f; p.last = 0; p.d0 = p.d1 = p.d2 = 0.f;
+      p.R0 = a.bg[0]; p.R1 = a.bg[1]; p.R2 = a.bg[2];
+      if (px < a.width && py[r] < a.height) {
+        const int pix = py[r] * a.width + px;
+        p.T = a.final_T[pix];
+        p.last = a.n_contrib[pix];
+        p.d0 = a.dL_dimage[3 * pix + 0];
+        p.d1 = a.dL_dimage[3 * pix + 1];
+        p.d2 = a.dL_dimage[3 * pix + 2];
+      }
     }
-    mylast = max(mylast, p.last);
+    pp.T = make_float2(pxs[0].T, pxs[1].T);
+    pp.R0 = make_float2(pxs[0].R0, pxs[1].R0);
+    pp.R1 = make_float2(pxs[0].R1, pxs[1].R1);
+    pp.R2 = make_float2(pxs[0].R2, pxs[1].R2);
+    pp.d0 = make_float2(pxs[0].d0, pxs[1].d0);
+    pp.d1 = make_float2(pxs[0].d1, pxs[1].d1);
+    pp.d2 = make_float2(pxs[0].d2, pxs[1].d2);
+    pp.last0 = pxs[0].last;
+    pp.last1 = pxs[1].last;
   }
+  const uint32_t mylast = max(pp.last0, pp.last1);
+  const float2 fy2 = make_float2(fy[0], fy[1]);
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
   atomicMax(&s_max, mylast);
@@ -154,11 +184,15 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
       const float4 q = scaled_conic(co_k);
       const float4 c = s_rgb[k];
       const uint32_t pos = (uint32_t)(lo + k);
-      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float2 g2[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g2[i] = make_float2(0.f, 0.f);
       const float dx = fx - m.x;
-      const bool b0 = unblend(pxs[0], co_k, q, c, dx, fy[0] - m.y, pos, g);
-      const bool b1 = unblend(pxs[1], co_k, q, c, dx, fy[1] - m.y, pos, g);
-      if (__any_sync(0xffffffffu, b0 || b1)) {
+      const bool hit = unblend2(pp, co_k, q, c, dx, __fadd2_rn(fy2, make_float2(-m.y, -m.y)), pos, g2);
+      if (__any_sync(0xffffffffu, hit)) {
+        float g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = g2[i].x + g2[i].y;
         const float tot = warp_sum9(g);
         const int v = lane >> 1;
         if ((lane & 1) == 0 && v < 9) atomicAdd(&s_g[k][v], tot);
