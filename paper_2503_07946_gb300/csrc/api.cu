@@ -131,7 +131,8 @@ int sdgs_slice_project(const sdgs_scene* scene, const sdgs_view* view, const sdg
 int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t height, size_t* bytes) {
   g_error[0] = 0;
   if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 30) || capacity < 0 || capacity >= (int64_t(1) << 30) ||
-      width <= 0 || height <= 0 || width > 65535 * kTile || height > 65535 * kTile) {
+      width <= 0 || height <= 0 || width > 65535 * kTile || height > 65535 * kTile ||
+      (int64_t)((width + kTile - 1) / kTile) * ((height + kTile - 1) / kTile) > ((int64_t)1 << 26)) {
     set_error("bad arguments to sdgs_bin_workspace_size");
     return SDGS_ERR_INVALID_ARG;
   }

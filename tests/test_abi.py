@@ -85,3 +85,30 @@ def test_invalid_arguments_are_rejected_before_any_gpu_work(lib):
     s.n = 0
     rc = lib.sdgs_slice_project(ctypes.byref(s), ctypes.byref(v), None, None)
     assert rc == 1 and b"image size" in lib.sdgs_last_error()
+
+
+def test_new_entry_points_reject_invalid_arguments_before_any_gpu_work(lib):
+    v = sdgs.View()
+    v.width, v.height, v.fx, v.fy = 64, 64, 50.0, 50.0
+    s = sdgs.Scene(None, None, None, None, 0, 3, 0.05, 0.05, 2)
+    rc = lib.sdgs_slice_project(ctypes.byref(s), ctypes.byref(v), None, None)
+    assert rc == 1 and b"dir_mode" in lib.sdgs_last_error()
+    s.dir_mode = 0
+    w = sdgs.Agr(None, None, None, None)
+    rc = lib.sdgs_agr_refine(ctypes.byref(s), ctypes.byref(w), 0.5, None, None, None)
+    assert rc == 1 and b"AGR" in lib.sdgs_last_error()
+    rc = lib.sdgs_agr_refine(ctypes.byref(s), None, 0.5, None, None, None)
+    assert rc == 1
+    b = ctypes.c_size_t(0)
+    assert lib.sdgs_agr_bwd_workspace_size(1000, ctypes.byref(b)) == 0 and b.value > 0
+    assert lib.sdgs_agr_bwd_workspace_size(-1, ctypes.byref(b)) == 1
+    rc = lib.sdgs_densify_stats(ctypes.byref(s), ctypes.byref(v), None, None, None)
+    assert rc == 1 and b"densify" in lib.sdgs_last_error()
+    cfg = sdgs.DensifyCfg(float("nan"), 0.05, 0.25, 0.01)
+    out = sdgs.Densify(None, None, None, None, None, None)
+    rc = lib.sdgs_densify_stats(ctypes.byref(s), ctypes.byref(v), ctypes.byref(cfg), ctypes.byref(out), None)
+    assert rc == 1 and b"finite" in lib.sdgs_last_error()
+    # an image whose tile count would not fit the binning's 32-bit prefix sums
+    v.width = v.height = 65535 * 16
+    rc = lib.sdgs_bin_workspace_size(10, 10, v.width, v.height, ctypes.byref(b))
+    assert rc == 1
