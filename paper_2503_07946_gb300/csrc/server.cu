@@ -402,6 +402,7 @@ void worker_main(sdgs_server* s) {
 
 int check_server_view(const sdgs_view* v) {
   if (!v || v->width <= 0 || v->height <= 0 || v->width > 65535 * kTile || v->height > 65535 * kTile ||
+      (int64_t)((v->width + kTile - 1) / kTile) * ((v->height + kTile - 1) / kTile) > ((int64_t)1 << 26) ||
       !(v->fx > 0.f) || !(v->fy > 0.f)) {
     set_error("bad view");
     return SDGS_ERR_INVALID_ARG;
