@@ -656,6 +656,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency benchmark")
     ap.add_argument("--frames-only", action="store_true",
                     help="time the forward frames only (no e2e, fwd+bwd or CPU baseline); for profiling")
+    ap.add_argument("--fwd-bwd-only", action="store_true",
+                    help="time the fwd+bwd iterations only (config 3 workload); for profiling the backward")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -665,6 +667,12 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.fwd_bwd_only:
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(dev)
+        fb = fwd_bwd_its(synth.config_scene(1), synth.config_cameras(1)[0], args.steps, args.warmup, dev)
+        if rank == 0:
+            print(json.dumps({"metric": "fwd+bwd it/s", "fwd_bwd_it_s": fb}), flush=True)
     else:
         run_ours(args, rank, world)
     if world > 1 and args.impl == "ours":
