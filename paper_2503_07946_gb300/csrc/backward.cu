@@ -26,18 +26,19 @@ struct RasterBwdArgs {
   float* g2;  // [n][12]
 };
 
-// Sums g[0..8] over the warp by recursive halving: at each level a lane keeps one half of its
-// values and adds its partner's copy of that half, so 16 exchanges replace 9 full butterflies.
-// Afterwards lanes 2v and 2v + 1 hold the warp total of g[v] (v < 9); the result is returned
-// for those lanes (and 0 for lanes whose v >= 9).
+// Sums g[0..8] over the warp.  g[0..7] by recursive halving over lane bits 16, 8 and 4 (at each
+// level a lane keeps one half of its values and adds its partner's copy of that half), g[8] by
+// butterflies over the same bits; then the pair (g[c], g[8]) is halved over bit 2 and summed over
+// bit 1: 12 exchanges.  Afterwards a lane with bit 2 clear holds the warp total of
+// g[(lane >> 2) & 7] and a lane with bit 2 set the total of g[8].
 __device__ __forceinline__ float warp_sum9(const float g[9]) {
   const int lane = threadIdx.x & 31;
-  float v[16];
+  float v[8];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = i < 9 ? g[i] : 0.f;
-  // level k keeps the half of v selected by lane bit (4 - k) and folds the other half in
+  for (int i = 0; i < 8; ++i) v[i] = g[i];
+  float e = g[8];
 #pragma unroll
-  for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+  for (int half = 4, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
     const bool upper = (lane & bit) != 0;
 #pragma unroll
     for (int i = 0; i < half; ++i) {
@@ -45,36 +46,40 @@ __device__ __forceinline__ float warp_sum9(const float g[9]) {
       const float keep = upper ? v[i + half] : v[i];
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
     }
+    e += __shfl_xor_sync(0xffffffffu, e, bit);
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  const bool upper = (lane & 2) != 0;
+  const float keep = upper ? e : v[0];
+  const float x = keep + __shfl_xor_sync(0xffffffffu, upper ? v[0] : e, 2);
+  return x + __shfl_xor_sync(0xffffffffu, x, 1);
 }
 
-// Per-pixel state of the back-to-front replay.
-struct BwdPixel {
-  float T;                 // transmittance in front of the current position
-  float R0, R1, R2;        // colour seen behind the current position, normalised by T there
-  float d0, d1, d2;        // dL/dC of the pixel
-  uint32_t last;           // positions >= last were not blended in the forward
-};
-
-// Adjoint of one (pixel, Gaussian) blend for the thread's two pixels at once (rows r and r + 8:
-// same dx, dy as a pair), without branches, accumulated into g[9] = d(u, v, a, b, c, alpha_cond,
-// r, g, b).  A pixel that does not take the Gaussian gets alpha 0, which leaves its T, R and the
-// gradient unchanged exactly; the decisions are those of the forward (same exponent, alpha and
-// thresholds).  The gradient is accumulated per pixel in g2[9] (x: first pixel, y: second).
+// Per-pixel state of the back-to-front replay for the thread's two pixels (rows r and r + 8, the
+// same dx): transmittance in front of the current position, DR = dL/dC . R with R the colour seen
+// behind the current position normalised by T there, dL/dC, and the forward's stop position
+// (positions >= last were not blended).
 struct BwdPair {
-  float2 T, R0, R1, R2, d0, d1, d2;
+  float2 T, DR, d0, d1, d2;
   uint32_t last0, last1;
 };
 
-__device__ __forceinline__ bool unblend2(BwdPair& px, const float4& co, const float4& q, const float4& c,
-                                         float dx, float2 dy, uint32_t pos, float2 g[9]) {
+// Adjoint of one (pixel, Gaussian) blend for both pixels, without branches.  A pixel that does not
+// take the Gaussian gets alpha 0, which leaves T, DR and the sums unchanged exactly; the decisions
+// are those of the forward (same exponent, alpha and thresholds).  With dl = dL/d alpha (0 where
+// not taken or where the 0.99 clamp was active) and G the Gaussian's value, it accumulates, per
+// pixel (x: first, y: second),
+//   g = (dlG dx, dlG dy, dlG dx^2, dlG dx dy, dlG dy^2, dlG, dL/dr, dL/dg, dL/db),  dlG = dl G,
+// from which the flush forms d(u, v, a, b, c) with the conic and alpha_cond (alpha = alpha_cond G,
+// d alpha / d power = alpha) and d alpha_cond = sum dlG.  q is the scaled conic with q.w =
+// alpha_cond.
+__device__ __forceinline__ bool unblend2(BwdPair& px, const float4& q, const float4& c, float dx, float2 dy,
+                                         uint32_t pos, float2 g[9]) {
   const float a = __fmul_rn(__fmul_rn(q.x, dx), dx);
   const float bx = __fmul_rn(q.y, dx);
   const float2 t = __ffma2_rn(make_float2(q.z, q.z), dy, make_float2(bx, bx));
   const float2 p2 = __ffma2_rn(dy, t, make_float2(a, a));
   const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
-  const float2 raw = __fmul2_rn(make_float2(co.w, co.w), G);
+  const float2 raw = __fmul2_rn(make_float2(q.w, q.w), G);
   const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
   const bool h0 = pos < px.last0 && p2.x <= 0.f && al.x >= kAlphaMin;
   const bool h1 = pos < px.last1 && p2.y <= 0.f && al.y >= kAlphaMin;
@@ -85,39 +90,38 @@ __device__ __forceinline__ bool unblend2(BwdPair& px, const float4& co, const fl
   g[6] = __ffma2_rn(px.d0, w, g[6]);
   g[7] = __ffma2_rn(px.d1, w, g[7]);
   g[8] = __ffma2_rn(px.d2, w, g[8]);
-  float2 s = __fmul2_rn(px.d0, __fadd2_rn(make_float2(c.x, c.x), make_float2(-px.R0.x, -px.R0.y)));
-  s = __ffma2_rn(px.d1, __fadd2_rn(make_float2(c.y, c.y), make_float2(-px.R1.x, -px.R1.y)), s);
-  s = __ffma2_rn(px.d2, __fadd2_rn(make_float2(c.z, c.z), make_float2(-px.R2.x, -px.R2.y)), s);
-  const float2 dal = __fmul2_rn(px.T, s);
-  px.R0 = __ffma2_rn(om, px.R0, __fmul2_rn(make_float2(c.x, c.x), ae));
-  px.R1 = __ffma2_rn(om, px.R1, __fmul2_rn(make_float2(c.y, c.y), ae));
-  px.R2 = __ffma2_rn(om, px.R2, __fmul2_rn(make_float2(c.z, c.z), ae));
+  // dL/dC . c, then dL/d alpha = T (dL/dC . c - DR) and DR <- (1 - alpha) DR + alpha dL/dC . c
+  float2 dc = __fmul2_rn(px.d0, make_float2(c.x, c.x));
+  dc = __ffma2_rn(px.d1, make_float2(c.y, c.y), dc);
+  dc = __ffma2_rn(px.d2, make_float2(c.z, c.z), dc);
+  const float2 dal = __fmul2_rn(px.T, __fadd2_rn(dc, make_float2(-px.DR.x, -px.DR.y)));
+  px.DR = __ffma2_rn(ae, dc, __fmul2_rn(om, px.DR));
   // no derivative through the 0.99 clamp
   const float2 dl = make_float2(h0 && raw.x < kAlphaMax ? dal.x : 0.f, h1 && raw.y < kAlphaMax ? dal.y : 0.f);
-  g[5] = __ffma2_rn(dl, make_float2(fminf(G.x, 1.f), fminf(G.y, 1.f)), g[5]);  // G <= 1 where taken
-  const float2 dp = __fmul2_rn(dl, al);  // d alpha / d(power) = alpha
-  const float2 ddx = __ffma2_rn(make_float2(co.y, co.y), dy, make_float2(co.x * dx, co.x * dx));
-  const float2 ddy = __ffma2_rn(make_float2(co.z, co.z), dy, make_float2(co.y * dx, co.y * dx));
-  g[0] = __ffma2_rn(dp, ddx, g[0]);
-  g[1] = __ffma2_rn(dp, ddy, g[1]);
-  const float hdx2 = -0.5f * dx * dx;
-  g[2] = __ffma2_rn(dp, make_float2(hdx2, hdx2), g[2]);
-  g[3] = __ffma2_rn(dp, __fmul2_rn(make_float2(-dx, -dx), dy), g[3]);
-  g[4] = __ffma2_rn(dp, __fmul2_rn(make_float2(-0.5f, -0.5f), __fmul2_rn(dy, dy)), g[4]);
+  const float2 dlG = __fmul2_rn(dl, G);
+  g[5] = __fadd2_rn(g[5], dlG);
+  const float2 dx2 = make_float2(dx, dx);
+  g[0] = __ffma2_rn(dlG, dx2, g[0]);
+  g[1] = __ffma2_rn(dlG, dy, g[1]);
+  const float dxx = dx * dx;
+  g[2] = __ffma2_rn(dlG, make_float2(dxx, dxx), g[2]);
+  g[3] = __ffma2_rn(dlG, __fmul2_rn(dx2, dy), g[3]);
+  g[4] = __ffma2_rn(dlG, __fmul2_rn(dy, dy), g[4]);
   return h0 || h1;
 }
 
 // Back-to-front replay per 16x16 tile, 128 threads with two pixels each (rows r and r + 8).
-// The tile's list is staged from the back in batches of 128; each Gaussian's gradient is summed
-// over the thread's pixels, then over the warp, and added to the per-Gaussian buffer with one
-// atomic per component and warp.
+// The tile's list is staged from the back in batches of 128; each Gaussian's sums are added over
+// the thread's pixels, then over the warp, then over the block's warps in shared memory, and the
+// batch ends with one set of global atomics per Gaussian.
 __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArgs a) {
   griddep_wait();
   __shared__ float2 s_xy[kThreads];
-  __shared__ float4 s_co[kThreads];
+  __shared__ float4 s_co[kThreads];  // conic and alpha_cond
+  __shared__ float4 s_q[kThreads];   // scaled conic and alpha_cond
   __shared__ float4 s_rgb[kThreads];
   __shared__ uint32_t s_id[kThreads];
-  __shared__ float s_g[kThreads][9];  // this batch's per-Gaussian gradient, summed over the warps
+  __shared__ float s_g[kThreads][9];  // this batch's per-Gaussian sums over the tile
   __shared__ uint32_t s_max;
 
   const int tile = blockIdx.x;
@@ -131,30 +135,28 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
 
   BwdPair pp;
   {
-    BwdPixel pxs[2];
+    float T[2], DR[2], d[2][3];
+    uint32_t last[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-      BwdPixel& p = pxs[r];
-      p.T = 1.f; p.last = 0; p.d0 = p.d1 = p.d2 = 0.f;
-      p.R0 = a.bg[0]; p.R1 = a.bg[1]; p.R2 = a.bg[2];
+      T[r] = 1.f; last[r] = 0; d[r][0] = d[r][1] = d[r][2] = 0.f;
       if (px < a.width && py[r] < a.height) {
         const int pix = py[r] * a.width + px;
-        p.T = a.final_T[pix];
-        p.last = a.n_contrib[pix];
-        p.d0 = a.dL_dimage[3 * pix + 0];
-        p.d1 = a.dL_dimage[3 * pix + 1];
-        p.d2 = a.dL_dimage[3 * pix + 2];
+        T[r] = a.final_T[pix];
+        last[r] = a.n_contrib[pix];
+        d[r][0] = a.dL_dimage[3 * pix + 0];
+        d[r][1] = a.dL_dimage[3 * pix + 1];
+        d[r][2] = a.dL_dimage[3 * pix + 2];
       }
+      DR[r] = d[r][0] * a.bg[0] + d[r][1] * a.bg[1] + d[r][2] * a.bg[2];  // R = background at the end
     }
-    pp.T = make_float2(pxs[0].T, pxs[1].T);
-    pp.R0 = make_float2(pxs[0].R0, pxs[1].R0);
-    pp.R1 = make_float2(pxs[0].R1, pxs[1].R1);
-    pp.R2 = make_float2(pxs[0].R2, pxs[1].R2);
-    pp.d0 = make_float2(pxs[0].d0, pxs[1].d0);
-    pp.d1 = make_float2(pxs[0].d1, pxs[1].d1);
-    pp.d2 = make_float2(pxs[0].d2, pxs[1].d2);
-    pp.last0 = pxs[0].last;
-    pp.last1 = pxs[1].last;
+    pp.T = make_float2(T[0], T[1]);
+    pp.DR = make_float2(DR[0], DR[1]);
+    pp.d0 = make_float2(d[0][0], d[1][0]);
+    pp.d1 = make_float2(d[0][1], d[1][1]);
+    pp.d2 = make_float2(d[0][2], d[1][2]);
+    pp.last0 = last[0];
+    pp.last1 = last[1];
   }
   const uint32_t mylast = max(pp.last0, pp.last1);
   const float2 fy2 = make_float2(fy[0], fy[1]);
@@ -164,6 +166,9 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
   __syncthreads();
   const int end = (int)s_max;  // positions >= end were blended at no pixel of the tile
 
+  // the lane that adds a warp total into s_g, and which sum it holds
+  const bool adder = (lane & 3) == 0 || lane == 2;
+  const int slot = (lane & 2) ? 8 : (lane >> 2);
   for (int i = threadIdx.x; i < kThreads * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
   for (int top = end; top > 0; top -= kThreads) {
     const int lo = max(0, top - kThreads);
@@ -171,8 +176,10 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
     __syncthreads();  // the previous batch is fully consumed
     if (j < top) {
       const uint32_t gid = a.point_list[range.x + j];
+      const float4 co = a.conic_opacity[gid];
       s_xy[threadIdx.x] = a.mean2d[gid];
-      s_co[threadIdx.x] = a.conic_opacity[gid];
+      s_co[threadIdx.x] = co;
+      s_q[threadIdx.x] = scaled_conic(co);
       s_rgb[threadIdx.x] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
       s_id[threadIdx.x] = gid;
     }
@@ -180,33 +187,42 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
     __syncthreads();
     for (int k = cnt - 1; k >= 0; --k) {
       const float2 m = s_xy[k];
-      const float4 co_k = s_co[k];
-      const float4 q = scaled_conic(co_k);
+      const float4 q = s_q[k];
       const float4 c = s_rgb[k];
       const uint32_t pos = (uint32_t)(lo + k);
       float2 g2[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) g2[i] = make_float2(0.f, 0.f);
       const float dx = fx - m.x;
-      const bool hit = unblend2(pp, co_k, q, c, dx, __fadd2_rn(fy2, make_float2(-m.y, -m.y)), pos, g2);
+      const bool hit = unblend2(pp, q, c, dx, __fadd2_rn(fy2, make_float2(-m.y, -m.y)), pos, g2);
       if (__any_sync(0xffffffffu, hit)) {
         float g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = g2[i].x + g2[i].y;
         const float tot = warp_sum9(g);
-        const int v = lane >> 1;
-        if ((lane & 1) == 0 && v < 9) atomicAdd(&s_g[k][v], tot);
+        if (adder) atomicAdd(&s_g[k][slot], tot);
       }
     }
     __syncthreads();
-    // one set of global atomics per Gaussian and block
+    // one set of global atomics per Gaussian and block: d(u, v) = alpha_cond Conic (Sx, Sy),
+    // d(a, b, c) = -alpha_cond (Sxx / 2, Sxy, Syy / 2)
     if (threadIdx.x < cnt) {
       float* out = a.g2 + (size_t)kG2 * s_id[threadIdx.x];
+      const float4 co = s_co[threadIdx.x];
+      float* S = s_g[threadIdx.x];
+      const float al = co.w;
+      float o[9];
+      o[0] = al * (co.x * S[0] + co.y * S[1]);
+      o[1] = al * (co.y * S[0] + co.z * S[1]);
+      o[2] = -0.5f * al * S[2];
+      o[3] = -al * S[3];
+      o[4] = -0.5f * al * S[4];
+#pragma unroll
+      for (int i = 5; i < 9; ++i) o[i] = S[i];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const float x = s_g[threadIdx.x][i];
-        if (x != 0.f) atomicAdd(out + i, x);
-        s_g[threadIdx.x][i] = 0.f;
+        if (o[i] != 0.f) atomicAdd(out + i, o[i]);
+        S[i] = 0.f;
       }
     }
   }
