@@ -38,7 +38,7 @@ FLOP_PER_EVAL = 23
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one
 # `ncu --set full` capture of render_fwd_kernel.  Set to None whenever render_fwd_kernel changes
 # until it is captured again.
-RENDER_FWD_TRAFFIC_BYTES = 12.82688e6
+RENDER_FWD_TRAFFIC_BYTES = 12.827392e6
 
 
 def load_peaks() -> dict:
@@ -612,10 +612,13 @@ def fwd_bwd_its(scene, cam, steps: int, warm: int, dev, agr: bool = False) -> di
     from paper_2503_07946_gb300 import sdgs
     target_scene = synth.perturb_scene(scene)
     view = sdgs.view_struct(cam)
-    r = prender.Renderer(scene.n, cam.width, cam.height)
+    # the training-loop renderer: no host synchronisation per frame (the instance count is
+    # checked one frame later; no timed frame may have overflowed)
+    r = prender.Renderer(scene.n, cam.width, cam.height, deferred_check=True)
     tt = prender.scene_to_device(target_scene)
-    with torch.no_grad():
-        target = r.forward(sdgs.scene_struct(tt, scene.lambda_t, scene.lambda_d), view).clone()
+    with torch.no_grad():  # the target through the synchronising renderer (capacity checked)
+        target = prender.Renderer(scene.n, cam.width, cam.height).forward(
+            sdgs.scene_struct(tt, scene.lambda_t, scene.lambda_d), view).clone()
     params = {k: v.clone().requires_grad_(True) for k, v in prender.scene_to_device(scene).items()}
     weights = {k: v.clone().requires_grad_(True) for k, v in agr_weights_dev(dev).items()} if agr else None
 
@@ -633,13 +636,17 @@ def fwd_bwd_its(scene, cam, steps: int, warm: int, dev, agr: bool = False) -> di
 
     for _ in range(max(warm, 1)):
         it()
+    r.check_deferred()
     torch.cuda.synchronize()
+    overflowed = r.overflowed_frames
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
         it()
     e1.record()
     torch.cuda.synchronize()
+    r.check_deferred()
+    assert r.overflowed_frames == overflowed, "a timed frame exceeded the bins' capacity"
     ms = e0.elapsed_time(e1) / steps
     return {"value": 1000.0 / ms, "unit": "it/s", "ms_per_it": ms,
             "workload": "config 3: 300k Gaussians, 800x800, camera 0, L2 loss vs a perturbed-parameter target"

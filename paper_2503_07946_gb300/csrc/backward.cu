@@ -9,7 +9,6 @@ namespace sdgs {
 
 namespace {
 
-constexpr int kThreads = kTilePixels / 2;
 constexpr int kG2 = 12;  // floats per Gaussian of screen-space gradient: u v a b c alpha r g b _ _ _
 
 struct RasterBwdArgs {
@@ -54,7 +53,7 @@ __device__ __forceinline__ float warp_sum9(const float g[9]) {
   return x + __shfl_xor_sync(0xffffffffu, x, 1);
 }
 
-// Per-pixel state of the back-to-front replay for the thread's two pixels (rows r and r + 8, the
+// Per-pixel state of the back-to-front replay for a pair of a thread's pixels (one column, the
 // same dx): transmittance in front of the current position, DR = dL/dC . R with R the colour seen
 // behind the current position normalised by T there, dL/dC, and the forward's stop position
 // (positions >= last were not blended).
@@ -110,56 +109,64 @@ __device__ __forceinline__ bool unblend2(BwdPair& px, const float4& q, const flo
   return h0 || h1;
 }
 
-// Back-to-front replay per 16x16 tile, 128 threads with two pixels each (rows r and r + 8).
-// The tile's list is staged from the back in batches of 128; each Gaussian's sums are added over
-// the thread's pixels, then over the warp, then over the block's warps in shared memory, and the
-// batch ends with one set of global atomics per Gaussian.
-__global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArgs a) {
+// Back-to-front replay per 16x16 tile, 64 threads with four pixels each: column x, rows r, r + 8
+// (pair A) and r + 4, r + 12 (pair B).  The tile's list is staged from the back in batches of 128;
+// each Gaussian's sums are added over the thread's pixels, then over the warp, then over the
+// block's warps in shared memory, and the batch ends with one set of global atomics per Gaussian.
+constexpr int kBwdThreads = kTilePixels / 4;
+constexpr int kBatch = 128;
+
+// The pixel state of a pair (rows py0 and py1 of column px) from the forward's outputs.
+__device__ __forceinline__ void load_pair(const RasterBwdArgs& a, int px, int py0, int py1, BwdPair& pp) {
+  float T[2], DR[2], d[2][3];
+  uint32_t last[2];
+  const int py[2] = {py0, py1};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    T[r] = 1.f; last[r] = 0; d[r][0] = d[r][1] = d[r][2] = 0.f;
+    if (px < a.width && py[r] < a.height) {
+      const int pix = py[r] * a.width + px;
+      T[r] = a.final_T[pix];
+      last[r] = a.n_contrib[pix];
+      d[r][0] = a.dL_dimage[3 * pix + 0];
+      d[r][1] = a.dL_dimage[3 * pix + 1];
+      d[r][2] = a.dL_dimage[3 * pix + 2];
+    }
+    DR[r] = d[r][0] * a.bg[0] + d[r][1] * a.bg[1] + d[r][2] * a.bg[2];  // R = background at the end
+  }
+  pp.T = make_float2(T[0], T[1]);
+  pp.DR = make_float2(DR[0], DR[1]);
+  pp.d0 = make_float2(d[0][0], d[1][0]);
+  pp.d1 = make_float2(d[0][1], d[1][1]);
+  pp.d2 = make_float2(d[0][2], d[1][2]);
+  pp.last0 = last[0];
+  pp.last1 = last[1];
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 16) raster_bwd_kernel(const RasterBwdArgs a) {
   griddep_wait();
-  __shared__ float2 s_xy[kThreads];
-  __shared__ float4 s_co[kThreads];  // conic and alpha_cond
-  __shared__ float4 s_q[kThreads];   // scaled conic and alpha_cond
-  __shared__ float4 s_rgb[kThreads];
-  __shared__ uint32_t s_id[kThreads];
-  __shared__ float s_g[kThreads][9];  // this batch's per-Gaussian sums over the tile
+  __shared__ float2 s_xy[kBatch];
+  __shared__ float4 s_co[kBatch];  // conic and alpha_cond
+  __shared__ float4 s_q[kBatch];   // scaled conic and alpha_cond
+  __shared__ float4 s_rgb[kBatch];
+  __shared__ uint32_t s_id[kBatch];
+  __shared__ float s_g[kBatch][9];  // this batch's per-Gaussian sums over the tile
   __shared__ uint32_t s_max;
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   const int lane = threadIdx.x & 31;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py[2] = {ty * kTile + (int)(threadIdx.x / kTile), ty * kTile + (int)(threadIdx.x / kTile) + kTile / 2};
+  const int r0 = ty * kTile + (int)(threadIdx.x / kTile);
   const float fx = (float)px + 0.5f;
-  const float fy[2] = {(float)py[0] + 0.5f, (float)py[1] + 0.5f};
   const uint2 range = a.ranges[tile];
 
-  BwdPair pp;
-  {
-    float T[2], DR[2], d[2][3];
-    uint32_t last[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      T[r] = 1.f; last[r] = 0; d[r][0] = d[r][1] = d[r][2] = 0.f;
-      if (px < a.width && py[r] < a.height) {
-        const int pix = py[r] * a.width + px;
-        T[r] = a.final_T[pix];
-        last[r] = a.n_contrib[pix];
-        d[r][0] = a.dL_dimage[3 * pix + 0];
-        d[r][1] = a.dL_dimage[3 * pix + 1];
-        d[r][2] = a.dL_dimage[3 * pix + 2];
-      }
-      DR[r] = d[r][0] * a.bg[0] + d[r][1] * a.bg[1] + d[r][2] * a.bg[2];  // R = background at the end
-    }
-    pp.T = make_float2(T[0], T[1]);
-    pp.DR = make_float2(DR[0], DR[1]);
-    pp.d0 = make_float2(d[0][0], d[1][0]);
-    pp.d1 = make_float2(d[0][1], d[1][1]);
-    pp.d2 = make_float2(d[0][2], d[1][2]);
-    pp.last0 = last[0];
-    pp.last1 = last[1];
-  }
-  const uint32_t mylast = max(pp.last0, pp.last1);
-  const float2 fy2 = make_float2(fy[0], fy[1]);
+  BwdPair pa, pb;
+  load_pair(a, px, r0, r0 + 8, pa);
+  load_pair(a, px, r0 + 4, r0 + 12, pb);
+  const uint32_t mylast = max(max(pa.last0, pa.last1), max(pb.last0, pb.last1));
+  const float2 fya = make_float2((float)r0 + 0.5f, (float)(r0 + 8) + 0.5f);
+  const float2 fyb = make_float2((float)(r0 + 4) + 0.5f, (float)(r0 + 12) + 0.5f);
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
   atomicMax(&s_max, mylast);
@@ -169,19 +176,23 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
   // the lane that adds a warp total into s_g, and which sum it holds
   const bool adder = (lane & 3) == 0 || lane == 2;
   const int slot = (lane & 2) ? 8 : (lane >> 2);
-  for (int i = threadIdx.x; i < kThreads * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
-  for (int top = end; top > 0; top -= kThreads) {
-    const int lo = max(0, top - kThreads);
-    const int j = lo + threadIdx.x;
+  for (int i = threadIdx.x; i < kBatch * 9; i += kBwdThreads) (&s_g[0][0])[i] = 0.f;
+  for (int top = end; top > 0; top -= kBatch) {
+    const int lo = max(0, top - kBatch);
     __syncthreads();  // the previous batch is fully consumed
-    if (j < top) {
-      const uint32_t gid = a.point_list[range.x + j];
-      const float4 co = a.conic_opacity[gid];
-      s_xy[threadIdx.x] = a.mean2d[gid];
-      s_co[threadIdx.x] = co;
-      s_q[threadIdx.x] = scaled_conic(co);
-      s_rgb[threadIdx.x] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
-      s_id[threadIdx.x] = gid;
+#pragma unroll
+    for (int h = 0; h < kBatch / kBwdThreads; ++h) {
+      const int e = threadIdx.x + h * kBwdThreads;
+      const int j = lo + e;
+      if (j < top) {
+        const uint32_t gid = a.point_list[range.x + j];
+        const float4 co = a.conic_opacity[gid];
+        s_xy[e] = a.mean2d[gid];
+        s_co[e] = co;
+        s_q[e] = scaled_conic(co);
+        s_rgb[e] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
+        s_id[e] = gid;
+      }
     }
     const int cnt = top - lo;
     __syncthreads();
@@ -194,8 +205,10 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
 #pragma unroll
       for (int i = 0; i < 9; ++i) g2[i] = make_float2(0.f, 0.f);
       const float dx = fx - m.x;
-      const bool hit = unblend2(pp, q, c, dx, __fadd2_rn(fy2, make_float2(-m.y, -m.y)), pos, g2);
-      if (__any_sync(0xffffffffu, hit)) {
+      const float2 my = make_float2(-m.y, -m.y);
+      const bool ha = unblend2(pa, q, c, dx, __fadd2_rn(fya, my), pos, g2);
+      const bool hb = unblend2(pb, q, c, dx, __fadd2_rn(fyb, my), pos, g2);
+      if (__any_sync(0xffffffffu, ha || hb)) {
         float g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = g2[i].x + g2[i].y;
@@ -206,10 +219,10 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(const RasterBwdArg
     __syncthreads();
     // one set of global atomics per Gaussian and block: d(u, v) = alpha_cond Conic (Sx, Sy),
     // d(a, b, c) = -alpha_cond (Sxx / 2, Sxy, Syy / 2)
-    if (threadIdx.x < cnt) {
-      float* out = a.g2 + (size_t)kG2 * s_id[threadIdx.x];
-      const float4 co = s_co[threadIdx.x];
-      float* S = s_g[threadIdx.x];
+    for (int e = threadIdx.x; e < cnt; e += kBwdThreads) {
+      float* out = a.g2 + (size_t)kG2 * s_id[e];
+      const float4 co = s_co[e];
+      float* S = s_g[e];
       const float al = co.w;
       float o[9];
       o[0] = al * (co.x * S[0] + co.y * S[1]);
@@ -567,7 +580,7 @@ cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdg
   for (int c = 0; c < 3; ++c) r.bg[c] = v.bg[c];
   r.g2 = g2;
   const int tiles = r.tiles_x * tiles_of(v.height);
-  raster_bwd_kernel<<<tiles, kThreads, 0, st>>>(r);
+  raster_bwd_kernel<<<tiles, kBwdThreads, 0, st>>>(r);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   GeomBwdArgs a;

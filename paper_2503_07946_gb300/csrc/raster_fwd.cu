@@ -51,8 +51,8 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
   const float2 e = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
   const float2 m = __fmul2_rn(make_float2(q.w, q.w), e);
   const float2 al = make_float2(fminf(kAlphaMax, m.x), fminf(kAlphaMax, m.y));
-  const float2 Tn = __fmul2_rn(px.T, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-al.x, -al.y)));
   const float2 aT = __fmul2_rn(al, px.T);
+  const float2 Tn = __fadd2_rn(px.T, make_float2(-aT.x, -aT.y));  // T (1 - alpha) as T - alpha T
   const bool hit0 = !px.done0 && p2.x <= 0.f && al.x >= kAlphaMin;
   const bool hit1 = !px.done1 && p2.y <= 0.f && al.y >= kAlphaMin;
   const bool stop0 = hit0 && Tn.x < kTMin, stop1 = hit1 && Tn.y < kTMin;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
   px.c0 = __ffma2_rn(make_float2(c.x, c.x), w, px.c0);
   px.c1 = __ffma2_rn(make_float2(c.y, c.y), w, px.c1);
   px.c2 = __ffma2_rn(make_float2(c.z, c.z), w, px.c2);
-  px.T = make_float2(take0 ? Tn.x : px.T.x, take1 ? Tn.y : px.T.y);
+  px.T = __fadd2_rn(px.T, make_float2(-w.x, -w.y));  // Tn where taken, T - 0 = T elsewhere
   px.last0 = take0 ? pos1 : px.last0;
   px.last1 = take1 ? pos1 : px.last1;
   px.done0 = px.done0 || stop0;

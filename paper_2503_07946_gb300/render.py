@@ -5,6 +5,8 @@ render_bwd) and own the device buffers; all arithmetic is in the CUDA kernels.
 """
 from __future__ import annotations
 
+import warnings
+
 import numpy as np
 import torch
 
@@ -24,12 +26,25 @@ class Renderer:
 
     `capacity` bounds the (tile, Gaussian) instances; when a frame needs more, the bins are
     reallocated at 1.25x the count and binning runs again.
+
+    deferred_check=True removes the host synchronisation after binning: the frame's instance
+    count is copied to pinned host memory behind the binning and read at the next forward (by
+    then the GPU is normally past it, so the host never waits for an idle GPU).  A frame that
+    needed more than the capacity is then rendered with the nearest `capacity` instances (the
+    overflow contract of sdgs_bin_sort); the next forward warns, counts it in
+    `overflowed_frames` and grows the bins.  Meant for training loops, where the capacity is
+    sized by the first frames.
     """
 
     def __init__(self, n: int, width: int, height: int, capacity: int | None = None, device="cuda",
-                 tile_keys: bool = False):
+                 tile_keys: bool = False, deferred_check: bool = False):
         self.n, self.width, self.height, self.device = n, width, height, device
         self.tile_keys = tile_keys
+        self.deferred_check = deferred_check
+        self.overflowed_frames = 0
+        self._k_host = torch.zeros(1, dtype=torch.int64, pin_memory=True) if deferred_check else None
+        self._k_event = None
+        self._k_capacity = 0
         self.proj = sdgs.ProjectedBuffers(n, device)
         self.bins = sdgs.BinBuffers(n, capacity if capacity is not None else max(4096, 16 * n), width,
                                     height, device, tile_keys=tile_keys)
@@ -53,9 +68,40 @@ class Renderer:
         self.num_instances = k
         return k
 
+    def check_deferred(self) -> bool:
+        """Reads the instance count of the last deferred frame (waiting only for that point of its
+        stream); grows the bins and returns True when that frame exceeded the capacity."""
+        if self._k_event is None:
+            return False
+        self._k_event.synchronize()
+        self._k_event = None
+        k = int(self._k_host[0])
+        self.num_instances = k
+        if k <= self._k_capacity:
+            return False
+        self.overflowed_frames += 1
+        if k > self.bins.capacity:
+            self.grow(k)
+        return True
+
+    def _bin_deferred(self, view: sdgs.View, stream=None):
+        if self.check_deferred():
+            warnings.warn("the previous frame had more (tile, Gaussian) instances than the bins' capacity and "
+                          "was rendered with the nearest ones; the bins have grown", RuntimeWarning, stacklevel=3)
+        sdgs.bin_sort(self.proj, view, self.bins, sync=False, stream=stream)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            self._k_host.copy_(self.bins.num_instances, non_blocking=True)
+            self._k_event = torch.cuda.Event()
+            self._k_event.record(st)
+        self._k_capacity = self.bins.capacity
+
     def forward(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
         sdgs.slice_project(scene, view, self.proj, stream)
-        self.bin(view, stream)
+        if self.deferred_check:
+            self._bin_deferred(view, stream)
+        else:
+            self.bin(view, stream)
         sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream)
         return self.image
 
@@ -78,10 +124,11 @@ class Render7DGS(torch.autograd.Function):
     def forward(ctx, mean7, L28, opacity, sh, lam, view: sdgs.View, renderer: Renderer, dir_mode: int):
         t = dict(mean7=mean7.contiguous(), L28=L28.contiguous(), opacity=opacity.contiguous(),
                  sh=sh.contiguous())
-        lam_t, lam_d = (float(x) for x in lam.detach().cpu().tolist())
+        lam_t, lam_d = (float(x) for x in lam.detach().cpu().tolist())  # no device round trip for a host lam
         scene = sdgs.scene_struct(t, lam_t, lam_d, dir_mode)
         image = renderer.forward(scene, view).clone()
         ctx.renderer, ctx.view, ctx.lam, ctx.dir_mode = renderer, view, (lam_t, lam_d), dir_mode
+        ctx.lam_device = lam.device
         ctx.final_T = renderer.final_T.clone()
         ctx.n_contrib = renderer.n_contrib.clone()
         ctx.save_for_backward(t["mean7"], t["L28"], t["opacity"], t["sh"])
@@ -93,20 +140,29 @@ class Render7DGS(torch.autograd.Function):
         t = dict(mean7=mean7, L28=L28, opacity=opacity, sh=sh)
         scene = sdgs.scene_struct(t, *ctx.lam, ctx.dir_mode)
         grads = {k: torch.zeros_like(v) for k, v in t.items()}
-        grads["lam"] = torch.zeros(2, dtype=torch.float32, device=mean7.device)
+        want_lam = ctx.needs_input_grad[4]
+        if want_lam:  # otherwise no dlambda: the kernel skips that reduction
+            grads["lam"] = torch.zeros(2, dtype=torch.float32, device=mean7.device)
         r = ctx.renderer
         ws = torch.empty(max(sdgs.bwd_workspace_size(r.n), 256), dtype=torch.uint8, device=mean7.device)
         sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, ctx.final_T, ctx.n_contrib,
                         grad_image.contiguous(), ws, grads)
-        return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], grads["lam"], None, None, None
+        dlam = grads["lam"].to(ctx.lam_device) if want_lam else None
+        return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], dlam, None, None, None
 
 
 def render_image(mean7, L28, opacity, sh, view: sdgs.View, lambda_t, lambda_d, renderer: Renderer,
                  dir_mode: int = 0) -> torch.Tensor:
-    """lambda_t, lambda_d: floats or 0-d tensors (gradients reach tensors that require them)."""
-    dev = mean7.device
-    lam = torch.stack([torch.as_tensor(lambda_t, dtype=torch.float32, device=dev).reshape(()),
-                       torch.as_tensor(lambda_d, dtype=torch.float32, device=dev).reshape(())])
+    """lambda_t, lambda_d: floats or 0-d tensors (gradients reach tensors that require them).
+
+    The kernels take lambda by value, so a device tensor is read back to the host (one
+    synchronisation); plain floats stay on the host."""
+    if torch.is_tensor(lambda_t) or torch.is_tensor(lambda_d):
+        dev = mean7.device
+        lam = torch.stack([torch.as_tensor(lambda_t, dtype=torch.float32, device=dev).reshape(()),
+                           torch.as_tensor(lambda_d, dtype=torch.float32, device=dev).reshape(())])
+    else:
+        lam = torch.tensor([float(lambda_t), float(lambda_d)], dtype=torch.float32)
     return Render7DGS.apply(mean7, L28, opacity, sh, lam, view, renderer, dir_mode)
 
 

@@ -64,3 +64,39 @@ def test_gradients_match_oracle(case):
     rep = _check(scene, cam, seed=3)
     for k, v in rep.items():
         assert v <= GRAD_TOL, (k, rep)
+
+
+@pytest.mark.parametrize("lam_kind", ["host_float", "host_tensor"])
+def test_host_lambda_matches_device_lambda(lam_kind):
+    """Lambdas given on the host (no device round trip; a plain float also skips the lambda
+    reduction) give the image and parameter gradients of device lambdas; a host tensor that
+    requires grad gets its gradient on the host."""
+    scene, cam = _case("rotated")
+    rng = np.random.default_rng(4)
+    dL = torch.as_tensor(rng.normal(size=(cam.height, cam.width, 3)), dtype=torch.float32, device="cuda")
+    dev = prender.scene_to_device(scene)
+    view = sdgs.view_struct(cam)
+    runs = []
+    for kind in ("device", lam_kind):
+        params = {k: v.clone().requires_grad_(True) for k, v in dev.items()}
+        r = prender.Renderer(scene.n, cam.width, cam.height)
+        lam = None
+        if kind == "host_float":
+            lt, ld = scene.lambda_t, scene.lambda_d
+        else:
+            lam = torch.tensor([scene.lambda_t, scene.lambda_d], dtype=torch.float32,
+                               device="cuda" if kind == "device" else "cpu", requires_grad=True)
+            lt, ld = lam[0], lam[1]
+        img = prender.render_image(params["mean7"], params["L28"], params["opacity"], params["sh"], view,
+                                   lt, ld, r)
+        (img * dL).sum().backward()
+        grads = {k: v.grad.cpu() for k, v in params.items()}
+        if lam is not None:
+            assert lam.grad.device == lam.device
+            grads["lam"] = lam.grad.cpu()
+        runs.append((img.detach().cpu(), grads))
+    assert torch.equal(runs[0][0], runs[1][0])
+    for k, g in runs[1][1].items():
+        ref = runs[0][1][k]
+        # the same sums, added by atomics in another order
+        assert float((g - ref).abs().max()) <= 1e-4 * float(ref.abs().max()), k

@@ -178,3 +178,31 @@ def test_render_end_to_end_against_fp64_oracle(scene0, ci):
     # (they may differ by Gaussians on the reachability boundary, which reach no pixel)
     match = np.mean(nc[ok] == ref["n_contrib"].numpy()[ok])
     assert match > 0.99, match
+
+
+def test_renderer_deferred_check_matches_and_grows(scene0):
+    """Renderer(deferred_check=True) renders the frames of the synchronising renderer; a frame
+    that exceeded the capacity is reported at the next forward, which grows the bins first."""
+    import warnings as _w
+    from paper_2503_07946_gb300 import render as prender
+    cam = _cams()[1]
+    dev = prender.scene_to_device(scene0)
+    st = U.sdgs.scene_struct(dev, scene0.lambda_t, scene0.lambda_d)
+    view = U.sdgs.view_struct(cam)
+    ref_r = prender.Renderer(scene0.n, cam.width, cam.height)
+    ref = ref_r.forward(st, view).clone()
+    k = ref_r.num_instances
+    r = prender.Renderer(scene0.n, cam.width, cam.height, deferred_check=True)
+    with _w.catch_warnings():
+        _w.simplefilter("error")
+        for _ in range(2):
+            img = r.forward(st, view).clone()
+            assert torch.equal(img, ref)
+    assert not r.check_deferred() and r.num_instances == k and r.overflowed_frames == 0
+    small = prender.Renderer(scene0.n, cam.width, cam.height, capacity=k // 4, deferred_check=True)
+    small.forward(st, view)  # truncated to the nearest k // 4 instances
+    with pytest.warns(RuntimeWarning):
+        img = small.forward(st, view).clone()
+    assert small.overflowed_frames == 1 and small.bins.capacity >= k
+    assert torch.equal(img, ref)
+    assert not small.check_deferred() and small.num_instances == k
