@@ -278,13 +278,14 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
       run += c;
     }
     uint32_t* mine = status + tile * kBins + dg;
-    store_status(mine, (tile == 0 ? kStatusInclusive : kStatusAggregate) | run);
+    const bool used = dg <= (int)dmask;  // digits of `width` bits: the other bins stay empty
+    if (used) store_status(mine, (tile == 0 ? kStatusInclusive : kStatusAggregate) | run);
     uint32_t before = 0;  // keys with digit dg in tiles 0 .. tile - 1
     int spins = 0;
     // Wait for the nearest unresolved tile (one load per poll, with a short sleep), then take up
     // to kLookbackWindow - 1 further tiles from one round of parallel loads, nearest first, until
     // an inclusive count or a tile that has published nothing yet.
-    for (int64_t j = tile - 1; j >= 0;) {
+    for (int64_t j = used ? tile - 1 : -1; j >= 0;) {
       const uint32_t near = load_status(status + j * kBins + dg);
       if ((near & ~kStatusCount) == 0u) {
         if (++spins > kLookbackSpins) {
@@ -314,7 +315,7 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
       }
       if (done) break;
     }
-    if (tile > 0) store_status(mine, kStatusInclusive | (before + run));
+    if (used && tile > 0) store_status(mine, kStatusInclusive | (before + run));
     uint32_t tot;
     const uint32_t incl = block_inclusive_scan<uint32_t, kRadixThreads>(run, &tot);
     s_dstart[dg] = incl - run;
@@ -449,8 +450,8 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
 // Binning-specific kernels.
 // ------------------------------------------------------------------------------------------
 
-// Zeroes the words binning accumulates into or reads before writing: the tile ranges, the error
-// word, the instance count (when there are no Gaussians) and both sorts' scratch.  One kernel
+// Zeroes the words binning accumulates into or reads before writing: the error word, the tile
+// ranges and the instance count (when there are no Gaussians) and both sorts' scratch.  One kernel
 // instead of several memsets keeps the render's launches a chain of kernels.
 struct ClearJob {
   uint32_t* ptr[5];
@@ -725,15 +726,36 @@ span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__
   flush_digits(s_hist, passes, hist);
 }
 
+// First position in keys[0, n) (sorted) whose key is >= t, found by the calling warp: each round
+// probes 32 evenly spaced positions of [lo, hi) and keeps the part between the last probe below t
+// and the first probe at or above it (32 times shorter), until [lo, hi) is empty.  All 32 lanes
+// call; every lane returns the answer.
+__device__ __forceinline__ int64_t warp_lower_bound(const uint32_t* __restrict__ keys, int64_t n, uint32_t t) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;  // keys before lo are < t; keys from hi on are >= t
+  while (hi > lo) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t p = lo + (int64_t)lane * step;
+    const bool below = p < hi && keys[p] < t;
+    const int c = __popc(__ballot_sync(0xffffffffu, below));  // the probes below t are a prefix
+    const int64_t nhi = lo + (int64_t)c * step;
+    lo = c > 0 ? lo + (int64_t)(c - 1) * step + 1 : lo;
+    hi = nhi < hi ? nhi : hi;
+  }
+  return lo;
+}
+
+// ranges[t] = [first, end) of tile t in the sorted keys, (0, 0) for a tile without instances; one
+// warp per tile.
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t cap,
-                              uint2* __restrict__ ranges) {
+                              int num_tiles, uint2* __restrict__ ranges) {
   griddep_wait();
   const int64_t n = element_count(nptr, 0, cap);
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const uint32_t t = keys[j];
-  if (j == 0 || keys[j - 1] != t) ranges[t].x = (uint32_t)j;
-  if (j == n - 1 || keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
+  const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (t >= num_tiles) return;  // whole warps
+  const int64_t a = warp_lower_bound(keys, n, (uint32_t)t);
+  const int64_t b = warp_lower_bound(keys, n, (uint32_t)t + 1u);
+  if ((threadIdx.x & 31) == 0) ranges[t] = b > a ? make_uint2((uint32_t)a, (uint32_t)b) : make_uint2(0u, 0u);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -782,7 +804,8 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   const float4* co = reinterpret_cast<const float4*>(proj.conic_opacity);
 
   ClearJob clear;
-  clear.ptr[0] = out.ranges; clear.words[0] = 2 * (size_t)plan.num_tiles;
+  // (with Gaussians, the ranges kernel writes every tile's range)
+  clear.ptr[0] = n == 0 ? out.ranges : nullptr; clear.words[0] = 2 * (size_t)plan.num_tiles;
   clear.ptr[1] = err; clear.words[1] = 1;
   clear.ptr[2] = n == 0 ? reinterpret_cast<uint32_t*>(out.num_instances) : nullptr; clear.words[2] = 2;
   clear.ptr[3] = n > 0 ? sort_d : nullptr; clear.words[3] = sort_scratch_bytes(n, 32) / 4;
@@ -826,10 +849,11 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   if (e != cudaSuccess) return e;
   // 4. Stable sort by tile id; 5. tile ranges.
   radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_t, err, true, st);
-  if (plan.capacity > 0) {
-    const unsigned gr = (unsigned)((plan.capacity + 255) / 256);
+  {
+    const unsigned gr = (unsigned)((plan.num_tiles + 7) / 8);  // 8 warps per block, one per tile
     e = launch_pdl(ranges_kernel, dim3(gr), dim3(256), 0, st, (const uint32_t*)out_keys,
-                   (const int64_t*)out.num_instances, plan.capacity, reinterpret_cast<uint2*>(out.ranges));
+                   (const int64_t*)out.num_instances, plan.capacity, (int)plan.num_tiles,
+                   reinterpret_cast<uint2*>(out.ranges));
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
