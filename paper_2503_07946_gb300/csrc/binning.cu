@@ -24,8 +24,6 @@ namespace sdgs {
 namespace {
 
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;  // keys per block
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kBins = 256;
 
@@ -223,7 +221,7 @@ __device__ __forceinline__ void store_status(uint32_t* p, uint32_t v) {
 }
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 16 ? 4 : 6)
+__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 6)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* nptr,
                 int64_t n_static, int64_t cap, int shift, int width, const uint32_t* __restrict__ digit_hist,
@@ -356,11 +354,11 @@ int radix_pass_count(int bits) {
   return k;
 }
 
-// Keys per sort block for `cap` slots: the largest tile (16, 8 or 4 keys per thread) that still
+// Keys per sort block for `cap` slots: the largest tile (12, 8 or 4 keys per thread) that still
 // gives two blocks per SM, so that small sorts are not latency-bound on a few blocks.
 int sort_items(int64_t cap) {
   const int64_t want = 2 * 152;
-  if ((cap + 16 * kRadixThreads - 1) / (16 * kRadixThreads) >= want) return 16;
+  if ((cap + 12 * kRadixThreads - 1) / (12 * kRadixThreads) >= want) return 12;
   if ((cap + 8 * kRadixThreads - 1) / (8 * kRadixThreads) >= want) return 8;
   return 4;
 }
@@ -438,7 +436,7 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
   for (int p = 0; p < passes; ++p) {
     uint32_t* stp = status + (size_t)p * nblocks * kBins;
     const int shift = p * width;
-    auto* kern = items == 16 ? onesweep_kernel<16> : items == 8 ? onesweep_kernel<8> : onesweep_kernel<4>;
+    auto* kern = items == 12 ? onesweep_kernel<12> : items == 8 ? onesweep_kernel<8> : onesweep_kernel<4>;
     launch_pdl(kern, dim3((unsigned)nblocks), dim3(kRadixThreads), 0, st, keys[cur], vals[cur], keys[cur ^ 1],
                vals[cur ^ 1], nptr, n_static, cap, shift, width, hist + p * kBins, stp, tickets + p, err);
     cur ^= 1;
