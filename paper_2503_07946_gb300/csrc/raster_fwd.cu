@@ -103,23 +103,31 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
     const int cnt = min(kThreads, n - base);
     __syncthreads();
     if (!(pp.done0 && pp.done1)) {
-      // Entries past cnt are never read: the batch is padded by predication.  The stop test runs
-      // every 4 Gaussians; a stopped pixel ignores the rest (blend2 is a no-op for it).
-      for (int k0 = 0; k0 < cnt; k0 += 4) {
+      // A full batch runs as straight-line groups of 8 Gaussians with the stop test after each
+      // group; the tile's last, partial batch in groups of 4 with bound checks (entries past cnt
+      // are never read).  A stopped pixel ignores the rest (blend2 is a no-op for it).
+      auto one = [&](int k) {
+        const float2 m = s_xy[k];
+        const float4 q = s_q[k];
+        const float4 c = s_rgb[k];
+        const uint32_t pos1 = (uint32_t)(base + k) + 1u;
+        // offsets exactly as the backward forms them, so both passes take the same decisions
+        const float dx = fx - m.x;
+        blend2<kCount>(pp, q, c, dx, __fadd2_rn(fy, make_float2(-m.y, -m.y)), pos1);
+      };
+      if (cnt == kThreads) {  // a full batch: no bound checks
+        for (int k0 = 0; k0 < kThreads; k0 += 8) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = k0 + u;
-          if (k < cnt) {
-            const float2 m = s_xy[k];
-            const float4 q = s_q[k];
-            const float4 c = s_rgb[k];
-            const uint32_t pos1 = (uint32_t)(base + k) + 1u;
-            // offsets exactly as the backward forms them, so both passes take the same decisions
-            const float dx = fx - m.x;
-            blend2<kCount>(pp, q, c, dx, __fadd2_rn(fy, make_float2(-m.y, -m.y)), pos1);
-          }
+          for (int u = 0; u < 8; ++u) one(k0 + u);
+          if (pp.done0 && pp.done1) break;
         }
-        if (pp.done0 && pp.done1) break;
+      } else {
+        for (int k0 = 0; k0 < cnt; k0 += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (k0 + u < cnt) one(k0 + u);
+          if (pp.done0 && pp.done1) break;
+        }
       }
     }
   }
