@@ -38,7 +38,7 @@ FLOP_PER_EVAL = 23
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one
 # `ncu --set full` capture of render_fwd_kernel.  Set to None whenever render_fwd_kernel changes
 # until it is captured again.
-RENDER_FWD_TRAFFIC_BYTES = None
+RENDER_FWD_TRAFFIC_BYTES = 12.836864e6
 
 
 def load_peaks() -> dict:
