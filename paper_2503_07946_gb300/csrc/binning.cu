@@ -162,8 +162,9 @@ cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partia
 
 // Lanes of the warp whose digit equals this lane's (d has `width` bits; lanes with !valid are in
 // no lane's set): one ballot per digit bit.
+template <bool FULL>
 __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool valid, int width) {
-  unsigned peers = __ballot_sync(0xffffffffu, valid);
+  unsigned peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     if (b < width) {  // uniform over the warp
@@ -220,6 +221,36 @@ __device__ __forceinline__ void store_status(uint32_t* p, uint32_t v) {
   *reinterpret_cast<volatile uint32_t*>(p) = v;
 }
 
+// Loads a warp's ITEMS rows of 32 keys and ranks each key among the warp's keys with the same
+// digit (stable: earlier rows, then lower lanes, first), counting them in s_whist[warp].  FULL: the
+// whole tile is in range, so no key needs a bound check.
+template <int ITEMS, bool FULL>
+__device__ __forceinline__ void load_and_rank(const uint32_t* __restrict__ keys_in, int64_t wbase, int64_t n,
+                                              int shift, int width, uint32_t* whist, uint32_t key[ITEMS],
+                                              uint32_t rank[ITEMS]) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const uint32_t dmask = (1u << width) - 1u;
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const int64_t idx = wbase + r * 32 + lane;
+    key[r] = (FULL || idx < n) ? keys_in[idx] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const bool valid = FULL || wbase + r * 32 + lane < n;
+    const uint32_t d = (key[r] >> shift) & dmask;
+    const unsigned peers = width >= 8 ? (__match_any_sync(0xffffffffu, valid ? d : 0x100u) &
+                                         (FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid)))
+                                      : digit_peers<FULL>(d, valid, width);
+    const uint32_t before = valid ? whist[d] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) whist[d] = before + __popc(peers);
+    __syncwarp();
+    rank[r] = before + __popc(peers & lt);
+  }
+}
+
 template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 6)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
@@ -243,28 +274,12 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
   if (base >= n) return;  // so do all later tiles: nobody waits on this one
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
   const uint32_t dmask = (1u << width) - 1u;
   const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
+  const bool full = base + TILE <= n;  // uniform over the block
   uint32_t key[ITEMS], rank[ITEMS];
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    const int64_t idx = wbase + r * 32 + lane;
-    key[r] = idx < n ? keys_in[idx] : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    const bool valid = wbase + r * 32 + lane < n;
-    const uint32_t d = (key[r] >> shift) & dmask;
-    const unsigned peers = width >= 8 ? (__match_any_sync(0xffffffffu, valid ? d : 0x100u) &
-                                         __ballot_sync(0xffffffffu, valid))
-                                      : digit_peers(d, valid, width);
-    const uint32_t before = valid ? s_whist[warp][d] : 0u;
-    __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
-    __syncwarp();
-    rank[r] = before + __popc(peers & lt);
-  }
+  if (full) load_and_rank<ITEMS, true>(keys_in, wbase, n, shift, width, s_whist[warp], key, rank);
+  else load_and_rank<ITEMS, false>(keys_in, wbase, n, shift, width, s_whist[warp], key, rank);
   __syncthreads();
   {
     const int dg = threadIdx.x;
@@ -325,7 +340,7 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     const int64_t idx = wbase + r * 32 + lane;
-    if (idx < n) {
+    if (full || idx < n) {
       const uint32_t d = (key[r] >> shift) & dmask;
       const uint32_t pos = s_dstart[d] + s_whist[warp][d] + rank[r];
       s_keys[pos] = key[r];
@@ -333,13 +348,25 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     }
   }
   __syncthreads();
-  const int cnt = (int)((n - base) < TILE ? (n - base) : TILE);
-  for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
-    const uint32_t k = s_keys[i];
-    const uint32_t d = (k >> shift) & dmask;
-    const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
-    keys_out[g] = k;
-    vals_out[g] = s_vals[i];
+  if (full) {
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int i = r * kRadixThreads + threadIdx.x;
+      const uint32_t k = s_keys[i];
+      const uint32_t d = (k >> shift) & dmask;
+      const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
+      keys_out[g] = k;
+      vals_out[g] = s_vals[i];
+    }
+  } else {
+    const int cnt = (int)(n - base);
+    for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+      const uint32_t k = s_keys[i];
+      const uint32_t d = (k >> shift) & dmask;
+      const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
+      keys_out[g] = k;
+      vals_out[g] = s_vals[i];
+    }
   }
 }
 
