@@ -109,10 +109,6 @@ __device__ __forceinline__ bool unblend2(BwdPair& px, const float4& q, const flo
   return h0 || h1;
 }
 
-// Back-to-front replay per 16x16 tile, 64 threads with four pixels each: column x, rows r, r + 8
-// (pair A) and r + 4, r + 12 (pair B).  The tile's list is staged from the back in batches of 128;
-// each Gaussian's sums are added over the thread's pixels, then over the warp, then over the
-// block's warps in shared memory, and the batch ends with one set of global atomics per Gaussian.
 constexpr int kBwdThreads = kTilePixels / 4;
 constexpr int kBatch = 128;
 
@@ -143,6 +139,10 @@ __device__ __forceinline__ void load_pair(const RasterBwdArgs& a, int px, int py
   pp.last1 = last[1];
 }
 
+// Back-to-front replay per 16x16 tile, 64 threads with four pixels each: column x, rows r, r + 8
+// (pair A) and r + 4, r + 12 (pair B).  The tile's list is staged from the back in batches of 128;
+// each Gaussian's sums are added over the thread's pixels, then over the warp, then over the
+// block's warps in shared memory, and the batch ends with one set of global atomics per Gaussian.
 __global__ void __launch_bounds__(kBwdThreads, 16) raster_bwd_kernel(const RasterBwdArgs a) {
   griddep_wait();
   __shared__ float2 s_xy[kBatch];
