@@ -355,12 +355,9 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
       dY[(4 * q + 1) / 3] += v.y * dc[(4 * q + 1) % 3];
       dY[(4 * q + 2) / 3] += v.z * dc[(4 * q + 2) % 3];
       dY[(4 * q + 3) / 3] += v.w * dc[(4 * q + 3) % 3];
-      float4 d = dshp[q];
-      d.x += Y[(4 * q) / 3] * dc[(4 * q) % 3];
-      d.y += Y[(4 * q + 1) / 3] * dc[(4 * q + 1) % 3];
-      d.z += Y[(4 * q + 2) / 3] * dc[(4 * q + 2) % 3];
-      d.w += Y[(4 * q + 3) / 3] * dc[(4 * q + 3) % 3];
-      dshp[q] = d;
+      atomicAdd(dshp + q, make_float4(Y[(4 * q) / 3] * dc[(4 * q) % 3], Y[(4 * q + 1) / 3] * dc[(4 * q + 1) % 3],
+                                      Y[(4 * q + 2) / 3] * dc[(4 * q + 2) % 3],
+                                      Y[(4 * q + 3) / 3] * dc[(4 * q + 3) % 3]));
     }
     const float xx = x * x, yy = y * y, zz = z * z;
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -500,7 +497,7 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
   // ---- alpha_cond = alpha exp(e_t) exp(e_d) ----
   {
     const float ft = expf(s.e_t), fd = expf(s.e_d);
-    a.dopacity[i] += dalc * ft * fd;
+    atomicAdd(a.dopacity + i, dalc * ft * fd);
     const float de_ = dalc * alpha_c;  // d alpha_c / d e_t = d alpha_c / d e_d = alpha_c
     const float e0 = q.t - m[3];
     // e_t = -1/2 lambda_t e0^2 / S_t
@@ -545,13 +542,9 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
 
   float4* dLp = reinterpret_cast<float4*>(a.dL28 + 28 * i);
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    float4 d = dLp[q];
-    d.x += dLg[4 * q]; d.y += dLg[4 * q + 1]; d.z += dLg[4 * q + 2]; d.w += dLg[4 * q + 3];
-    dLp[q] = d;
-  }
+  for (int q = 0; q < 7; ++q) atomicAdd(dLp + q, make_float4(dLg[4 * q], dLg[4 * q + 1], dLg[4 * q + 2], dLg[4 * q + 3]));
 #pragma unroll
-  for (int k = 0; k < 7; ++k) a.dmean7[7 * i + k] += dm[k];
+  for (int k = 0; k < 7; ++k) atomicAdd(a.dmean7 + 7 * i + k, dm[k]);
 }
 
 }  // namespace
