@@ -166,6 +166,19 @@ def render_image(mean7, L28, opacity, sh, view: sdgs.View, lambda_t, lambda_d, r
     return Render7DGS.apply(mean7, L28, opacity, sh, lam, view, renderer, dir_mode)
 
 
+_AGR_UNUSED: dict = {}
+
+
+def _agr_unused_arrays(n: int, device) -> tuple[torch.Tensor, torch.Tensor]:
+    """Opacity and SH arrays for the scene struct of the refinement calls, which read neither
+    (the ABI still wants valid arrays of the scene's size); allocated once per (n, device)."""
+    key = (n, str(device))
+    if key not in _AGR_UNUSED:
+        _AGR_UNUSED.clear()
+        _AGR_UNUSED[key] = (torch.zeros(n, device=device), torch.zeros(n, 16, 3, device=device))
+    return _AGR_UNUSED[key]
+
+
 class AGRRefine(torch.autograd.Function):
     """(mean7^, L28^) = adaptive refinement of (mean7, L28) at time t by the four MLPs (w1, b1, w2,
     b2); backward is the CUDA adjoint (input and weight gradients)."""
@@ -175,8 +188,7 @@ class AGRRefine(torch.autograd.Function):
         w = dict(w1=w1.contiguous(), b1=b1.contiguous(), w2=w2.contiguous(), b2=b2.contiguous())
         m7, l28 = mean7.contiguous(), L28.contiguous()
         n = m7.shape[0]
-        opacity = torch.zeros(n, device=m7.device)
-        sh = torch.zeros(n, 16, 3, device=m7.device)
+        opacity, sh = _agr_unused_arrays(n, m7.device)
         scene = sdgs.scene_struct(dict(mean7=m7, L28=l28, opacity=opacity, sh=sh), 0.0, 0.0)
         m_out, l_out = torch.empty_like(m7), torch.empty_like(l28)
         sdgs.agr_refine(scene, w, t, m_out, l_out)
@@ -189,8 +201,7 @@ class AGRRefine(torch.autograd.Function):
         m7, l28, w1, b1, w2, b2 = ctx.saved_tensors
         n = m7.shape[0]
         w = dict(w1=w1, b1=b1, w2=w2, b2=b2)
-        opacity = torch.zeros(n, device=m7.device)
-        sh = torch.zeros(n, 16, 3, device=m7.device)
+        opacity, sh = _agr_unused_arrays(n, m7.device)
         scene = sdgs.scene_struct(dict(mean7=m7, L28=l28, opacity=opacity, sh=sh), 0.0, 0.0)
         d_m = torch.zeros_like(m7) if d_m is None else d_m.contiguous()
         d_l = torch.zeros_like(l28) if d_l is None else d_l.contiguous()
