@@ -158,16 +158,56 @@ __global__ void __launch_bounds__(kAgrThreads) agr_refine_kernel(const float* __
 constexpr int kO1 = kUnits * (kX + 1);
 constexpr int kO2 = kOut * (kHidden + 1);
 constexpr int kPartial = kO1 + kO2;
-constexpr int kAcc1 = kO1 / kAgrThreads;                          // 16 per thread
-constexpr int kAcc2 = (kO2 + kAgrThreads - 1) / kAgrThreads;      // 18 per thread
+constexpr int kOutPad = 36;  // dout rows padded to whole float4
 
 struct AgrBwdShared {
   AgrWeights W;
-  float x[kAgrThreads][kX + 1];      // the tile's x, then 1 (live) for the bias column
-  float dout[kAgrThreads][kOut];     // gradients w.r.t. the 35 residuals
-  float h[kAgrThreads][kHidden + 1]; // this MLP's hidden activations, then 1 (live)
-  float dz[kAgrThreads][kHidden + 1];
+  alignas(16) float x[kAgrThreads][kX + 1];      // the tile's x, then 1 (live) for the bias column
+  alignas(16) float dout[kAgrThreads][kOutPad];  // gradients w.r.t. the 35 residuals, then 0
+  float h[kAgrThreads][kHidden + 1];             // this MLP's hidden activations and dz (odd
+  float dz[kAgrThreads][kHidden + 1];            // stride: rows written per thread conflict-free)
 };
+static_assert(sizeof(float) * kAgrThreads * (kHidden + 1) >= sizeof(float) * kPartial,
+              "the final combine stages one half's sums in h");
+
+// Weight-gradient sums of thread (j, half): hidden unit j of every MLP over the Gaussians of one
+// half of each tile, kept in registers across tiles.  w1[m][c]: dW1 row m * 64 + j (7 x-columns,
+// then the bias); w2[r]: dW2 column j of output row r; b2: the bias of output row tid % 35 for the
+// 70 threads that own one.
+struct AgrSums {
+  float w1[kMlps][kX + 1];
+  float w2[kOut];
+  float b2;
+};
+
+// Adds MLP M's terms of the half's 64 Gaussians: x and dout are read as broadcast float4, dz and
+// h once per Gaussian.
+template <int M>
+__device__ __forceinline__ void agr_weight_sums(const AgrBwdShared& S, int j, int half, AgrSums& acc) {
+  constexpr int rb = row_begin(M), re = row_end(M);
+  constexpr int q0 = rb / 4, q1 = (re + 3) / 4;  // float4 chunks of dout covering the rows
+  const int g0 = half * (kAgrThreads / 2);
+#pragma unroll 4
+  for (int g = g0; g < g0 + kAgrThreads / 2; ++g) {
+    const float dzj = S.dz[g][j];
+    const float4 xa = *reinterpret_cast<const float4*>(&S.x[g][0]);
+    const float4 xb = *reinterpret_cast<const float4*>(&S.x[g][4]);
+    float* a1 = acc.w1[M];
+    a1[0] += dzj * xa.x; a1[1] += dzj * xa.y; a1[2] += dzj * xa.z; a1[3] += dzj * xa.w;
+    a1[4] += dzj * xb.x; a1[5] += dzj * xb.y; a1[6] += dzj * xb.z; a1[7] += dzj * xb.w;
+    const float hj = S.h[g][j];
+#pragma unroll
+    for (int q = q0; q < q1; ++q) {
+      const float4 d = *reinterpret_cast<const float4*>(&S.dout[g][4 * q]);
+      const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 4 * q + e;
+        if (r >= rb && r < re) acc.w2[r] += dv[e] * hj;
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kAgrThreads) agr_bwd_kernel(
     const float* __restrict__ mean7, int64_t n, sdgs_agr agr, float t, const float* __restrict__ dmean7_hat,
@@ -177,16 +217,20 @@ __global__ void __launch_bounds__(kAgrThreads) agr_bwd_kernel(
   AgrBwdShared& S = *reinterpret_cast<AgrBwdShared*>(s_dyn);
   AgrWeights& W = S.W;
   float (*s_x)[kX + 1] = S.x;
-  float (*s_dout)[kOut] = S.dout;
+  float (*s_dout)[kOutPad] = S.dout;
   float (*s_h)[kHidden + 1] = S.h;
   float (*s_dz)[kHidden + 1] = S.dz;
   load_weights(W, agr, t);
   const int tid = threadIdx.x;
-  float acc1[kAcc1], acc2[kAcc2];
+  const int hj = tid & (kHidden - 1), half = tid / kHidden;  // this thread's weight-gradient sums
+  AgrSums acc;
 #pragma unroll
-  for (int k = 0; k < kAcc1; ++k) acc1[k] = 0.f;
+  for (int m = 0; m < kMlps; ++m)
 #pragma unroll
-  for (int k = 0; k < kAcc2; ++k) acc2[k] = 0.f;
+    for (int c = 0; c <= kX; ++c) acc.w1[m][c] = 0.f;
+#pragma unroll
+  for (int r = 0; r < kOut; ++r) acc.w2[r] = 0.f;
+  acc.b2 = 0.f;
 
   const int64_t tiles = (n + kAgrThreads - 1) / kAgrThreads;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -206,6 +250,13 @@ __global__ void __launch_bounds__(kAgrThreads) agr_bwd_kernel(
     for (int r = kX; r < kOut; ++r) dout[r] = live ? dL28_hat[28 * i + r - kX] : 0.f;
 #pragma unroll
     for (int r = 0; r < kOut; ++r) s_dout[tid][r] = dout[r];
+    s_dout[tid][kOut] = 0.f;
+    __syncthreads();  // the tile's x and dout are in
+    if (tid < 2 * kOut) {  // bias of output row tid % 35 over the half's Gaussians (dout is 0 past the end)
+      const int r = tid % kOut, g0 = (tid / kOut) * (kAgrThreads / 2);
+#pragma unroll 8
+      for (int g = g0; g < g0 + kAgrThreads / 2; ++g) acc.b2 += s_dout[g][r];
+    }
 #pragma unroll
     for (int m = 0; m < kMlps; ++m) {
       __syncthreads();  // the previous MLP's sums are done with s_h / s_dz
@@ -224,28 +275,11 @@ __global__ void __launch_bounds__(kAgrThreads) agr_bwd_kernel(
       }
       s_h[tid][kHidden] = live ? 1.f : 0.f;
       __syncthreads();
-      // this MLP's weight-gradient sums over the tile's Gaussians
-#pragma unroll
-      for (int k = 0; k < kAcc1; ++k) {
-        const int o = tid + k * kAgrThreads;
-        if (o / ((kX + 1) * kHidden) != m) continue;
-        const int j = (o / (kX + 1)) % kHidden, c = o % (kX + 1);
-        float s = 0.f;
-#pragma unroll 8
-        for (int g = 0; g < kAgrThreads; ++g) s += s_dz[g][j] * s_x[g][c];
-        acc1[k] += s;
-      }
-#pragma unroll
-      for (int k = 0; k < kAcc2; ++k) {
-        const int o = tid + k * kAgrThreads;
-        if (o >= kO2) continue;
-        const int r = o / (kHidden + 1), j = o % (kHidden + 1);
-        if (r < row_begin(m) || r >= row_end(m)) continue;
-        float s = 0.f;
-#pragma unroll 8
-        for (int g = 0; g < kAgrThreads; ++g) s += s_dout[g][r] * s_h[g][j];
-        acc2[k] += s;
-      }
+      // this MLP's weight-gradient terms of the tile's Gaussians
+      if (m == 0) agr_weight_sums<0>(S, hj, half, acc);
+      if (m == 1) agr_weight_sums<1>(S, hj, half, acc);
+      if (m == 2) agr_weight_sums<2>(S, hj, half, acc);
+      if (m == 3) agr_weight_sums<3>(S, hj, half, acc);
     }
     if (live) {
 #pragma unroll
@@ -255,13 +289,37 @@ __global__ void __launch_bounds__(kAgrThreads) agr_bwd_kernel(
     }
     __syncthreads();  // s_x / s_dout are rewritten by the next tile
   }
+  // the block's sums: the second half's staged in shared memory, added to the first half's
+  float* stage = &S.h[0][0];
   float* mine = partial + (size_t)blockIdx.x * kPartial;
+  __syncthreads();
+  if (half == 1) {
 #pragma unroll
-  for (int k = 0; k < kAcc1; ++k) mine[tid + k * kAgrThreads] = acc1[k];
+    for (int m = 0; m < kMlps; ++m)
 #pragma unroll
-  for (int k = 0; k < kAcc2; ++k) {
-    const int o = tid + k * kAgrThreads;
-    if (o < kO2) mine[kO1 + o] = acc2[k];
+      for (int c = 0; c <= kX; ++c) stage[(m * kHidden + hj) * (kX + 1) + c] = acc.w1[m][c];
+#pragma unroll
+    for (int r = 0; r < kOut; ++r) stage[kO1 + r * (kHidden + 1) + hj] = acc.w2[r];
+  }
+  if (tid >= kOut && tid < 2 * kOut) stage[kO1 + (tid - kOut) * (kHidden + 1) + kHidden] = acc.b2;
+  __syncthreads();
+  if (half == 0) {
+#pragma unroll
+    for (int m = 0; m < kMlps; ++m)
+#pragma unroll
+      for (int c = 0; c <= kX; ++c) {
+        const int o = (m * kHidden + hj) * (kX + 1) + c;
+        mine[o] = acc.w1[m][c] + stage[o];
+      }
+#pragma unroll
+    for (int r = 0; r < kOut; ++r) {
+      const int o = kO1 + r * (kHidden + 1) + hj;
+      mine[o] = acc.w2[r] + stage[o];
+    }
+  }
+  if (tid < kOut) {
+    const int o = kO1 + tid * (kHidden + 1) + kHidden;
+    mine[o] = acc.b2 + stage[o];
   }
 }
 
