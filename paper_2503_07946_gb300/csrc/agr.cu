@@ -99,6 +99,10 @@ __device__ __forceinline__ float fwd_hidden(const AgrFwdWeights& F, int u, const
   return fmaxf(z, 0.f);
 }
 
+__device__ __forceinline__ void agr_refine_one(const AgrFwdWeights& F, const float* __restrict__ mean7,
+                                               const float* __restrict__ L28, int64_t i,
+                                               float* __restrict__ mean7_out, float* __restrict__ L28_out);
+
 __global__ void __launch_bounds__(kAgrThreads) agr_refine_kernel(const float* __restrict__ mean7,
                                                                  const float* __restrict__ L28, int64_t n,
                                                                  sdgs_agr agr, float t,
@@ -106,9 +110,15 @@ __global__ void __launch_bounds__(kAgrThreads) agr_refine_kernel(const float* __
                                                                  float* __restrict__ L28_out) {
   __shared__ AgrWeights W;
   __shared__ AgrFwdWeights F;
-  load_fwd_weights(F, W, agr, t);
-  const int64_t i = (int64_t)blockIdx.x * kAgrThreads + threadIdx.x;
-  if (i >= n) return;
+  load_fwd_weights(F, W, agr, t);  // once per block: the grid strides over the Gaussians
+  for (int64_t i = (int64_t)blockIdx.x * kAgrThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kAgrThreads)
+    agr_refine_one(F, mean7, L28, i, mean7_out, L28_out);
+}
+
+__device__ __forceinline__ void agr_refine_one(const AgrFwdWeights& F, const float* __restrict__ mean7,
+                                               const float* __restrict__ L28, int64_t i,
+                                               float* __restrict__ mean7_out, float* __restrict__ L28_out) {
   float x[kX];
 #pragma unroll
   for (int c = 0; c < kX; ++c) x[c] = mean7[kX * i + c];
@@ -361,7 +371,8 @@ size_t agr_bwd_workspace_bytes(int64_t n) { return sizeof(float) * (size_t)kPart
 cudaError_t launch_agr_refine(const sdgs_scene& s, const sdgs_agr& a, float t, float* mean7_out, float* L28_out,
                               cudaStream_t st) {
   if (s.n == 0) return cudaSuccess;
-  agr_refine_kernel<<<(unsigned)((s.n + kAgrThreads - 1) / kAgrThreads), kAgrThreads, 0, st>>>(
+  const int64_t tiles = (s.n + kAgrThreads - 1) / kAgrThreads;
+  agr_refine_kernel<<<(unsigned)std::min<int64_t>(tiles, 4 * 152), kAgrThreads, 0, st>>>(
       s.mean7, s.L28, s.n, a, t, mean7_out, L28_out);
   return cudaGetLastError();
 }
