@@ -199,6 +199,27 @@ def cpu_baseline(scene, cam) -> dict:
                        % (est["t_gauss"], est["t_tiles"]))}
 
 
+def replica_order(rank: int, n_cams: int, count: int) -> list[int]:
+    """Cameras of a rank's frames: each rank starts at its own offset of the orbit and renders the
+    same number of frames at every N (replicas: per-rank work fixed, no data exchanged)."""
+    return [(rank * 37 + i) % n_cams for i in range(count)]
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's value: the job's throughput is every rank's work over the slowest rank's
+    time.  A collective over the default process group when world > 1."""
+    if world <= 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_s(world: int, pixels_per_step: int, ms_per_step: float) -> float:
+    """Whole-job Mpix/s: every rank renders pixels_per_step per step in ms_per_step (its slowest)."""
+    return world * pixels_per_step / (ms_per_step * 1e-3) / 1e6
+
+
 def run_ours(args, rank: int, world: int):
     from paper_2503_07946_gb300 import render as prender
     from paper_2503_07946_gb300 import sdgs
@@ -213,7 +234,7 @@ def run_ours(args, rank: int, world: int):
     t_scene = prender.scene_to_device(scene)
     st = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
     steps, warm = args.steps, args.warmup
-    order = [(rank * 37 + i) % len(cams) for i in range(steps + warm)]
+    order = replica_order(rank, len(cams), steps + warm)
     views = [sdgs.view_struct(cams[i]) for i in order]
 
     # size the instance lists once from the frames this run renders
@@ -279,18 +300,14 @@ def run_ours(args, rank: int, world: int):
         sdgs.render_fwd(r.proj, r.bins, v, r.image, r.final_T, r.n_contrib, n_eval, stream)
     torch.cuda.synchronize()
     step_ms = phase.sum(1)
-    ms = float(step_ms.mean())
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(step_ms.mean()), world, dev)
     evals = int(n_eval.item())
     k_inst = int(r.bins.num_instances.item())
     visible = int(((r.proj.rect[:, 2] > r.proj.rect[:, 0]) & (r.proj.rect[:, 3] > r.proj.rect[:, 1])).sum())
 
     if args.frames_only:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": world * W * H / (ms * 1e-3) / 1e6, "unit": "Mpix/s",
+            print(json.dumps({"metric": METRIC, "value": job_mpix_s(world, W * H, ms), "unit": "Mpix/s",
                               "ms_per_step": ms, "frames_only": True,
                               "phases_ms": {"slice_project": float(phase[:, 0].mean()),
                                             "bin_sort": float(phase[:, 1].mean()),
@@ -314,7 +331,7 @@ def run_ours(args, rank: int, world: int):
         re_.forward(st, views[warm + i])
         host_img.copy_(re_.image, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     re_.check_deferred()
     assert re_.overflowed_frames == overflowed, "a timed end-to-end frame exceeded the bins' capacity"
     del re_
@@ -333,7 +350,7 @@ def run_ours(args, rank: int, world: int):
     serving = None if args.no_serving else serving_bench(dev)
 
     pix = W * H
-    value = world * pix / (ms * 1e-3) / 1e6
+    value = job_mpix_s(world, pix, ms)
     raster_ms = float(phase[:, 2].mean())
     achieved_tflops = (evals / steps) * FLOP_PER_EVAL / (raster_ms * 1e-3) / 1e12
     clocks = clk.summary()
@@ -358,7 +375,7 @@ def run_ours(args, rank: int, world: int):
         "agr_frames": agr,
         "densify_stats": dens,
         "serving": serving,
-        "e2e": {"value": world * pix / e2e_s / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
+        "e2e": {"value": job_mpix_s(world, pix, e2e_s * 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
                 "d2h_bytes_per_step": pix * 3 * 4 + 8},
         "gpu_launches": steps * launches_per_frame(scene.n, r.bins.capacity, W, H),
         "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
