@@ -2,13 +2,16 @@
 
 The paper blends the projected Gaussians in depth order by opacity, with the 3DGS differentiable
 rasteriser (Sec. 4.4).  The rules, fixed here as readings of that rasteriser:
-  * a Gaussian is considered at a pixel iff the pixel's 16x16 tile lies in its tile rectangle;
-    candidates are visited in ascending (depth, id) order;
+  * a Gaussian is considered at a pixel iff the pixel's 16x16 tile lies in its tile rectangle
+    (callers build the candidate lists; `render.composite_all` does so from the rectangles alone
+    unless asked to apply the binning's reachability rule as well); candidates are visited in
+    ascending (depth, id) order;
   * power = -1/2 (a dx^2 + c dy^2) - b dx dy with (dx, dy) = pixel centre - mean, conic [[a,b],[b,c]];
   * alpha_i = min(0.99, alpha_cond exp(power)); skip when power > 0 or alpha_i < 1/255;
   * T_next = T (1 - alpha_i); if T_next < 1e-4 stop *without* adding this Gaussian;
   * C += c_i alpha_i T; T = T_next; out = C + T_final bg.
-  * n_contrib = 1 + position (in the tile list) of the last Gaussian added, 0 if none.
+  * n_contrib = 1 + position (in the tile list) of the last Gaussian added, 0 if none; last_id is
+    that Gaussian's id (-1 if none), which does not depend on which skipped candidates a list holds.
 
 `composite_tile` evaluates all candidates of one tile at once: the transmittance in front of
 candidate k is the running product of (1 - alpha_j) over the candidates j < k that were not
@@ -31,7 +34,8 @@ def composite_tile(pix: torch.Tensor, g: torch.Tensor, mean2d: torch.Tensor, con
                    depth: torch.Tensor | None = None) -> dict:
     """pix [P, 2] pixel centres; g [n] candidate ids in (depth, id) order.
 
-    Returns colour [P, 3], final_T [P], n_contrib [P] (int64) and margin: a dict of [P] tensors
+    Returns colour [P, 3], final_T [P], n_contrib [P] (int64), last_id [P] (int64, -1 if no
+    Gaussian was added) and margin: a dict of [P] tensors
     with the smallest relative distance of the pixel's decisions to their thresholds (alpha vs
     1/255, T vs 1e-4, relative depth gap of neighbouring candidates up to the stop).
     """
@@ -42,6 +46,7 @@ def composite_tile(pix: torch.Tensor, g: torch.Tensor, mean2d: torch.Tensor, con
         inf = torch.full((P,), float("inf"), dtype=dtype)
         return dict(color=bg.expand(P, 3).clone(), final_T=torch.ones(P, dtype=dtype),
                     n_contrib=torch.zeros(P, dtype=torch.int64),
+                    last_id=torch.full((P,), -1, dtype=torch.int64),
                     margin=dict(alpha=inf, T=inf.clone(), depth=inf.clone()))
     m = mean2d[g]
     q = conic[g]
@@ -83,7 +88,9 @@ def composite_tile(pix: torch.Tensor, g: torch.Tensor, mean2d: torch.Tensor, con
     T_stop = torch.gather(T_excl, 0, last[None, :])[0]
     final_T = torch.where(has_stop, T_stop, T_incl[-1])
     color = color + final_T[:, None] * bg[None, :]
-    return dict(color=color, final_T=final_T, n_contrib=n_contrib, margin=margin)
+    last_id = torch.where(n_contrib > 0, g.to(torch.int64)[torch.clamp(n_contrib - 1, min=0)],
+                          torch.full_like(n_contrib, -1))
+    return dict(color=color, final_T=final_T, n_contrib=n_contrib, last_id=last_id, margin=margin)
 
 
 def composite_pixel_loop(px: float, py: float, g, mean2d, conic, alpha_cond, rgb, bg):

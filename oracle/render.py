@@ -70,26 +70,33 @@ def cull_inputs(mean2d, conic, alpha):
     return (f(mean2d), f(conic), f(alpha))
 
 
-def composite_all(mean2d, conic, alpha, rgb, depth, rect, cam, bg, tiles=None) -> dict:
-    """Composite every tile (or the listed ones) of the image."""
+def composite_all(mean2d, conic, alpha, rgb, depth, rect, cam, bg, tiles=None, reach: bool = False) -> dict:
+    """Composite every tile (or the listed ones) of the image.
+
+    Each tile's candidates are the Gaussians whose tile rectangle contains it (Sec. 4.4, the 3DGS
+    blending rule).  With reach=True they are further restricted to the tiles the binning's
+    reachability rule keeps, which can only drop candidates that no pixel of the tile takes
+    (alpha < 1/255 everywhere): the image is the same, but list positions (n_contrib) then match
+    the binned lists.
+    """
     num_tiles = cam.tiles_x * cam.tiles_y
     lists = binning.tile_lists(depth.detach().numpy(), rect.numpy(), cam.tiles_x, num_tiles,
-                               cull=cull_inputs(mean2d, conic, alpha))
+                               cull=cull_inputs(mean2d, conic, alpha) if reach else None)
     H, W = cam.height, cam.width
-    colors, Ts, ncs, margins, rcs = [], [], [], [], []
+    colors, Ts, ncs, lasts, margins, rcs = [], [], [], [], [], []
     for tile in (range(num_tiles) if tiles is None else tiles):
         pix, rc = pixel_centres(cam, tile)
         g = torch.as_tensor(lists[tile], dtype=torch.int64)
         r = composite.composite_tile(pix, g, mean2d, conic, alpha, rgb, bg, depth=depth.detach())
         colors.append(r["color"]); Ts.append(r["final_T"]); ncs.append(r["n_contrib"])
-        margins.append(r["margin"]); rcs.append(rc)
+        lasts.append(r["last_id"]); margins.append(r["margin"]); rcs.append(rc)
     rc = torch.cat(rcs)
     flat = rc[:, 0] * W + rc[:, 1]
     color = torch.cat(colors)
     image = torch.zeros(H * W, 3, dtype=color.dtype).index_add(0, flat, color).reshape(H, W, 3)
     out = dict(image=image)
     with torch.no_grad():
-        for name, vals, fill in (("final_T", Ts, 1.0), ("n_contrib", ncs, 0),
+        for name, vals, fill in (("final_T", Ts, 1.0), ("n_contrib", ncs, 0), ("last_id", lasts, -1),
                                  ("margin_alpha", [m["alpha"] for m in margins], float("inf")),
                                  ("margin_T", [m["T"] for m in margins], float("inf")),
                                  ("margin_depth", [m["depth"] for m in margins], float("inf"))):
@@ -103,37 +110,40 @@ def composite_all(mean2d, conic, alpha, rgb, depth, rect, cam, bg, tiles=None) -
     return out
 
 
-def render(scene, cam, tiles=None, params: dict | None = None) -> dict:
+def render(scene, cam, tiles=None, params: dict | None = None, reach: bool = False) -> dict:
     """Full-image (or listed-tile) render of a scene; returns image [H, W, 3] and per-Gaussian data."""
     p = params if params is not None else params_from_scene(scene)
     g = gaussians(p, cam, scene.lambda_t, scene.lambda_d, scene.dir_mode)
     bg = torch.as_tensor(cam.bg, dtype=F64)
     out = composite_all(g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], g["depth"], g["rect"],
-                        cam, bg, tiles)
+                        cam, bg, tiles, reach)
     out["g"] = g
     return out
 
 
-def render_pixels(g: dict, cam, pixels: np.ndarray) -> dict:
-    """Colour, final_T, n_contrib and margin of listed pixels [P, 2] (row, col) from per-Gaussian data.
+def render_pixels(g: dict, cam, pixels: np.ndarray, reach: bool = False) -> dict:
+    """Colour, final_T, n_contrib, last contributor id and margins of listed pixels [P, 2] (row,
+    col) from per-Gaussian data.
 
     Candidate lists are built per tile from rectangle containment over all Gaussians, so this
-    scales to full-size scenes for a sample of pixels.
+    scales to full-size scenes for a sample of pixels; reach=True restricts them as in
+    composite_all.
     """
     bg = torch.as_tensor(cam.bg, dtype=F64)
     pixels = np.asarray(pixels, dtype=np.int64)
     tiles = (pixels[:, 0] // TILE) * cam.tiles_x + pixels[:, 1] // TILE
     rect = g["rect"]
     depth = g["depth"].detach()
-    keys = ("color", "final_T", "n_contrib", "margin_alpha", "margin_T", "margin_depth")
+    keys = ("color", "final_T", "n_contrib", "last_id", "margin_alpha", "margin_T", "margin_depth")
     res = {k: [None] * len(pixels) for k in keys}
     for tile in np.unique(tiles):
         sel = np.nonzero(tiles == tile)[0]
         tx, ty = int(tile % cam.tiles_x), int(tile // cam.tiles_x)
         inside = (rect[:, 0] <= tx) & (tx < rect[:, 2]) & (rect[:, 1] <= ty) & (ty < rect[:, 3])
         ids = torch.nonzero(inside).reshape(-1)
-        m2, co, al = cull_inputs(g["mean2d"][ids], g["conic"][ids], g["alpha_cond"][ids])
-        ids = ids[torch.as_tensor(binning.tile_reachable(m2, co, al, tx, ty))]
+        if reach:
+            m2, co, al = cull_inputs(g["mean2d"][ids], g["conic"][ids], g["alpha_cond"][ids])
+            ids = ids[torch.as_tensor(binning.tile_reachable(m2, co, al, tx, ty))]
         order = np.lexsort((ids.numpy(), depth[ids].numpy()))
         cand = ids[torch.as_tensor(order, dtype=torch.int64)]
         pix = torch.as_tensor(pixels[sel][:, ::-1].copy(), dtype=F64) + 0.5
@@ -147,7 +157,7 @@ def render_pixels(g: dict, cam, pixels: np.ndarray) -> dict:
     return {k: torch.stack(v) for k, v in res.items()}
 
 
-def render_projected(rec: dict, width: int, height: int, bg, tiles=None) -> dict:
+def render_projected(rec: dict, width: int, height: int, bg, tiles=None, reach: bool = False) -> dict:
     """Composite given screen-space records (float32 inputs evaluated in float64).
 
     rec: mean2d [N, 2], conic [N, 3], opacity [N], rgb [N, 3], depth [N] (float32), rect [N, 4].
@@ -161,7 +171,7 @@ def render_projected(rec: dict, width: int, height: int, bg, tiles=None) -> dict
     t = lambda k: torch.as_tensor(np.asarray(rec[k], dtype=np.float32).astype(np.float64))
     rect = torch.as_tensor(np.asarray(rec["rect"], dtype=np.int64))
     return composite_all(t("mean2d"), t("conic"), t("opacity"), t("rgb"), t("depth"), rect, cam,
-                         torch.as_tensor(bg, dtype=F64), tiles)
+                         torch.as_tensor(bg, dtype=F64), tiles, reach)
 
 
 def refined_params(scene, agr_weights: dict | None, t, requires_grad: bool = False):

@@ -79,6 +79,62 @@ def pixel_ok(margin_alpha, margin_T, margin_depth=None, depth_rel=PIX_DEPTH):
     return ok
 
 
+def last_ids(n_contrib: np.ndarray, point_list: np.ndarray, ranges: np.ndarray, tiles_x: int,
+             rows=None, cols=None) -> np.ndarray:
+    """Id of the last Gaussian each pixel took (-1 if none), from n_contrib and its tile's list.
+
+    Unlike n_contrib (a list position) this does not depend on which skipped candidates a tile
+    list holds, so it compares with the oracle's rectangle lists.  rows / cols select pixels of a
+    full image; by default n_contrib is the whole image [H, W].
+    """
+    nc = np.asarray(n_contrib, np.int64)
+    if rows is None:
+        rows, cols = np.meshgrid(np.arange(nc.shape[0]), np.arange(nc.shape[1]), indexing="ij")
+    else:
+        nc = nc[rows, cols]
+    tile = (np.asarray(rows) // 16) * tiles_x + np.asarray(cols) // 16
+    pl = np.asarray(point_list).view(np.uint32).astype(np.int64)
+    pos = np.asarray(ranges, np.int64)[tile, 0] + nc - 1
+    return np.where(nc > 0, pl[np.clip(pos, 0, max(len(pl) - 1, 0))], -1)
+
+
+def dropped_pair_alpha(g: dict, cam, tiles, lists: dict, exclude=()) -> tuple[float, int]:
+    """Brute force over the (tile, Gaussian) pairs that the rectangle rule gives but a GPU tile
+    list leaves out: the largest alpha_cond exp(power) over the 16 x 16 pixel centres of the tile,
+    in float64 from the oracle's record.  Below 1/255 means every pixel would skip the Gaussian.
+
+    lists: tile -> GPU Gaussian ids; Gaussians in `exclude` (their rectangles differ between the
+    two sides) are left out.  Also asserts every listed Gaussian's oracle rectangle holds the tile.
+    Returns (largest alpha, number of pairs checked)."""
+    rect = g["rect"].numpy()
+    vis = g["visible"].numpy()
+    m2 = g["mean2d"].detach().numpy()
+    co = g["conic"].detach().numpy()
+    al = g["alpha_cond"].detach().numpy()
+    excl = np.zeros(len(rect), bool)
+    excl[np.asarray(list(exclude), np.int64)] = True
+    worst, pairs = 0.0, 0
+    for tile in tiles:
+        tx, ty = tile % cam.tiles_x, tile // cam.tiles_x
+        inside = vis & (rect[:, 0] <= tx) & (tx < rect[:, 2]) & (rect[:, 1] <= ty) & (ty < rect[:, 3])
+        got = np.asarray(lists[tile], np.int64)
+        got = got[~excl[got]]
+        assert inside[got].all(), (tile, got[~inside[got]])
+        miss = np.setdiff1d(np.nonzero(inside & ~excl)[0], got)
+        if len(miss) == 0:
+            continue
+        px, py = np.meshgrid(np.arange(16) + 0.5 + 16 * tx, np.arange(16) + 0.5 + 16 * ty)
+        px, py = px.reshape(1, -1), py.reshape(1, -1)
+        for c0 in range(0, len(miss), 4096):
+            m = miss[c0:c0 + 4096]
+            dx, dy = px - m2[m, 0:1], py - m2[m, 1:2]
+            power = -0.5 * (co[m, 0:1] * dx * dx + co[m, 2:3] * dy * dy) - co[m, 1:2] * dx * dy
+            a = al[m, None] * np.exp(np.minimum(power, 0.0))
+            worst = max(worst, float(a.max()))
+        pairs += len(miss)
+    return worst, pairs
+
+
 def assert_ranges_equal(got: np.ndarray, want: np.ndarray):
     """Tile ranges: counts everywhere, starts of non-empty tiles (an empty range may sit anywhere)."""
     got, want = np.asarray(got, np.int64), np.asarray(want, np.int64)

@@ -129,32 +129,15 @@ def test_sampled_tiles_lists_and_pixels(frame):
     differ = np.nonzero((grect != orect).any(1))[0]
     assert U.boundary_gaussians(g)[differ].all()
     odepth = g["depth"].numpy()
-    om2, oco, oal = orender.cull_inputs(g["mean2d"], g["conic"], g["alpha_cond"])
-    gm2, gco, gal = g["mean2d"].numpy(), g["conic"].numpy(), g["alpha_cond"].numpy()
+    lists = {t: pl[ranges[t, 0]:ranges[t, 1]] for t in tiles}
+    # every rectangle pair a list leaves out reaches no pixel centre of the tile (float64, brute force)
+    worst, pairs = U.dropped_pair_alpha(g, cam, tiles, lists, exclude=differ)
+    assert pairs > 0 and worst < 1.0 / 255.0, (pairs, worst)
     pixels = []
     for tile in tiles:
         lst = pl[ranges[tile, 0]:ranges[tile, 1]]
-        tx, ty = tile % cam.tiles_x, tile // cam.tiles_x
-        inside = (orect[:, 0] <= tx) & (tx < orect[:, 2]) & (orect[:, 1] <= ty) & (ty < orect[:, 3])
-        ref = np.nonzero(inside)[0]
-        reach = binning.tile_reachable(om2[ref], oco[ref], oal[ref], tx, ty)
-        ref = ref[reach]
-        ref = ref[np.lexsort((ref, odepth[ref]))]
         a = lst[~np.isin(lst, differ)]
-        b = ref[~np.isin(ref, differ)]
-        # members on which the two sides disagree sit on the reachability boundary: no pixel of
-        # the tile reaches alpha = 1/255 from them (float64, oracle record)
-        odd = np.setxor1d(a, b)
-        px_, py_ = np.meshgrid(np.arange(16) + 0.5 + 16 * tx, np.arange(16) + 0.5 + 16 * ty)
-        for gi in odd:
-            dx, dy = px_ - gm2[gi, 0], py_ - gm2[gi, 1]
-            qa, qb, qc = gco[gi]
-            al = gal[gi] * np.exp(-0.5 * (qa * dx * dx + 2 * qb * dx * dy + qc * dy * dy))
-            assert al.max() < (1 / 255) * 1.01, (gi, al.max())
-        a = a[~np.isin(a, odd)]
-        b = b[~np.isin(b, odd)]
-        assert np.array_equal(np.sort(a), np.sort(b))
-        # same order, except swaps of depths equal to FP32 accuracy
+        # depth order, except swaps of depths equal to FP32 accuracy
         za = odepth[a]
         assert np.all(np.diff(za) >= -4e-6 * np.abs(za[1:]))
         if not np.isin(lst, differ).any():
@@ -172,13 +155,15 @@ def test_sampled_tiles_lists_and_pixels(frame):
     ref = orender.render_pixels(g, cam, pix)
     img = r.image.cpu().numpy()[pix[:, 0], pix[:, 1]]
     ok = U.pixel_ok(ref["margin_alpha"].numpy(), ref["margin_T"].numpy(), ref["margin_depth"].numpy())
-    assert ok.mean() > 0.9, (ok.mean(), (ref["margin_alpha"].numpy() < U.PIX_ALPHA).mean(),
-                             (ref["margin_T"].numpy() < U.PIX_T).mean(),
-                             (ref["margin_depth"].numpy() < U.PIX_DEPTH).mean())
+    # pixels set aside where an FP32 decision may flip with visible effect: 1.1% of this sample
+    assert ok.mean() > 0.985, (ok.mean(), (ref["margin_alpha"].numpy() < U.PIX_ALPHA).mean(),
+                               (ref["margin_T"].numpy() < U.PIX_T).mean(),
+                               (ref["margin_depth"].numpy() < U.PIX_DEPTH).mean())
     err = np.abs(img - ref["color"].numpy()).max(-1)
     assert err[ok].max() <= COLOUR_TOL, err[ok].max()
-    nc = r.n_contrib.cpu().numpy()[pix[:, 0], pix[:, 1]]
-    assert np.mean(nc[ok] == ref["n_contrib"].numpy()[ok]) > 0.99
+    last = U.last_ids(r.n_contrib.cpu().numpy(), r.bins.point_list.cpu().numpy(), ranges, cam.tiles_x,
+                      rows=pix[:, 0], cols=pix[:, 1])
+    np.testing.assert_array_equal(last[ok], ref["last_id"].numpy()[ok])
 
 
 def test_fullsize_gradients_on_sampled_tiles():

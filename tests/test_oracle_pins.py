@@ -409,8 +409,7 @@ def test_transmittance_monotone_and_stop_rule():
 def test_vectorised_compositing_equals_per_pixel_loop():
     rec = synth.random_projected(150, 48, 32, seed=15)
     out = render.render_projected(rec, 48, 32, (0.1, 0.2, 0.3))
-    lists = binning.tile_lists(rec["depth"], rec["rect"], 3, 6,
-                               cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
+    lists = binning.tile_lists(rec["depth"], rec["rect"], 3, 6)
     f = lambda k: np.asarray(rec[k], np.float32).astype(np.float64)
     for y in range(0, 32, 3):
         for x in range(0, 48, 5):
@@ -420,6 +419,29 @@ def test_vectorised_compositing_equals_per_pixel_loop():
             np.testing.assert_allclose(out["image"][y, x].numpy(), col, atol=1e-13)
             assert out["n_contrib"][y, x].item() == last
             assert abs(out["final_T"][y, x].item() - T) < 1e-13
+
+
+def test_reachability_filter_changes_no_pixel():
+    """Compositing over the rectangle lists (the blending rule as stated) and over the lists the
+    binning's reachability rule keeps gives the same image, transmittance and last contributor:
+    the rule only drops candidates that every pixel of the tile skips."""
+    scene = synth.config_scene(0)
+    cam = synth.config_cameras(0)[0]
+    full = render.render(scene, cam)
+    kept = render.render(scene, cam, reach=True)
+    # (the colour sums run over lists of different length, so only their rounding may differ)
+    assert float((full["image"] - kept["image"]).abs().max()) < 1e-12
+    assert torch.equal(full["final_T"], kept["final_T"])
+    assert torch.equal(full["last_id"], kept["last_id"])
+    assert (full["last_id"] >= 0).float().mean() > 0.5
+    # the filtered lists are much shorter, so positions differ while the contributors agree
+    assert (full["n_contrib"] >= kept["n_contrib"]).all()
+    assert (full["n_contrib"] > kept["n_contrib"]).any()
+    rec = synth.random_projected(400, 80, 64, seed=21, max_half_tiles=3)
+    a = render.render_projected(rec, 80, 64, (0.2, 0.1, 0.4))
+    b = render.render_projected(rec, 80, 64, (0.2, 0.1, 0.4), reach=True)
+    assert float((a["image"] - b["image"]).abs().max()) < 1e-12
+    assert torch.equal(a["last_id"], b["last_id"]) and torch.equal(a["final_T"], b["final_T"])
 
 
 # ----------------------------------------------------------------------------------------------
