@@ -42,7 +42,7 @@ enum sdgs_status {
   SDGS_ERR_WORKSPACE = 2,   /* workspace missing or smaller than sdgs_bin_workspace_size() */
   SDGS_ERR_OVERFLOW = 3,    /* more (tile, Gaussian) instances than the bins' capacity */
   SDGS_ERR_CUDA = 4,        /* a CUDA runtime call failed; the message names it */
-  SDGS_ERR_TIMEOUT = 5,     /* a bounded wait ran out (server) */
+  SDGS_ERR_TIMEOUT = 5,     /* a bounded wait ran out (server; a binning look-back) */
   SDGS_ERR_BUSY = 6,        /* server queue full */
   SDGS_ERR_OOM_BUDGET = 7,  /* a request does not fit the server's memory budget */
   SDGS_ERR_NOT_FOUND = 8    /* unknown scene or request id */
@@ -182,7 +182,13 @@ int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t 
  * If num_instances_host is not NULL the call synchronises the stream, stores K there and returns
  * SDGS_ERR_OVERFLOW when K > capacity; otherwise it never synchronises (K stays on the device and
  * an overflow only truncates the lists).
- * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_OVERFLOW, SDGS_ERR_CUDA. */
+ * Every wait inside the sort (a block reading the counts of the blocks before it) is bounded.  If
+ * one ever gives up (never expected: a block only waits on blocks that are already running), the
+ * later binning kernels skip their work, every tile range is left empty (so compositing reads no
+ * list entry) and the device instance count is set to -1: a negative count read back on any path
+ * means the frame failed.  With num_instances_host the call then returns SDGS_ERR_TIMEOUT.
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_OVERFLOW, SDGS_ERR_TIMEOUT,
+ * SDGS_ERR_CUDA. */
 int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
                   size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                   void* stream);
@@ -198,18 +204,53 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  The call itself allocates
  * nothing.  All calls share the one array: calls whose work overlaps on the GPU (different streams,
- * or host threads without ordering) race and corrupt each other's results. */
+ * or host threads without ordering) race and corrupt each other's results.  The looked-up address
+ * is cached per device for the life of the process and is not refreshed by cudaDeviceReset: after
+ * resetting a device, do not call this function on it again in the same process. */
 #define SDGS_STATIC_BIN_SCRATCH_BYTES ((size_t)64 << 20)
 int sdgs_bin_sort_static(const sdgs_projected* proj, const sdgs_view* view, const sdgs_bins* out,
                          int64_t* num_instances_host, void* stream);
+
+/* Test support for the sort's bounded waits (no counterpart in the paper).  Runs one stable 8-bit
+ * radix pass of the binning sort (digit = key & 255) over n device (key, value) pairs into
+ * keys_out / vals_out, with the pass's block tickets starting at first_ticket instead of 0.  With
+ * first_ticket = 0 it is an ordinary pass.  With first_ticket > 0 the tiles before first_ticket
+ * are never processed, so the blocks that wait on them give up after spin_limit polling rounds
+ * (each a short sleep), flag the error and return: the call then returns SDGS_ERR_TIMEOUT.  Every
+ * write stays inside keys_out[0, n) / vals_out[0, n).  Synchronises the stream.  `workspace` is
+ * device memory of at least sdgs_lookback_selftest_workspace_size() bytes, 256-byte aligned.
+ * Errors: SDGS_ERR_INVALID_ARG (n outside [0, 2^30), first_ticket > 2^20, spin_limit outside
+ * [1, 2^20]), SDGS_ERR_WORKSPACE, SDGS_ERR_TIMEOUT, SDGS_ERR_CUDA. */
+int sdgs_lookback_selftest_workspace_size(int64_t n, size_t* bytes);
+/* Test support (no counterpart in the paper): sdgs_bin_sort as if the first pass of its sort had
+ * given up waiting (its error bit set before any work), to exercise what every later kernel does
+ * then: the lists stay empty, the device instance count becomes -1 and, with num_instances_host,
+ * the call returns SDGS_ERR_TIMEOUT.  Same arguments as sdgs_bin_sort. */
+int sdgs_bin_sort_failure_selftest(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                                   size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                                   void* stream);
+int sdgs_lookback_selftest(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out,
+                           int64_t n, uint32_t first_ticket, int32_t spin_limit, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
+/* Measurement support (no counterpart in the paper): one launch of a throughput probe of an SM
+ * pipe the rasteriser is bound by, kind 0 = scalar FP32 FMA, 1 = paired FP32 FMA (two FMAs per
+ * instruction), 2 = MUFU ex2.approx.  Many independent chains per thread over 64 warps per SM, so
+ * the pipe, not latency, limits the rate.  Stores in *ops (host) the operations the launch performs
+ * (FLOP for kinds 0 and 1, with an FMA counted as 2; ex2 evaluations for kind 2); the caller times
+ * the launch on `stream`.  `sink` is device float32 of at least
+ * 8 * 256 * (multiprocessor count) elements (overwritten).  Enqueues only.
+ * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE (sink too small), SDGS_ERR_CUDA. */
+int sdgs_alu_peak_probe(int32_t kind, int32_t iters, float* sink, int64_t sink_len, double* ops, void* stream);
 
 /* Front-to-back compositing of each 16x16 tile's sorted instances.
  * Per pixel: alpha_i = min(0.99, alpha_cond exp(-1/2 (a dx^2 + c dy^2) - b dx dy)), skipped when
  * below 1/255; the pixel stops before the Gaussian that would take its transmittance below 1e-4.
  * Writes image [height][width][3] = sum c_i alpha_i T_i + T_final bg, final_T [height][width] and
  * n_contrib [height][width] (1 + position in the tile list of the last Gaussian blended, 0 if
- * none).  All outputs are device float32 / uint32.  If n_evaluated (device uint64) is not NULL,
- * the number of (pixel, Gaussian) pairs evaluated is ADDED to it (the compositing work).
+ * none).  All outputs are device float32 / uint32.  If n_evaluated (device uint64[2]) is not
+ * NULL, the number of (pixel, Gaussian) pairs evaluated is ADDED to n_evaluated[0] and the number
+ * of those that were blended (contributions) to n_evaluated[1]: the compositing work.
  * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_CUDA. */
 int sdgs_render_fwd(const sdgs_projected* proj, const sdgs_bins* bins, const sdgs_view* view,
                     float* image, float* final_T, uint32_t* n_contrib, uint64_t* n_evaluated,

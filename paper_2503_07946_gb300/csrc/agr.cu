@@ -361,7 +361,7 @@ __global__ void agr_reduce_kernel(const float* __restrict__ partial, int blocks,
 
 int agr_bwd_blocks(int64_t n) {
   const int64_t tiles = (n + kAgrThreads - 1) / kAgrThreads;
-  return (int)std::min<int64_t>(tiles, 2 * 152);
+  return (int)std::min<int64_t>(tiles, 2 * (int64_t)device_sm_count());
 }
 
 }  // namespace
@@ -372,7 +372,7 @@ cudaError_t launch_agr_refine(const sdgs_scene& s, const sdgs_agr& a, float t, f
                               cudaStream_t st) {
   if (s.n == 0) return cudaSuccess;
   const int64_t tiles = (s.n + kAgrThreads - 1) / kAgrThreads;
-  agr_refine_kernel<<<(unsigned)std::min<int64_t>(tiles, 4 * 152), kAgrThreads, 0, st>>>(
+  agr_refine_kernel<<<(unsigned)std::min<int64_t>(tiles, 4 * (int64_t)device_sm_count()), kAgrThreads, 0, st>>>(
       s.mean7, s.L28, s.n, a, t, mean7_out, L28_out);
   return cudaGetLastError();
 }

@@ -19,6 +19,21 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+int device_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static int counts[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+  std::lock_guard<std::mutex> lock(mu);
+  if (counts[dev] == 0) {
+    int c = 0;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) c = 152;
+    counts[dev] = c;
+  }
+  return counts[dev];
+}
+
 int cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return SDGS_OK;
   set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
@@ -143,7 +158,8 @@ int sdgs_bin_workspace_size(int64_t n, int64_t capacity, int32_t width, int32_t 
 }  // extern "C"
 
 // With a host count requested: synchronise, then report a sort that gave up waiting (never
-// expected: every wait is on a block that is already running) or an overflow.
+// expected: every wait is on a block that is already running) or an overflow.  A sort that gave
+// up leaves every tile range empty and the device instance count at -1.
 static int finish_bin_sort(const BinPlan& plan, const char* ws, const sdgs_bins* out, int64_t* num_instances_host,
                            cudaStream_t st) {
   if (num_instances_host == nullptr) return SDGS_OK;
@@ -153,9 +169,9 @@ static int finish_bin_sort(const BinPlan& plan, const char* ws, const sdgs_bins*
   SDGS_TRY(cuda_status(cudaMemcpyAsync(&err, ws + plan.off_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
                        "copy sort status"));
   SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "bin_sort synchronize"));
-  if (err != 0) {
-    set_error("binning sort: a look-back wait gave up; the lists are invalid");
-    return SDGS_ERR_CUDA;
+  if (err != 0 || *num_instances_host < 0) {
+    set_error("binning sort: a look-back wait gave up (status 0x%x); every tile list was left empty", err);
+    return SDGS_ERR_TIMEOUT;
   }
   if (*num_instances_host > out->capacity) {
     set_error("%lld instances exceed capacity %lld", (long long)*num_instances_host, (long long)out->capacity);
@@ -166,9 +182,9 @@ static int finish_bin_sort(const BinPlan& plan, const char* ws, const sdgs_bins*
 
 extern "C" {
 
-int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
-                  size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
-                  void* stream) {
+static int bin_sort_impl(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                         size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                         void* stream, uint32_t inject_err) {
   g_error[0] = 0;
   SDGS_TRY(check_projected(proj));
   SDGS_TRY(check_view(view));
@@ -179,8 +195,21 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
     return SDGS_ERR_WORKSPACE;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st), "bin_sort launch"));
+  SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st, inject_err),
+                       "bin_sort launch"));
   return finish_bin_sort(plan, (const char*)workspace, out, num_instances_host, st);
+}
+
+int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                  size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                  void* stream) {
+  return bin_sort_impl(proj, view, workspace, workspace_bytes, out, num_instances_host, stream, 0u);
+}
+
+int sdgs_bin_sort_failure_selftest(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                                   size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                                   void* stream) {
+  return bin_sort_impl(proj, view, workspace, workspace_bytes, out, num_instances_host, stream, 1u);
 }
 
 }  // extern "C"
@@ -199,6 +228,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
+// The array's device address for the current device, looked up at the first call on that device
+// and cached.  The cache is not invalidated by cudaDeviceReset: a caller that resets a device and
+// keeps using the library in the same process must not call sdgs_bin_sort_static again.
 int static_scratch(void** ptr) {
   int dev = 0;
   SDGS_TRY(cuda_status(cudaGetDevice(&dev), "cudaGetDevice"));
@@ -234,6 +266,60 @@ int sdgs_bin_sort_static(const sdgs_projected* proj, const sdgs_view* view, cons
   cudaStream_t st = (cudaStream_t)stream;
   SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)ws, *out, st), "bin_sort launch"));
   return finish_bin_sort(plan, (const char*)ws, out, num_instances_host, st);
+}
+
+int sdgs_alu_peak_probe(int32_t kind, int32_t iters, float* sink, int64_t sink_len, double* ops, void* stream) {
+  g_error[0] = 0;
+  const int64_t need = alu_probe_sink_len();
+  if (kind < 0 || kind > 2 || iters < 1 || ops == nullptr) {
+    set_error("alu_peak_probe: kind in {0, 1, 2}, iters >= 1, ops not NULL");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (sink == nullptr || sink_len < need || !aligned(sink, 4)) {
+    set_error("alu_peak_probe: sink needs %lld floats", (long long)need);
+    return SDGS_ERR_WORKSPACE;
+  }
+  return cuda_status(launch_alu_probe(kind, iters, sink, ops, (cudaStream_t)stream), "alu probe launch");
+}
+
+int sdgs_lookback_selftest_workspace_size(int64_t n, size_t* bytes) {
+  g_error[0] = 0;
+  if (bytes == nullptr || n < 0 || n >= (int64_t(1) << 30)) {
+    set_error("bad arguments to sdgs_lookback_selftest_workspace_size");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  *bytes = lookback_selftest_bytes(n);
+  return SDGS_OK;
+}
+
+int sdgs_lookback_selftest(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out,
+                           int64_t n, uint32_t first_ticket, int32_t spin_limit, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  g_error[0] = 0;
+  if (n < 0 || n >= (int64_t(1) << 30) || first_ticket > (1u << 20) || spin_limit < 1 || spin_limit > (1 << 20)) {
+    set_error("lookback selftest: n in [0, 2^30), first_ticket <= 2^20, spin_limit in [1, 2^20]");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  if (n > 0 && (!keys || !vals || !keys_out || !vals_out)) { set_error("NULL key / value array"); return SDGS_ERR_INVALID_ARG; }
+  const size_t need = lookback_selftest_bytes(n);
+  if (workspace == nullptr || workspace_bytes < need || !aligned(workspace, 256)) {
+    set_error("lookback selftest workspace needs %zu bytes, 256-byte aligned", need);
+    return SDGS_ERR_WORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* err_dev = nullptr;
+  SDGS_TRY(cuda_status(launch_lookback_selftest(keys, vals, keys_out, vals_out, n, first_ticket, spin_limit,
+                                                (char*)workspace, &err_dev, st),
+                       "lookback selftest launch"));
+  uint32_t err = 0;
+  SDGS_TRY(cuda_status(cudaMemcpyAsync(&err, err_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                       "copy sort status"));
+  SDGS_TRY(cuda_status(cudaStreamSynchronize(st), "lookback selftest synchronize"));
+  if (err != 0) {
+    set_error("radix pass: a look-back wait gave up after %d rounds (status 0x%x)", spin_limit, err);
+    return SDGS_ERR_TIMEOUT;
+  }
+  return SDGS_OK;
 }
 
 int sdgs_render_fwd(const sdgs_projected* proj, const sdgs_bins* bins, const sdgs_view* view,

@@ -21,6 +21,7 @@ struct RasterBwdArgs {
   const uint32_t* n_contrib;
   const float* dL_dimage;
   int width, height, tiles_x;
+  uint32_t n;  // Gaussians in the records; a list entry >= n (never written by binning) is skipped
   float bg[3];
   float* g2;  // [n][12]
 };
@@ -186,12 +187,14 @@ __global__ void __launch_bounds__(kBwdThreads, 16) raster_bwd_kernel(const Raste
       const int j = lo + e;
       if (j < top) {
         const uint32_t gid = a.point_list[range.x + j];
-        const float4 co = a.conic_opacity[gid];
-        s_xy[e] = a.mean2d[gid];
+        const bool ok = gid < a.n;
+        const float4 co = ok ? a.conic_opacity[gid] : make_float4(0.f, 0.f, 0.f, 0.f);  // alpha 0: skipped
+        s_xy[e] = ok ? a.mean2d[gid] : make_float2(0.f, 0.f);
         s_co[e] = co;
         s_q[e] = scaled_conic(co);
-        s_rgb[e] = make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f);
-        s_id[e] = gid;
+        s_rgb[e] = ok ? make_float4(a.rgb[3 * gid + 0], a.rgb[3 * gid + 1], a.rgb[3 * gid + 2], 0.f)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        s_id[e] = ok ? gid : 0xffffffffu;
       }
     }
     const int cnt = top - lo;
@@ -220,6 +223,7 @@ __global__ void __launch_bounds__(kBwdThreads, 16) raster_bwd_kernel(const Raste
     // one set of global atomics per Gaussian and block: d(u, v) = alpha_cond Conic (Sx, Sy),
     // d(a, b, c) = -alpha_cond (Sxx / 2, Sxy, Syy / 2)
     for (int e = threadIdx.x; e < cnt; e += kBwdThreads) {
+      if (s_id[e] == 0xffffffffu) continue;  // a skipped entry gathered nothing
       float* out = a.g2 + (size_t)kG2 * s_id[e];
       const float4 co = s_co[e];
       float* S = s_g[e];
@@ -567,6 +571,7 @@ cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdg
   r.final_T = final_T;
   r.n_contrib = n_contrib;
   r.dL_dimage = dL_dimage;
+  r.n = (uint32_t)p.n;
   r.width = v.width;
   r.height = v.height;
   r.tiles_x = tiles_of(v.width);

@@ -143,9 +143,37 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const TIn* in, 
   }
 }
 
+// The whole scan in one block, for up to kSingleScanItems * 1024 elements: each thread sums its
+// run of consecutive elements, the block scans the sums, and each thread writes its run.
+constexpr int kSingleScanItems = 16;
+
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(1024) scan_single_kernel(const TIn* in, int64_t n, TOut* out, int64_t* total_out) {
+  griddep_wait();
+  const int64_t per = (n + 1023) / 1024;  // <= kSingleScanItems
+  const int64_t base = (int64_t)threadIdx.x * per;
+  TIn v[kSingleScanItems];
+  TOut local = 0;
+#pragma unroll
+  for (int k = 0; k < kSingleScanItems; ++k) {
+    v[k] = (k < per && base + k < n) ? in[base + k] : TIn(0);
+    local += (TOut)v[k];
+  }
+  TOut tot;
+  TOut run = block_inclusive_scan<TOut, 1024>(local, &tot) - local;
+#pragma unroll
+  for (int k = 0; k < kSingleScanItems; ++k) {
+    if (k < per && base + k < n) out[base + k] = run;
+    run += (TOut)v[k];
+  }
+  if (threadIdx.x == 0 && total_out != nullptr) *total_out = (int64_t)tot;
+}
+
 template <typename TIn, typename TOut>
 cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partials,
                            int64_t* total_out, cudaStream_t st) {
+  if (n <= (int64_t)kSingleScanItems * 1024)
+    return launch_pdl(scan_single_kernel<TIn, TOut>, dim3(1), dim3(1024), 0, st, in, n, out, total_out);
   const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
   TOut* part = reinterpret_cast<TOut*>(partials);
   cudaError_t e = cudaSuccess;
@@ -190,7 +218,7 @@ constexpr uint32_t kStatusAggregate = 1u << 30;  // this tile's own count of the
 constexpr uint32_t kStatusInclusive = 2u << 30;  // count of the digit in tiles 0 .. this one
 constexpr uint32_t kStatusCount = (1u << 30) - 1u;
 constexpr int kLookbackSpins = 1 << 20;
-constexpr int kLookbackWindow = 8;
+constexpr int kLookbackWindow = 16;
 constexpr int kMaxPasses = 4;
 
 __global__ void __launch_bounds__(kRadixThreads)
@@ -225,9 +253,9 @@ __device__ __forceinline__ void store_status(uint32_t* p, uint32_t v) {
 // digit (stable: earlier rows, then lower lanes, first), counting them in s_whist[warp].  FULL: the
 // whole tile is in range, so no key needs a bound check.
 template <int ITEMS, bool FULL>
-__device__ __forceinline__ void load_and_rank(const uint32_t* __restrict__ keys_in, int64_t wbase, int64_t n,
-                                              int shift, int width, uint32_t* whist, uint32_t key[ITEMS],
-                                              uint32_t rank[ITEMS]) {
+__device__ __forceinline__ void load_and_rank(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                                              int64_t wbase, int64_t n, int shift, int width, uint32_t* whist,
+                                              uint32_t key[ITEMS], uint32_t val[ITEMS], uint32_t rank[ITEMS]) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   const uint32_t dmask = (1u << width) - 1u;
@@ -235,6 +263,7 @@ __device__ __forceinline__ void load_and_rank(const uint32_t* __restrict__ keys_
   for (int r = 0; r < ITEMS; ++r) {
     const int64_t idx = wbase + r * 32 + lane;
     key[r] = (FULL || idx < n) ? keys_in[idx] : 0u;
+    val[r] = (FULL || idx < n) ? vals_in[idx] : 0u;
   }
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
@@ -251,12 +280,51 @@ __device__ __forceinline__ void load_and_rank(const uint32_t* __restrict__ keys_
   }
 }
 
+// Keys with digit dg in sort tiles 0 .. tile - 1, from the status words of the earlier tiles: each
+// round loads the next kLookbackWindow of them at once (nearest first) and adds their counts up to
+// the first inclusive one; an entry not yet published ends the round, and the next round starts at
+// it after a short sleep.  Every wait is bounded: after spin_limit rounds that found an
+// unpublished entry the block sets this pass's bit of *err and returns what it has.
+__device__ __forceinline__ uint32_t lookback(const uint32_t* status, int64_t tile, int dg, int spin_limit,
+                                             uint32_t pass_bit, uint32_t* err) {
+  uint32_t before = 0;
+  int64_t j = tile - 1;
+  int spins = 0;
+  while (j >= 0) {
+    uint32_t st[kLookbackWindow];
+#pragma unroll
+    for (int w = 0; w < kLookbackWindow; ++w)
+      st[w] = j - w >= 0 ? load_status(status + (j - w) * kBins + dg) : kStatusInclusive;  // before tile 0: 0
+    bool done = false, blocked = false;
+#pragma unroll
+    for (int w = 0; w < kLookbackWindow; ++w) {
+      if (done || blocked) continue;
+      if ((st[w] & ~kStatusCount) == 0u) {
+        blocked = true;  // not published yet: poll it next round
+        continue;
+      }
+      before += st[w] & kStatusCount;
+      if (st[w] & kStatusInclusive) done = true;
+      else --j;
+    }
+    if (done) break;
+    if (blocked) {
+      if (++spins > spin_limit) {
+        atomicOr(err, pass_bit);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  return before;
+}
+
 template <int ITEMS>
 __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 6)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* nptr,
                 int64_t n_static, int64_t cap, int shift, int width, const uint32_t* __restrict__ digit_hist,
-                uint32_t* status, uint32_t* ticket, uint32_t* err) {
+                uint32_t* status, uint32_t* ticket, uint32_t* err, uint32_t pass_bit, int spin_limit) {
   griddep_wait();
   constexpr int TILE = kRadixThreads * ITEMS;
   __shared__ uint32_t s_keys[TILE];
@@ -272,80 +340,55 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
   const int64_t n = element_count(nptr, n_static, cap);
   const int64_t base = tile * TILE;
   if (base >= n) return;  // so do all later tiles: nobody waits on this one
+  // An earlier pass gave up waiting: its output is not a permutation of its input, so this pass's
+  // digit histogram no longer bounds its positions.  Skip (ranges_kernel then empties the lists).
+  // (Bits of this pass are set only by its own blocks, which never make another block skip.)
+  if ((*reinterpret_cast<volatile uint32_t*>(err) & (pass_bit - 1u)) != 0u) return;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t dmask = (1u << width) - 1u;
   const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
   const bool full = base + TILE <= n;  // uniform over the block
-  uint32_t key[ITEMS], rank[ITEMS];
-  if (full) load_and_rank<ITEMS, true>(keys_in, wbase, n, shift, width, s_whist[warp], key, rank);
-  else load_and_rank<ITEMS, false>(keys_in, wbase, n, shift, width, s_whist[warp], key, rank);
-  __syncthreads();
+  const int dg = threadIdx.x;
+  const bool used = dg <= (int)dmask;  // digits of `width` bits: the other bins stay empty
+  uint32_t* mine = status + tile * kBins + dg;
+  uint32_t run = 0;  // this tile's keys with digit dg
   {
-    const int dg = threadIdx.x;
-    uint32_t run = 0;  // this tile's keys with digit dg
+    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+    if (full) load_and_rank<ITEMS, true>(keys_in, vals_in, wbase, n, shift, width, s_whist[warp], key, val, rank);
+    else load_and_rank<ITEMS, false>(keys_in, vals_in, wbase, n, shift, width, s_whist[warp], key, val, rank);
+    __syncthreads();
 #pragma unroll
     for (int w = 0; w < kRadixWarps; ++w) {
       const uint32_t c = s_whist[w][dg];
       s_whist[w][dg] = run;
       run += c;
     }
-    uint32_t* mine = status + tile * kBins + dg;
-    const bool used = dg <= (int)dmask;  // digits of `width` bits: the other bins stay empty
+    // publish this tile's count at once, so later tiles can pass over it while it waits
     if (used) store_status(mine, (tile == 0 ? kStatusInclusive : kStatusAggregate) | run);
-    uint32_t before = 0;  // keys with digit dg in tiles 0 .. tile - 1
-    int spins = 0;
-    // Wait for the nearest unresolved tile (one load per poll, with a short sleep), then take up
-    // to kLookbackWindow - 1 further tiles from one round of parallel loads, nearest first, until
-    // an inclusive count or a tile that has published nothing yet.
-    for (int64_t j = used ? tile - 1 : -1; j >= 0;) {
-      const uint32_t near = load_status(status + j * kBins + dg);
-      if ((near & ~kStatusCount) == 0u) {
-        if (++spins > kLookbackSpins) {
-          atomicOr(err, 1u);
-          break;
-        }
-        __nanosleep(32);
-        continue;
-      }
-      before += near & kStatusCount;
-      if (near & kStatusInclusive) break;
-      --j;
-      uint32_t st[kLookbackWindow - 1];
-#pragma unroll
-      for (int w = 0; w < kLookbackWindow - 1; ++w) st[w] = j - w >= 0 ? load_status(status + (j - w) * kBins + dg) : 0u;
-      bool done = false, stop = false;
-#pragma unroll
-      for (int w = 0; w < kLookbackWindow - 1; ++w) {
-        if (done || stop || j < 0) continue;
-        if ((st[w] & ~kStatusCount) == 0u) {
-          stop = true;  // not published yet: poll it next
-          continue;
-        }
-        before += st[w] & kStatusCount;
-        if (st[w] & kStatusInclusive) done = true;
-        else --j;
-      }
-      if (done) break;
-    }
-    if (used && tile > 0) store_status(mine, kStatusInclusive | (before + run));
     uint32_t tot;
     const uint32_t incl = block_inclusive_scan<uint32_t, kRadixThreads>(run, &tot);
     s_dstart[dg] = incl - run;
+    __syncthreads();
+    // the tile's keys in digit order, in shared memory (stable: warps, then ranks)
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const int64_t idx = wbase + r * 32 + lane;
+      if (full || idx < n) {
+        const uint32_t d = (key[r] >> shift) & dmask;
+        const uint32_t pos = s_dstart[d] + s_whist[warp][d] + rank[r];
+        s_keys[pos] = key[r];
+        s_vals[pos] = val[r];
+      }
+    }
+  }
+  const uint32_t before = used && tile > 0 ? lookback(status, tile, dg, spin_limit, pass_bit, err) : 0u;
+  if (used && tile > 0) store_status(mine, kStatusInclusive | (before + run));
+  {
+    uint32_t tot;
     const uint32_t all = digit_hist[dg];
     const uint32_t gincl = block_inclusive_scan<uint32_t, kRadixThreads>(all, &tot);
     s_gbase[dg] = gincl - all + before;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    const int64_t idx = wbase + r * 32 + lane;
-    if (full || idx < n) {
-      const uint32_t d = (key[r] >> shift) & dmask;
-      const uint32_t pos = s_dstart[d] + s_whist[warp][d] + rank[r];
-      s_keys[pos] = key[r];
-      s_vals[pos] = vals_in[idx];
-    }
   }
   __syncthreads();
   if (full) {
@@ -355,8 +398,10 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
       const uint32_t k = s_keys[i];
       const uint32_t d = (k >> shift) & dmask;
       const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
-      keys_out[g] = k;
-      vals_out[g] = s_vals[i];
+      if (g < (uint64_t)n) {  // always, unless a look-back gave up
+        keys_out[g] = k;
+        vals_out[g] = s_vals[i];
+      }
     }
   } else {
     const int cnt = (int)(n - base);
@@ -364,8 +409,10 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
       const uint32_t k = s_keys[i];
       const uint32_t d = (k >> shift) & dmask;
       const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
-      keys_out[g] = k;
-      vals_out[g] = s_vals[i];
+      if (g < (uint64_t)n) {
+        keys_out[g] = k;
+        vals_out[g] = s_vals[i];
+      }
     }
   }
 }
@@ -384,7 +431,7 @@ int radix_pass_count(int bits) {
 // Keys per sort block for `cap` slots: the largest tile (12, 8 or 4 keys per thread) that still
 // gives two blocks per SM, so that small sorts are not latency-bound on a few blocks.
 int sort_items(int64_t cap) {
-  const int64_t want = 2 * 152;
+  const int64_t want = 2 * (int64_t)device_sm_count();
   if ((cap + 12 * kRadixThreads - 1) / (12 * kRadixThreads) >= want) return 12;
   if ((cap + 8 * kRadixThreads - 1) / (8 * kRadixThreads) >= want) return 8;
   return 4;
@@ -444,7 +491,8 @@ __device__ __forceinline__ void flush_digits(const uint32_t (*s_hist)[kBins], in
 // With hist_ready, the caller has cleared the scratch (sort_clear) and accumulated the digit
 // histograms of all keys into its first kMaxPasses * kBins words while producing them.
 int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_t n_static,
-               int64_t cap, int bits, uint32_t* scratch, uint32_t* err, bool hist_ready, cudaStream_t st) {
+               int64_t cap, int bits, uint32_t* scratch, uint32_t* err, int first_pass, bool hist_ready,
+               cudaStream_t st, int spin_limit = kLookbackSpins) {
   int cur = 0;
   if (cap <= 0 || bits <= 0) return cur;
   const int width = radix_digit_width(bits);
@@ -456,7 +504,7 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
   uint32_t* status = tickets + kMaxPasses;
   if (!hist_ready) {
     sort_clear(scratch, cap, bits, st);
-    const int64_t hist_blocks = std::min<int64_t>((cap + kRadixThreads - 1) / kRadixThreads, 4 * 152);
+    const int64_t hist_blocks = std::min<int64_t>((cap + kRadixThreads - 1) / kRadixThreads, 4 * device_sm_count());
     digit_hist_kernel<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], nptr, n_static, cap, passes,
                                                                        width, hist);
   }
@@ -465,7 +513,8 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
     const int shift = p * width;
     auto* kern = items == 12 ? onesweep_kernel<12> : items == 8 ? onesweep_kernel<8> : onesweep_kernel<4>;
     launch_pdl(kern, dim3((unsigned)nblocks), dim3(kRadixThreads), 0, st, keys[cur], vals[cur], keys[cur ^ 1],
-               vals[cur ^ 1], nptr, n_static, cap, shift, width, hist + p * kBins, stp, tickets + p, err);
+               vals[cur ^ 1], nptr, n_static, cap, shift, width, hist + p * kBins, stp, tickets + p, err,
+               1u << (first_pass + p), spin_limit);
     cur ^= 1;
   }
   return cur;
@@ -493,7 +542,8 @@ __global__ void __launch_bounds__(256) clear_kernel(const ClearJob job) {
   }
 }
 
-// Depth keys of the Gaussians (culled ones last) and their digit histograms for the depth sort.
+// Depth keys of the Gaussians (culled ones last) and their digit histograms for the depth sort.  A
+// few blocks per SM stride over the Gaussians, so that few block histograms are added globally.
 __global__ void __launch_bounds__(kRadixThreads)
 depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ rect, int64_t n,
                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ hist) {
@@ -501,16 +551,19 @@ depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ r
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * kRadixThreads + threadIdx.x;
-  uint32_t k = 0;
-  if (i < n) {
-    const ushort4 r = rect[i];
-    const bool vis = r.z > r.x && r.w > r.y;
-    k = vis ? __float_as_uint(depth[i]) : 0xffffffffu;  // visible depths are positive
-    keys[i] = k;
-    vals[i] = (uint32_t)i;
+  const int64_t stride = (int64_t)gridDim.x * kRadixThreads;
+  for (int64_t b = (int64_t)blockIdx.x * kRadixThreads; b < n; b += stride) {  // uniform over the block
+    const int64_t i = b + threadIdx.x;
+    uint32_t k = 0;
+    if (i < n) {
+      const ushort4 r = rect[i];
+      const bool vis = r.z > r.x && r.w > r.y;
+      k = vis ? __float_as_uint(depth[i]) : 0xffffffffu;  // visible depths are positive
+      keys[i] = k;
+      vals[i] = (uint32_t)i;
+    }
+    count_digits(s_hist, k, i < n, 4, 8);
   }
-  count_digits(s_hist, k, i < n, 4, 8);
   __syncthreads();
   flush_digits(s_hist, 4, hist);
 }
@@ -535,34 +588,98 @@ __device__ __forceinline__ ushort4 clip_rect(ushort4 r, int tiles_x, int tiles_y
   return r;
 }
 
-// The tested tiles of a block of kWalkThreads consecutive depth-ordered Gaussians form one
-// sequence -- Gaussian-major, each tested rectangle row-major -- cut into 32-tile words that the
-// block's warps share, so a few large rectangles do not leave one warp with all the work.
-constexpr int kSpanThreads = 256;
+// Span walks.  A warp takes 32 consecutive depth-ordered Gaussians and flattens their rows: lane i
+// sets up Gaussian i (its rectangle, clipped to the grid, and its reachability rule, kept in
+// shared memory), then the warp walks the sequence of (Gaussian, row) pairs 32 rows at a time, one
+// row per lane, so that no lane idles behind a Gaussian with many rows.
+constexpr int kWalkThreads = 256;
+constexpr int kWalkWarps = kWalkThreads / 32;
 
-// Kept tiles of each depth-ordered Gaussian (one thread each): its rectangle (clipped to the grid)
-// row by row, each row's span from the reachability rule (tile_reach.cuh).
-__global__ void __launch_bounds__(kSpanThreads)
-span_count_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
-                  int tiles_x, int tiles_y, uint32_t* __restrict__ counts) {
-  griddep_wait();
-  const int64_t s = (int64_t)blockIdx.x * kSpanThreads + threadIdx.x;
-  if (s >= n) return;
-  const uint32_t g = order[s];
-  const ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
-  uint32_t c = 0;
-  if (r.z > r.x && r.w > r.y) {
-    const SpanRule rule = span_setup(mean2d[g], conic_opacity[g]);
-    int y0, y1;
-    span_rows(rule, r.y, r.w, &y0, &y1);
-    for (int ty = y0; ty < y1; ++ty) {
-      int x0, x1;
-      span_cols(rule, ty, r.x, r.z, &x0, &x1);
-      c += (uint32_t)(x1 - x0);
+struct WalkWarp {  // one warp's 32 Gaussians, structure of arrays (conflict-free by owner lane)
+  float u[32], v[32], a[32], b[32], det[32], aQ[32], reach_y[32], dyr[32], padx[32];
+  int mode[32], rx0[32], rx1[32], y0[32];
+  uint32_t g[32];
+};
+
+// Sets up this lane's Gaussian (depth-order position s) and returns its number of candidate rows;
+// the warp's row sequence is then given by the inclusive scan of the counts.
+__device__ __forceinline__ int walk_setup(WalkWarp& w, const uint32_t* __restrict__ order,
+                                          const ushort4* __restrict__ rect, const float2* __restrict__ mean2d,
+                                          const float4* __restrict__ conic_opacity, int64_t s, int64_t n,
+                                          int tiles_x, int tiles_y) {
+  const int lane = threadIdx.x & 31;
+  int nr = 0;
+  if (s < n) {
+    const uint32_t g = order[s];
+    const ushort4 r = clip_rect(rect[g], tiles_x, tiles_y);
+    if (r.z > r.x && r.w > r.y) {
+      const SpanRule q = span_setup(mean2d[g], conic_opacity[g]);
+      int y0, y1;
+      span_rows(q, r.y, r.w, &y0, &y1);
+      nr = y1 - y0;
+      w.u[lane] = q.u; w.v[lane] = q.v; w.a[lane] = q.a; w.b[lane] = q.b; w.det[lane] = q.det;
+      w.aQ[lane] = q.aQ; w.reach_y[lane] = q.reach_y; w.dyr[lane] = q.dyr; w.padx[lane] = q.padx;
+      w.mode[lane] = q.mode; w.rx0[lane] = r.x; w.rx1[lane] = r.z; w.y0[lane] = y0; w.g[lane] = g;
     }
   }
-  counts[s] = c;
+  __syncwarp();
+  return nr;
+}
+
+// The lane holding element k of a sequence whose lanes own runs of lengths given by their
+// inclusive prefix `incl` (the first lane with incl > k); k < the total.  All lanes call.
+__device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t k) {
+  int o = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const uint32_t v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+    if (v <= k) o += step;
+  }
+  return o;
+}
+
+// Kept tiles [*x0, *x1) of row k of the warp's row sequence (row_incl: inclusive row counts by
+// lane); *ty its tile row, *o its Gaussian's lane.
+__device__ __forceinline__ void walk_row(const WalkWarp& w, uint32_t row_incl, int nr, uint32_t k, int* o, int* ty,
+                                         int* x0, int* x1) {
+  *o = owner_lane(row_incl, k);
+  const uint32_t first_row = __shfl_sync(0xffffffffu, row_incl - (uint32_t)nr, *o);
+  const int i = *o;
+  SpanRule q;
+  q.u = w.u[i]; q.v = w.v[i]; q.a = w.a[i]; q.b = w.b[i]; q.det = w.det[i]; q.aQ = w.aQ[i];
+  q.hx = 0.f; q.reach_y = w.reach_y[i]; q.dyr = w.dyr[i]; q.padx = w.padx[i]; q.mode = w.mode[i];
+  *ty = w.y0[i] + (int)(k - first_row);
+  span_cols(q, *ty, w.rx0[i], w.rx1[i], x0, x1);
+}
+
+// Kept-tile count of each warp's 32 depth-ordered Gaussians (wcount[warp]).
+__global__ void __launch_bounds__(kWalkThreads)
+walk_count_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
+                  int tiles_x, int tiles_y, const uint32_t* err, uint32_t* __restrict__ wcount) {
+  griddep_wait();
+  __shared__ WalkWarp s_walk[kWalkWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
+  if (wg * 32 >= n) return;  // whole warps
+  if (*err != 0u) {  // the depth sort gave up: `order` may hold any value, so emit nothing
+    if (lane == 0) wcount[wg] = 0;
+    return;
+  }
+  WalkWarp& w = s_walk[warp];
+  const int nr = walk_setup(w, order, rect, mean2d, conic_opacity, wg * 32 + lane, n, tiles_x, tiles_y);
+  const uint32_t row_incl = warp_inclusive_scan((uint32_t)nr);
+  const uint32_t rows = __shfl_sync(0xffffffffu, row_incl, 31);
+  uint32_t sum = 0;
+  for (uint32_t rb = 0; rb < rows; rb += 32) {
+    const uint32_t k = rb + lane;
+    int o, ty, x0, x1;
+    walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
+    if (k < rows) sum += (uint32_t)(x1 - x0);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) wcount[wg] = sum;
 }
 
 // Digit histograms of the tile ids of a row span id0 .. id0 + len - 1 for the tile sort.  Pass 0
@@ -606,131 +723,62 @@ __device__ __forceinline__ void count_span_digits(const DigitAcc& acc, uint32_t 
   }
 }
 
-constexpr uint32_t kBigInstances = 32;  // above this a Gaussian is written by its whole warp
-
-__device__ __forceinline__ SpanRule shfl_rule(const SpanRule& q, int src) {
-  SpanRule o;
-  o.u = __shfl_sync(0xffffffffu, q.u, src);
-  o.v = __shfl_sync(0xffffffffu, q.v, src);
-  o.a = __shfl_sync(0xffffffffu, q.a, src);
-  o.b = __shfl_sync(0xffffffffu, q.b, src);
-  o.det = __shfl_sync(0xffffffffu, q.det, src);
-  o.aQ = __shfl_sync(0xffffffffu, q.aQ, src);
-  o.hx = 0.f;  // not used past setup
-  o.reach_y = __shfl_sync(0xffffffffu, q.reach_y, src);
-  o.dyr = __shfl_sync(0xffffffffu, q.dyr, src);
-  o.padx = __shfl_sync(0xffffffffu, q.padx, src);
-  o.mode = __shfl_sync(0xffffffffu, q.mode, src);
-  return o;
-}
-
-// Writes each depth-ordered Gaussian's (tile id, Gaussian id) pairs from its first instance,
-// row-major over its spans, and accumulates the tile-digit histograms of what it writes.  A
-// Gaussian with at most kBigInstances instances is written by its own thread (runs stored four
-// at a time when keys and vals are 16-byte aligned, `vec`); larger ones are then written by the
-// whole warp one at a time -- lanes take 32 rows, a warp scan places their spans, and the lanes
-// store consecutive instances -- so that one large Gaussian does not hold up its warp.
-// Positions >= cap are dropped.
-__global__ void __launch_bounds__(kSpanThreads)
-span_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+// Writes the (tile id, Gaussian id) pairs of each warp's 32 depth-ordered Gaussians from the warp's
+// first instance wfirst[warp], row-major over each Gaussian's spans, and accumulates the tile-digit
+// histograms of what it writes.  The warp walks its row sequence 32 rows at a time (one row per
+// lane, as in walk_count_kernel); a warp scan places the rows' spans, and the lanes then store the
+// chunk's instances 32 consecutive ones at a time (coalesced).  Positions >= cap are dropped.
+__global__ void __launch_bounds__(kWalkThreads)
+walk_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
-                 int tiles_x, int tiles_y, const uint64_t* __restrict__ first, const uint32_t* __restrict__ counts,
-                 int64_t cap, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, bool vec, int passes,
-                 int width, uint32_t* __restrict__ hist) {
+                 int tiles_x, int tiles_y, const uint64_t* __restrict__ wfirst, int64_t cap,
+                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int passes, int width,
+                 const uint32_t* err, uint32_t* __restrict__ hist) {
   griddep_wait();
+  __shared__ WalkWarp s_walk[kWalkWarps];
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   __shared__ int32_t s_diff0[kBins + 1];
   __shared__ uint32_t s_all0;
-  for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kSpanThreads) (&s_hist[0][0])[i] = 0;
-  for (int i = threadIdx.x; i <= kBins; i += kSpanThreads) s_diff0[i] = 0;
+  for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kWalkThreads) (&s_hist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i <= kBins; i += kWalkThreads) s_diff0[i] = 0;
   if (threadIdx.x == 0) s_all0 = 0;
   __syncthreads();
   const DigitAcc acc{s_hist, s_diff0, &s_all0};
-  const int64_t s = (int64_t)blockIdx.x * kSpanThreads + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  uint32_t g = 0;
-  ushort4 r = make_ushort4(0, 0, 0, 0);
-  SpanRule rule;
-  rule.mode = 2;
-  int y0 = 0, y1 = 0;
-  uint64_t pos = 0;
-  bool live = false, big = false;
-  if (s < n) {
-    pos = first[s];
-    const uint32_t cnt = counts[s];
-    if (cnt > 0 && pos < (uint64_t)cap) {
-      g = order[s];
-      r = clip_rect(rect[g], tiles_x, tiles_y);
-      rule = span_setup(mean2d[g], conic_opacity[g]);
-      span_rows(rule, r.y, r.w, &y0, &y1);
-      live = true;
-      big = cnt > kBigInstances;
-    }
-  }
-  if (live && !big) {
-    const uint4 g4 = make_uint4(g, g, g, g);
-    for (int ty = y0; ty < y1 && pos < (uint64_t)cap; ++ty) {
-      int x0, x1;
-      span_cols(rule, ty, r.x, r.z, &x0, &x1);
-      const int64_t room = cap - (int64_t)pos;
-      const uint32_t len = (uint32_t)((int64_t)(x1 - x0) < room ? (int64_t)(x1 - x0) : room);
-      const uint32_t id0 = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0;
-      uint32_t k = 0;
-      if (vec) {
-        for (; k < len && ((pos + k) & 3u); ++k) {
-          keys[pos + k] = id0 + k;
-          vals[pos + k] = g;
-        }
-        for (; k + 4 <= len; k += 4) {
-          const uint32_t id = id0 + k;
-          *reinterpret_cast<uint4*>(keys + pos + k) = make_uint4(id, id + 1, id + 2, id + 3);
-          *reinterpret_cast<uint4*>(vals + pos + k) = g4;
-        }
-      }
-      for (; k < len; ++k) {
-        keys[pos + k] = id0 + k;
-        vals[pos + k] = g;
-      }
-      count_span_digits(acc, id0, len, passes, width);
-      pos += len;
-    }
-  }
-  for (unsigned bigs = __ballot_sync(0xffffffffu, big); bigs != 0u; bigs &= bigs - 1u) {  // uniform
-    const int i = __ffs(bigs) - 1;
-    const SpanRule q = shfl_rule(rule, i);
-    const uint32_t qg = __shfl_sync(0xffffffffu, g, i);
-    const int qx0 = __shfl_sync(0xffffffffu, (int)r.x, i), qx1 = __shfl_sync(0xffffffffu, (int)r.z, i);
-    const int qy0 = __shfl_sync(0xffffffffu, y0, i), qy1 = __shfl_sync(0xffffffffu, y1, i);
-    uint64_t qpos = __shfl_sync(0xffffffffu, pos, i);
-    for (int rb = qy0; rb < qy1; rb += 32) {
-      const int ty = rb + lane;
-      int x0 = 0, x1 = 0;
-      if (ty < qy1) span_cols(q, ty, qx0, qx1, &x0, &x1);
-      const uint32_t len = (uint32_t)(x1 - x0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
+  if (wg * 32 < n && *err == 0u) {  // uniform over the warp
+    WalkWarp& w = s_walk[warp];
+    const int nr = walk_setup(w, order, rect, mean2d, conic_opacity, wg * 32 + lane, n, tiles_x, tiles_y);
+    const uint32_t row_incl = warp_inclusive_scan((uint32_t)nr);
+    const uint32_t rows = __shfl_sync(0xffffffffu, row_incl, 31);
+    uint64_t pos = wfirst[wg];
+    for (uint32_t rb = 0; rb < rows && pos < (uint64_t)cap; rb += 32) {  // uniform
+      const uint32_t k = rb + lane;
+      int o, ty, x0, x1;
+      walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
+      const uint32_t len = k < rows ? (uint32_t)(x1 - x0) : 0u;
       const uint32_t incl = warp_inclusive_scan(len);
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      const int64_t rstart = (int64_t)qpos + (int64_t)(incl - len);
-      const int64_t room = cap - rstart;
-      const uint32_t written = room <= 0 ? 0u : (room < (int64_t)len ? (uint32_t)room : len);
-      count_span_digits(acc, (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0, written, passes, width);
+      const uint32_t id0 = (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)x0;  // the row's first tile id
+      const uint32_t gid = w.g[o];
+      {  // digit histograms of the instances this row writes
+        const int64_t room = cap - ((int64_t)pos + (int64_t)(incl - len));
+        const uint32_t written = room <= 0 ? 0u : (room < (int64_t)len ? (uint32_t)room : len);
+        count_span_digits(acc, id0, written, passes, width);
+      }
       for (uint32_t j0 = 0; j0 < total; j0 += 32) {
         const uint32_t j = j0 + lane;
-        int rl = 0;  // the row lane holding instance j: the first lane whose inclusive count exceeds j
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const uint32_t v = __shfl_sync(0xffffffffu, incl, rl + step - 1);
-          if (v <= j) rl += step;
-        }
+        const int rl = owner_lane(incl, j < total ? j : total - 1);  // the row holding instance j
         const uint32_t r_excl = __shfl_sync(0xffffffffu, incl - len, rl);
-        const int r_x0 = __shfl_sync(0xffffffffu, x0, rl);
-        const uint64_t p = qpos + j;
+        const uint32_t r_id0 = __shfl_sync(0xffffffffu, id0, rl);
+        const uint32_t r_gid = __shfl_sync(0xffffffffu, gid, rl);
+        const uint64_t p = pos + j;
         if (j < total && p < (uint64_t)cap) {
-          keys[p] = (uint32_t)(rb + rl) * (uint32_t)tiles_x + (uint32_t)(r_x0 + (int)(j - r_excl));
-          vals[p] = qg;
+          keys[p] = r_id0 + (j - r_excl);
+          vals[p] = r_gid;
         }
       }
-      qpos += total;
-      if (qpos >= (uint64_t)cap) break;  // uniform
+      pos += total;
     }
   }
   __syncthreads();
@@ -770,22 +818,68 @@ __device__ __forceinline__ int64_t warp_lower_bound(const uint32_t* __restrict__
   return lo;
 }
 
-// ranges[t] = [first, end) of tile t in the sorted keys, (0, 0) for a tile without instances; one
-// warp per tile.
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const int64_t* nptr, int64_t cap,
-                              int num_tiles, uint2* __restrict__ ranges) {
+// ranges[t] = [first, end) of tile t in the sorted keys, (0, 0) for a tile without instances.  A
+// block handles kRangeTiles consecutive tiles with one more warp than tiles: warp w finds where
+// tile t0 + w starts, and tile t ends where tile t + 1 starts, so every warp does one search.  If a
+// sort pass gave up waiting (*err), every range is empty and the instance count becomes -1, so
+// that no later kernel reads the lists and every reader of the count sees the failure.
+constexpr int kRangeTiles = 8;
+
+__global__ void __launch_bounds__((kRangeTiles + 1) * 32)
+ranges_kernel(const uint32_t* __restrict__ keys, int64_t* nptr, int64_t cap, int num_tiles, const uint32_t* err,
+              uint2* __restrict__ ranges) {
   griddep_wait();
+  __shared__ uint32_t s_start[kRangeTiles + 1];
+  const int warp = threadIdx.x >> 5;
+  const int t = blockIdx.x * kRangeTiles + warp;  // tile whose start this warp finds
+  if (*err != 0u) {
+    if (warp < kRangeTiles && t < num_tiles && (threadIdx.x & 31) == 0) ranges[t] = make_uint2(0u, 0u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nptr = -1;  // nothing else reads it after a failure
+    return;
+  }
   const int64_t n = element_count(nptr, 0, cap);
-  const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (t >= num_tiles) return;  // whole warps
-  const int64_t a = warp_lower_bound(keys, n, (uint32_t)t);
-  const int64_t b = warp_lower_bound(keys, n, (uint32_t)t + 1u);
-  if ((threadIdx.x & 31) == 0) ranges[t] = b > a ? make_uint2((uint32_t)a, (uint32_t)b) : make_uint2(0u, 0u);
+  if (t <= num_tiles) {  // whole warps
+    const int64_t a = t < num_tiles ? warp_lower_bound(keys, n, (uint32_t)t) : n;
+    if ((threadIdx.x & 31) == 0) s_start[warp] = (uint32_t)a;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRangeTiles) {
+    const int tt = blockIdx.x * kRangeTiles + threadIdx.x;
+    if (tt < num_tiles) {
+      const uint32_t a = s_start[threadIdx.x], b = s_start[threadIdx.x + 1];
+      ranges[tt] = b > a ? make_uint2(a, b) : make_uint2(0u, 0u);
+    }
+  }
 }
+
+__global__ void set_word_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
+
+// Test support: one 8-bit radix pass (the binning's look-back) whose tickets start at first_ticket,
+// so that for first_ticket > 0 the blocks look back at tiles that no block will ever publish and
+// each wait runs out after spin_limit rounds.  Workspace: an error word, then one sort's scratch.
+size_t lookback_selftest_bytes(int64_t n) { return 256 + align256(sort_scratch_bytes(n, 8)); }
+
+cudaError_t launch_lookback_selftest(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
+                                     uint32_t* vals_out, int64_t n, uint32_t first_ticket, int spin_limit, char* ws,
+                                     uint32_t** err_out, cudaStream_t st) {
+  uint32_t* err = reinterpret_cast<uint32_t*>(ws);
+  uint32_t* scratch = reinterpret_cast<uint32_t*>(ws + 256);
+  *err_out = err;
+  cudaError_t e = cudaMemsetAsync(ws, 0, lookback_selftest_bytes(n), st);
+  if (e != cudaSuccess || n == 0) return e;
+  // the pass's digit histogram, then its ticket counter moved past the first tiles
+  uint32_t* kin[2] = {const_cast<uint32_t*>(keys), keys_out};
+  uint32_t* vin[2] = {const_cast<uint32_t*>(vals), vals_out};
+  const int64_t hist_blocks = std::min<int64_t>((n + kRadixThreads - 1) / kRadixThreads, 4 * device_sm_count());
+  digit_hist_kernel<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys, nullptr, n, n, 1, 8, scratch);
+  set_word_kernel<<<1, 1, 0, st>>>(scratch + kMaxPasses * kBins, first_ticket);
+  radix_sort(kin, vin, nullptr, n, n, 8, scratch, err, 0, true, st, spin_limit);
+  return cudaGetLastError();
+}
 
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   BinPlan p;
@@ -812,7 +906,7 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
 }
 
 cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, const BinPlan& plan,
-                            char* ws, const sdgs_bins& out, cudaStream_t st) {
+                            char* ws, const sdgs_bins& out, cudaStream_t st, uint32_t inject_err) {
   const int64_t n = plan.n;
   const int tiles_x = tiles_of(v.width), tiles_y = tiles_of(v.height);
   uint32_t* dkeys[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[0]),
@@ -837,23 +931,28 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   clear.ptr[4] = n > 0 ? sort_t : nullptr; clear.words[4] = sort_scratch_bytes(plan.capacity, plan.tile_bits) / 4;
   size_t most = 0;
   for (int k = 0; k < 5; ++k) most = std::max(most, clear.ptr[k] ? clear.words[k] : 0);
-  const unsigned gc = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * 152));
+  const unsigned gc = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * (size_t)device_sm_count()));
   cudaError_t e = launch_pdl(clear_kernel, dim3(gc), dim3(256), 0, st, clear);
+  if (e == cudaSuccess && inject_err != 0u) {  // test support: as if a pass had given up waiting
+    set_word_kernel<<<1, 1, 0, st>>>(err, inject_err);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || n == 0) return e;
-  const unsigned gb = (unsigned)((n + kRadixThreads - 1) / kRadixThreads);
+  const unsigned gb = (unsigned)std::min<int64_t>((n + kRadixThreads - 1) / kRadixThreads, 2 * device_sm_count());
   // 1. Gaussians by float32 depth (stable; culled ones last).
   e = launch_pdl(depth_keys_kernel, dim3(gb), dim3(kRadixThreads), 0, st, proj.depth, rect, n, dkeys[0], dvals[0],
                  sort_d);
   if (e != cudaSuccess) return e;
-  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_d, err, true, st);
+  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_d, err, 0, true, st);
   const uint32_t* order = dvals[dcur];
-  // 2. Kept tiles per Gaussian (row spans); first instance of each; K.
-  uint32_t* counts = dkeys[dcur ^ 1];
-  const unsigned gs = (unsigned)((n + kSpanThreads - 1) / kSpanThreads);
-  e = launch_pdl(span_count_kernel, dim3(gs), dim3(kSpanThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
-                 counts);
+  // 2. Kept tiles per warp of 32 depth-ordered Gaussians (row spans); first instance of each warp; K.
+  uint32_t* wcount = dkeys[dcur ^ 1];
+  const int64_t nwarps = (n + 31) / 32;
+  const unsigned gw = (unsigned)((nwarps + kWalkWarps - 1) / kWalkWarps);
+  e = launch_pdl(walk_count_kernel, dim3(gw), dim3(kWalkThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
+                 (const uint32_t*)err, wcount);
   if (e != cudaSuccess) return e;
-  e = exclusive_scan<uint32_t, uint64_t>(counts, n, first, partials, out.num_instances, st);
+  e = exclusive_scan<uint32_t, uint64_t>(wcount, nwarps, first, partials, out.num_instances, st);
   if (e != cudaSuccess) return e;
   // 3. Instances in depth order, into the buffer that makes the tile passes end in `out`.
   const int passes = radix_pass_count(plan.tile_bits);
@@ -867,17 +966,16 @@ cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, cons
   } else {
     ikeys[0] = wk0; ivals[0] = wv0; ikeys[1] = out_keys; ivals[1] = out.point_list;
   }
-  const bool vec = ((reinterpret_cast<uintptr_t>(ikeys[0]) | reinterpret_cast<uintptr_t>(ivals[0])) & 15u) == 0;
-  e = launch_pdl(span_emit_kernel, dim3(gs), dim3(kSpanThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
-                 (const uint64_t*)first, (const uint32_t*)counts, plan.capacity, ikeys[0], ivals[0], vec, passes,
-                 radix_digit_width(plan.tile_bits), sort_t);
+  e = launch_pdl(walk_emit_kernel, dim3(gw), dim3(kWalkThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
+                 (const uint64_t*)first, plan.capacity, ikeys[0], ivals[0], passes,
+                 radix_digit_width(plan.tile_bits), (const uint32_t*)err, sort_t);
   if (e != cudaSuccess) return e;
   // 4. Stable sort by tile id; 5. tile ranges.
-  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_t, err, true, st);
+  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_t, err, kMaxPasses, true, st);
   {
-    const unsigned gr = (unsigned)((plan.num_tiles + 7) / 8);  // 8 warps per block, one per tile
-    e = launch_pdl(ranges_kernel, dim3(gr), dim3(256), 0, st, (const uint32_t*)out_keys,
-                   (const int64_t*)out.num_instances, plan.capacity, (int)plan.num_tiles,
+    const unsigned gr = (unsigned)((plan.num_tiles + kRangeTiles - 1) / kRangeTiles);
+    e = launch_pdl(ranges_kernel, dim3(gr), dim3((kRangeTiles + 1) * 32), 0, st, (const uint32_t*)out_keys,
+                   out.num_instances, plan.capacity, (int)plan.num_tiles, (const uint32_t*)err,
                    reinterpret_cast<uint2*>(out.ranges));
     if (e != cudaSuccess) return e;
   }

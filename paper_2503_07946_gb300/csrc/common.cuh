@@ -47,6 +47,9 @@ int cuda_status(cudaError_t e, const char* what);
 
 inline int tiles_of(int px) { return (px + kTile - 1) / kTile; }
 
+// Multiprocessor count of the current device (cached per device), for grid sizing.
+int device_sm_count();
+
 // Internal launchers (one .cu each).
 cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o,
                                  cudaStream_t st);
@@ -68,14 +71,21 @@ struct BinPlan {
   int64_t partial_cap;  // entries available for scan partials
 };
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);
+// inject_err != 0 (test support only) starts the sort's error word at that value.
 cudaError_t launch_bin_sort(const sdgs_projected& p, const sdgs_view& v, const BinPlan& plan,
-                            char* ws, const sdgs_bins& out, cudaStream_t st);
+                            char* ws, const sdgs_bins& out, cudaStream_t st, uint32_t inject_err = 0);
+size_t lookback_selftest_bytes(int64_t n);
+cudaError_t launch_lookback_selftest(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
+                                     uint32_t* vals_out, int64_t n, uint32_t first_ticket, int spin_limit, char* ws,
+                                     uint32_t** err_out, cudaStream_t st);
 
 cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const sdgs_view& v,
                               float* image, float* final_T, uint32_t* n_contrib,
                               uint64_t* n_evaluated, cudaStream_t st);
 
 size_t bwd_workspace_bytes(int64_t n);
+int64_t alu_probe_sink_len();
+cudaError_t launch_alu_probe(int kind, int iters, float* sink, double* ops, cudaStream_t st);
 cudaError_t launch_densify(const sdgs_scene& s, const sdgs_view& v, const sdgs_densify_cfg& cfg,
                            const sdgs_densify& out, cudaStream_t st);
 size_t agr_bwd_workspace_bytes(int64_t n);

@@ -20,11 +20,12 @@ struct FwdArgs {
   const uint32_t* point_list;
   const uint2* ranges;
   int width, height, tiles_x;
+  uint32_t n;  // Gaussians in the records; a list entry >= n (never written by binning) is skipped
   float bg[3];
   float* image;
   float* final_T;
   uint32_t* n_contrib;
-  unsigned long long* n_evaluated;  // optional work counter
+  unsigned long long* n_evaluated;  // optional work counters: [0] evaluations, [1] contributions
 };
 
 // The two pixels of a thread (rows r and r + 8 of one column) as pairs, so that the arithmetic
@@ -33,7 +34,7 @@ struct FwdArgs {
 struct PixelPair {
   float2 T = make_float2(1.f, 1.f), c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f),
          c2 = make_float2(0.f, 0.f);
-  uint32_t last0 = 0, last1 = 0, evaluated = 0;
+  uint32_t last0 = 0, last1 = 0, evaluated = 0, contributed = 0;
   bool done0, done1;
 };
 
@@ -57,7 +58,10 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
   const bool hit1 = !px.done1 && p2.y <= 0.f && al.y >= kAlphaMin;
   const bool stop0 = hit0 && Tn.x < kTMin, stop1 = hit1 && Tn.y < kTMin;
   const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
-  if (kCount) px.evaluated += (px.done0 ? 0u : 1u) + (px.done1 ? 0u : 1u);
+  if (kCount) {
+    px.evaluated += (px.done0 ? 0u : 1u) + (px.done1 ? 0u : 1u);
+    px.contributed += (take0 ? 1u : 0u) + (take1 ? 1u : 0u);
+  }
   const float2 w = make_float2(take0 ? aT.x : 0.f, take1 ? aT.y : 0.f);
   px.c0 = __ffma2_rn(make_float2(c.x, c.x), w, px.c0);
   px.c1 = __ffma2_rn(make_float2(c.y, c.y), w, px.c1);
@@ -96,9 +100,15 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
     const int j = base + threadIdx.x;
     if (j < n) {
       const uint32_t g = a.point_list[range.x + j];
-      s_xy[threadIdx.x] = a.mean2d[g];
-      s_q[threadIdx.x] = scaled_conic(a.conic_opacity[g]);
-      s_rgb[threadIdx.x] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
+      if (g < a.n) {
+        s_xy[threadIdx.x] = a.mean2d[g];
+        s_q[threadIdx.x] = scaled_conic(a.conic_opacity[g]);
+        s_rgb[threadIdx.x] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
+      } else {  // opacity 0: every pixel skips it
+        s_xy[threadIdx.x] = make_float2(0.f, 0.f);
+        s_q[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_rgb[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     const int cnt = min(kThreads, n - base);
     __syncthreads();
@@ -132,10 +142,14 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
     }
   }
   if (kCount) {
-    unsigned long long e = (unsigned long long)pp.evaluated;
+    unsigned long long e = (unsigned long long)pp.evaluated, c = (unsigned long long)pp.contributed;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
     if (lane == 0 && e) atomicAdd(a.n_evaluated, e);
+    if (lane == 0 && c) atomicAdd(a.n_evaluated + 1, c);
   }
   const float Ts[2] = {pp.T.x, pp.T.y};
   const float C0[2] = {pp.c0.x, pp.c0.y}, C1[2] = {pp.c1.x, pp.c1.y}, C2[2] = {pp.c2.x, pp.c2.y};
@@ -168,6 +182,7 @@ cudaError_t launch_render_fwd(const sdgs_projected& p, const sdgs_bins& b, const
   a.width = v.width;
   a.height = v.height;
   a.tiles_x = tiles_of(v.width);
+  a.n = (uint32_t)p.n;
   for (int c = 0; c < 3; ++c) a.bg[c] = v.bg[c];
   a.image = image;
   a.final_T = final_T;

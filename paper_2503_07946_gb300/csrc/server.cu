@@ -113,11 +113,14 @@ struct DoneArg {
   int slot;
 };
 
+// Largest instance capacity of a request: the binning sort's status words count in 30 bits.
+constexpr int64_t kMaxCapacity = (int64_t(1) << 30) - 1;
+
 int64_t capacity_estimate(const sdgs_server* s, int32_t scene, const sdgs_view& v) {
   const double px = (double)v.width * v.height;
   const double per = s->k_per_px[scene] > 0 ? s->k_per_px[scene] * 1.25 : 40.0;
   const double k = std::max(4096.0, per * px);
-  return (int64_t)std::min(k, (double)((int64_t(1) << 31) - 1));
+  return (int64_t)std::min(k, (double)kMaxCapacity);
 }
 
 size_t request_bytes(const sdgs_scene& sc, const sdgs_view& v, int64_t cap) {
@@ -275,15 +278,30 @@ void reap(sdgs_server* s) {
     Request* r = sl.req;
     const int64_t k = *sl.pinned_k;
     const double px = (double)r->view.width * r->view.height;
-    s->k_per_px[r->scene] = std::max(s->k_per_px[r->scene], (double)k / px);
-    if (k > r->capacity) {  // grow the instance lists and bin + composite again
-      r->capacity = std::min<int64_t>((int64_t)(k * 1.1) + 4096, (int64_t(1) << 31) - 1);
+    if (k >= 0) s->k_per_px[r->scene] = std::max(s->k_per_px[r->scene], (double)k / px);
+    if (k < 0) {  // a bounded wait of the binning sort gave up: the image holds only the background
+      set_error("request %llu: binning gave up waiting", (unsigned long long)r->id);
+      fail_request(s, r, SDGS_ERR_TIMEOUT);
+    } else if (k > kMaxCapacity) {
+      set_error("request %llu: %lld instances exceed the largest capacity", (unsigned long long)r->id, (long long)k);
+      fail_request(s, r, SDGS_ERR_OVERFLOW);
+    } else if (k > r->capacity) {  // grow the instance lists and bin + composite again
+      r->capacity = std::min<int64_t>((int64_t)(k * 1.1) + 4096, kMaxCapacity);
       s->stats.retried++;
-      cudaError_t e = ensure_slot(s, sl, s->scenes[r->scene], r->view, r->capacity);
-      if (e == cudaSuccess) e = enqueue_tail(s, i);
-      if (e == cudaSuccess) continue;
-      set_error("server retry: %s", cudaGetErrorString(e));
-      fail_request(s, r, SDGS_ERR_CUDA);
+      const size_t growth = slot_growth(sl, s->scenes[r->scene], r->view, r->capacity);
+      if (s->bytes_allocated + growth <= s->cfg.hbm_budget_bytes) {
+        cudaError_t e = ensure_slot(s, sl, s->scenes[r->scene], r->view, r->capacity);
+        if (e == cudaSuccess) e = enqueue_tail(s, i);
+        if (e == cudaSuccess) continue;
+        set_error("server retry: %s", cudaGetErrorString(e));
+        fail_request(s, r, SDGS_ERR_CUDA);
+      } else {
+        // the larger lists do not fit beside the other slots now: back to the head of the queue,
+        // where admission waits for memory as it does for a new request
+        r->state = SDGS_REQ_QUEUED;
+        r->slot = -1;
+        s->queue.push_front(r);
+      }
     } else {
       r->state = SDGS_REQ_DONE;
       r->t_done = Clock::time_point(Clock::duration(s->finished_at[i].load()));

@@ -77,6 +77,9 @@ class Renderer:
         self._k_event = None
         k = int(self._k_host[0])
         self.num_instances = k
+        if k < 0:  # a bounded wait inside the binning sort gave up: that frame's lists were empty
+            raise RuntimeError("binning of the previous frame failed (a sort wait gave up); "
+                               "its image holds only the background")
         if k <= self._k_capacity:
             return False
         self.overflowed_frames += 1

@@ -100,8 +100,17 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sdgs_bin_sort": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p, ctypes.c_size_t,
                        ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
+    "sdgs_bin_sort_failure_selftest": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p,
+                                        ctypes.c_size_t, ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.c_void_p], ctypes.c_int),
     "sdgs_bin_sort_static": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.POINTER(Bins),
                               ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
+    "sdgs_alu_peak_probe": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
+    "sdgs_lookback_selftest_workspace_size": ([ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sdgs_lookback_selftest": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p],
+                               ctypes.c_int),
     "sdgs_render_fwd": ([ctypes.POINTER(Projected), ctypes.POINTER(Bins), ctypes.POINTER(View),
                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                         ctypes.c_int),
@@ -283,6 +292,17 @@ def bin_sort(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = 
     return int(k.value) if sync else None
 
 
+def bin_sort_failure_selftest(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = True,
+                              stream=None):
+    """sdgs_bin_sort_failure_selftest: bin_sort with its sort's first pass marked as having given up
+    (test support for the failure path)."""
+    k = ctypes.c_int64(0)
+    _check(lib().sdgs_bin_sort_failure_selftest(ctypes.byref(proj.struct()), ctypes.byref(view), _ptr(bins.workspace),
+                                                bins.ws_bytes, ctypes.byref(bins.struct()),
+                                                ctypes.byref(k) if sync else None, _stream(stream)))
+    return int(k.value) if sync else None
+
+
 STATIC_BIN_SCRATCH_BYTES = 64 << 20
 
 
@@ -299,9 +319,32 @@ def bin_sort_static(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: 
     return int(k.value) if sync else None
 
 
+def alu_peak_probe(kind: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """sdgs_alu_peak_probe: enqueue one probe launch (0 FFMA, 1 paired FFMA, 2 MUFU ex2); returns
+    the operations it performs (FLOP or ex2 evaluations)."""
+    ops = ctypes.c_double(0.0)
+    _check(lib().sdgs_alu_peak_probe(kind, iters, _ptr(sink), sink.numel(), ctypes.byref(ops), _stream(stream)))
+    return float(ops.value)
+
+
+def lookback_selftest(keys: torch.Tensor, vals: torch.Tensor, keys_out: torch.Tensor, vals_out: torch.Tensor,
+                      n: int, first_ticket: int, spin_limit: int, stream=None):
+    """sdgs_lookback_selftest: one 8-bit radix pass of the binning sort with its block tickets
+    starting at first_ticket (test support for the sort's bounded waits).  Raises
+    SdgsError(TIMEOUT) when a wait gave up."""
+    b = ctypes.c_size_t(0)
+    _check(lib().sdgs_lookback_selftest_workspace_size(n, ctypes.byref(b)))
+    ws = torch.empty(max(int(b.value), 256), dtype=torch.uint8, device=keys.device)
+    _check(lib().sdgs_lookback_selftest(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n, first_ticket,
+                                        spin_limit, _ptr(ws), int(b.value), _stream(stream)))
+
+
 def render_fwd(proj: ProjectedBuffers, bins: BinBuffers, view: View, image: torch.Tensor,
                final_T: torch.Tensor, n_contrib: torch.Tensor, n_evaluated: torch.Tensor | None = None,
                stream=None):
+    """n_evaluated: optional device int64 [2]; (evaluated, blended) (pixel, Gaussian) pairs are added."""
+    if n_evaluated is not None and n_evaluated.numel() < 2:
+        raise ValueError("n_evaluated needs 2 int64 elements (evaluations, contributions)")
     _check(lib().sdgs_render_fwd(ctypes.byref(proj.struct()), ctypes.byref(bins.struct()), ctypes.byref(view),
                                  _ptr(image), _ptr(final_T), _ptr(n_contrib), _ptr(n_evaluated),
                                  _stream(stream)))

@@ -112,3 +112,34 @@ def test_new_entry_points_reject_invalid_arguments_before_any_gpu_work(lib):
     v.width = v.height = 65535 * 16
     rc = lib.sdgs_bin_workspace_size(10, 10, v.width, v.height, ctypes.byref(b))
     assert rc == 1
+
+
+def test_failure_test_support_rejects_invalid_arguments_before_any_gpu_work(lib):
+    b = ctypes.c_size_t(0)
+    assert lib.sdgs_lookback_selftest_workspace_size(4096, ctypes.byref(b)) == 0 and b.value > 0
+    assert lib.sdgs_lookback_selftest_workspace_size(-1, ctypes.byref(b)) == 1
+    for n, ticket, spins in ((-1, 1, 100), (4096, (1 << 20) + 1, 100), (4096, 1, 0), (4096, 1, (1 << 20) + 1)):
+        rc = lib.sdgs_lookback_selftest(None, None, None, None, n, ticket, spins, None, 0, None)
+        assert rc == 1 and b"selftest" in lib.sdgs_last_error(), (n, ticket, spins)
+    rc = lib.sdgs_lookback_selftest(None, None, None, None, 4096, 1, 100, None, 0, None)
+    assert rc == 1 and b"NULL" in lib.sdgs_last_error()
+    rc = lib.sdgs_bin_sort_failure_selftest(None, None, None, 0, None, None, None)
+    assert rc == 1 and b"projected" in lib.sdgs_last_error()
+
+
+def test_deferred_renderer_raises_when_the_previous_frame_failed():
+    """A negative instance count read back behind a frame means its binning gave up (its lists
+    were left empty): the next forward reports it instead of rendering on."""
+    import torch
+    from paper_2503_07946_gb300 import render as prender
+
+    class _Done:
+        def synchronize(self):
+            pass
+
+    r = object.__new__(prender.Renderer)
+    r._k_event, r._k_host, r._k_capacity, r.overflowed_frames = _Done(), torch.tensor([-1]), 1000, 0
+    with pytest.raises(RuntimeError, match="failed"):
+        r.check_deferred()
+    r._k_event, r._k_host = _Done(), torch.tensor([500])
+    assert r.check_deferred() is False and r.num_instances == 500
