@@ -31,10 +31,11 @@ import synth  # noqa: E402
 
 METRIC = "Mpix/s & FPS at 800×800/300k Gaussians; fwd+bwd it/s; p50/p99 serving latency"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# Source-level FP32 work of one (pixel, Gaussian) evaluation in the compositing loop: offsets (2),
-# exponent (8), opacity clamp (2), tests (2), transmittance (2), weight (1), colour FMAs (6) = 23
-# FLOP (an FMA counts 2) plus one exp2 on the MUFU pipe.
-FLOP_PER_EVAL = 23
+# FP32 work of compositing (the survey's count): 15 FLOP per evaluated (pixel, Gaussian) pair
+# (offsets, exponent, opacity clamp and tests, transmittance) plus one ex2, and 3 FMA = 6 FLOP per
+# blended pair (the colour update).  The counting variant of render_fwd counts both kinds of pair.
+FLOP_PER_EVAL = 15
+FLOP_PER_CONTRIB = 6
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one
 # `ncu --set full` capture of render_fwd_kernel.  Set to None whenever render_fwd_kernel changes
 # until it is captured again.
@@ -51,9 +52,29 @@ def load_peaks() -> dict:
         return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
 
-def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
-    """FP32 FMA peak: SMs x 128 lanes x 2 FLOP x clock."""
-    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+def measure_alu_peaks(dev, iters: int = 4096) -> dict:
+    """FP32 and MUFU ex2 peaks of this GPU, measured: one launch of each throughput probe of
+    libsdgs (scalar FFMA, paired FFMA2, ex2.approx; 64 warps per SM, independent chains), timed
+    with CUDA events after a warm-up launch.  FP32 TFLOP/s is the faster of the two FMA forms."""
+    from paper_2503_07946_gb300 import sdgs
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float32, device=dev)
+    out = {}
+    for kind, name in ((0, "ffma_tflops"), (1, "ffma2_tflops"), (2, "ex2_tera_per_s")):
+        sdgs.alu_peak_probe(kind, 64, sink)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = sdgs.alu_peak_probe(kind, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            rate = ops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            best = rate if best is None else max(best, rate)
+        out[name] = best
+    out["fp32_tflops"] = max(out["ffma_tflops"], out["ffma2_tflops"])
+    out["sms"] = sms
+    return out
 
 
 class ClockSampler:
@@ -110,69 +131,193 @@ class ClockSampler:
 # Reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------------------------
 
-def oracle_frame_estimate(scene, cam, tiles_sample: int, seed: int, gauss_frac: float = 1.0) -> dict:
-    """Time the oracle on one view: the per-Gaussian stage plus `tiles_sample` random tiles of
-    compositing, extrapolated to the full frame.  With gauss_frac < 1 both run on that fraction of
-    the Gaussians and their times are scaled by 1 / gauss_frac (both are linear in N)."""
-    from oracle import composite
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+ORACLE_KEYS = ("mean2d", "conic", "alpha_cond", "rgb", "depth", "rect")
+_WORKER = {}
+
+
+def _oracle_worker_init(shm_name: str, n: int, cfg: int):
+    """Pool worker: one torch thread; maps the per-Gaussian records from shared memory."""
+    from multiprocessing import shared_memory
+    torch.set_num_threads(1)
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _WORKER.update(shm=shm, n=n, cams=synth.config_cameras(cfg))
+
+
+def _oracle_records(buf, n: int) -> dict:
+    cols = {"mean2d": 2, "conic": 3, "alpha_cond": 1, "rgb": 3, "depth": 1, "rect": 4}
+    out, off = {}, 0
+    for k in ORACLE_KEYS:
+        dt = np.int64 if k == "rect" else np.float64
+        a = np.ndarray((n, cols[k]) if cols[k] > 1 else (n,), dtype=dt, buffer=buf, offset=off)
+        out[k] = a
+        off += a.nbytes
+    return out
+
+
+def _oracle_tiles(job) -> int:
+    """Composites whole tiles of camera cam_index from the shared records (the oracle as it stands:
+    render_pixels over the rectangle lists); returns the pixels done."""
     from oracle import render as orender
-    m = scene.n if gauss_frac >= 1.0 else max(1, int(scene.n * gauss_frac))
-    sc = scene if m == scene.n else scene.subset(np.arange(m))
-    scale = scene.n / m
-    t0 = time.perf_counter()
-    g = orender.gaussians(orender.params_from_scene(sc), cam, scene.lambda_t, scene.lambda_d)
-    t_g = (time.perf_counter() - t0) * scale
-    rng = np.random.default_rng(seed)
+    cam_index, tiles = job
+    cam = _WORKER["cams"][cam_index]
+    g = {k: torch.as_tensor(v) for k, v in _oracle_records(_WORKER["shm"].buf, _WORKER["n"]).items()}
+    pix = []
+    for t in tiles:
+        tx, ty = t % cam.tiles_x, t // cam.tiles_x
+        ys, xs = np.meshgrid(np.arange(ty * 16, min(ty * 16 + 16, cam.height)),
+                             np.arange(tx * 16, min(tx * 16 + 16, cam.width)), indexing="ij")
+        pix.append(np.stack([ys.reshape(-1), xs.reshape(-1)], 1))
+    pix = np.concatenate(pix)
+    orender.render_pixels(g, cam, pix)
+    return int(len(pix))
+
+
+class OracleFrames:
+    """The FP64 oracle on the host cores: its per-Gaussian stage (slicing, projection, SH, tile
+    rectangles) in this process with torch's threads, then the compositing of whole 16x16 tiles
+    spread over a spawn pool of one process per core, the records shared through shared memory."""
+
+    def __init__(self, cfg: int, procs: int | None = None):
+        from multiprocessing import get_context, shared_memory
+        self.cfg = cfg
+        self.scene = synth.config_scene(cfg)
+        self.cams = synth.config_cameras(cfg)
+        self.procs = procs or os.cpu_count() or 1
+        n = self.scene.n
+        nbytes = n * 8 * (2 + 3 + 1 + 3 + 1 + 4)
+        self.shm = shared_memory.SharedMemory(create=True, size=nbytes)
+        self.pool = get_context("spawn").Pool(self.procs, initializer=_oracle_worker_init,
+                                              initargs=(self.shm.name, n, cfg))
+        self.pool.map(int, range(self.procs))  # wait for the workers to start
+
+    def stage(self, cam_index: int) -> float:
+        from oracle import render as orender
+        t0 = time.perf_counter()
+        cam = self.cams[cam_index]
+        g = orender.gaussians(orender.params_from_scene(self.scene), cam, self.scene.lambda_t, self.scene.lambda_d)
+        recs = _oracle_records(self.shm.buf, self.scene.n)
+        for k in ORACLE_KEYS:
+            v = g[k].detach().numpy()
+            recs[k][...] = v.reshape(recs[k].shape)
+        return time.perf_counter() - t0
+
+    def tiles(self, cam_index: int, tiles) -> tuple[int, float]:
+        t0 = time.perf_counter()
+        tiles = list(tiles)
+        jobs = [(cam_index, tiles[i::self.procs * 2]) for i in range(self.procs * 2)]
+        pixels = sum(self.pool.map(_oracle_tiles, [j for j in jobs if j[1]]))
+        return pixels, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+        self.shm.close()
+        self.shm.unlink()
+
+
+def oracle_sample(frames: OracleFrames, cam_index: int, n_tiles: int, seed: int) -> dict:
+    """One bounded sample: the per-Gaussian stage for every Gaussian plus n_tiles random whole tiles,
+    both measured; `frame_s_estimate` scales the tiles' time to the whole frame."""
+    cam = frames.cams[cam_index]
     ntiles = cam.tiles_x * cam.tiles_y
-    tiles = rng.choice(ntiles, size=tiles_sample, replace=False)
-    bg = torch.as_tensor(cam.bg, dtype=torch.float64)
-    t1 = time.perf_counter()
-    rect, depth = g["rect"], g["depth"]
-    for tile in tiles:
-        tx, ty = int(tile % cam.tiles_x), int(tile // cam.tiles_x)
-        inside = (rect[:, 0] <= tx) & (tx < rect[:, 2]) & (rect[:, 1] <= ty) & (ty < rect[:, 3])
-        ids = torch.nonzero(inside).reshape(-1)
-        order = np.lexsort((ids.numpy(), depth[ids].numpy()))
-        cand = ids[torch.as_tensor(order, dtype=torch.int64)]
-        pix, _ = orender.pixel_centres(cam, int(tile))
-        composite.composite_tile(pix, cand, g["mean2d"], g["conic"], g["alpha_cond"], g["rgb"], bg)
-    t_t = (time.perf_counter() - t1) * scale
-    frame_s = t_g + t_t * ntiles / tiles_sample
-    return dict(frame_s=frame_s, t_gauss=t_g, t_tiles=t_t, tiles=tiles_sample, gauss_frac=m / scene.n)
+    t_stage = frames.stage(cam_index)
+    tiles = np.random.default_rng(seed).choice(ntiles, size=min(n_tiles, ntiles), replace=False)
+    pixels, t_tiles = frames.tiles(cam_index, tiles)
+    return dict(stage_s=t_stage, tiles_s=t_tiles, pixels=pixels, tiles=len(tiles), step_s=t_stage + t_tiles,
+                frame_s_estimate=t_stage + t_tiles * ntiles / len(tiles))
 
 
 def run_reference(args, rank: int, world: int):
+    """The reference arm: the oracle on the host cores, on our arm's workload.  Each step is one
+    measured bounded sample of a config-1 frame (the next orbit camera): the per-Gaussian stage of
+    all 300k Gaussians plus 4 whole tiles per host core; the value is the pixels composited per
+    second of step time (the per-Gaussian stage included), so ms_per_step is the measured step."""
     if rank != 0:
         return
-    scene = synth.config_scene(1)
-    cams = synth.config_cameras(1)
-    cores = torch.get_num_threads()
-    times = []
-    total = args.warmup + args.steps
-    budget_s = 150.0  # keep the whole reference run within a few minutes
-    frac = 1.0
-    for i in range(total):
-        t0 = time.perf_counter()
-        est = oracle_frame_estimate(scene, cams[i % len(cams)], tiles_sample=2, seed=i, gauss_frac=frac)
-        step_s = time.perf_counter() - t0
-        if i == 0 and step_s * total > budget_s:
-            frac = max(0.02, budget_s / (step_s * total))
-        if i >= args.warmup:
-            times.append(est["frame_s"])
-    frame_s = float(np.mean(times))
-    mpix = 800 * 800 / frame_s / 1e6
-    sample = ("per step: the oracle's per-Gaussian stage plus compositing of 2 random 16x16 tiles of one "
-              "800x800 view, extrapolated to the 2500-tile frame; run on %.0f%% of the 300k Gaussians "
-              "with times scaled by N/m" % (100 * frac))
+    frames = OracleFrames(1)
+    cores = frames.procs
+    try:
+        steps = []
+        for i in range(args.warmup + args.steps):
+            r = oracle_sample(frames, i % len(frames.cams), 4 * cores, seed=i)
+            if i >= args.warmup:
+                steps.append(r)
+    finally:
+        frames.close()
+    step_s = float(np.mean([r["step_s"] for r in steps]))
+    mpix = float(np.mean([r["pixels"] for r in steps])) / step_s / 1e6
+    est = float(np.mean([r["frame_s_estimate"] for r in steps]))
+    sample = ("per step, measured: the oracle's per-Gaussian stage for all 300k Gaussians (%.2f s) plus "
+              "compositing of %d random whole 16x16 tiles of one 800x800 view over %d processes (%.2f s)"
+              % (np.mean([r["stage_s"] for r in steps]), steps[0]["tiles"], cores,
+                 np.mean([r["tiles_s"] for r in steps])))
     line = {"impl": "reference", "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "fps": 1.0 / frame_s,
+            "data": "synthetic",
             "config": {"workload": "config 1: 300k 7D Gaussians, 800x800, 100 orbit cameras",
                        "n_gaussians": 300000, "width": 800, "height": 800},
-            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "frame_s_estimate": est,
+                             "frame_mpix_s_estimate": 800 * 800 / est / 1e6},
             "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_frames_report() -> dict:
+    """Whole frames of the oracle as the measurement plan lists them: config 0 (every tile), the
+    first camera of config 1 (every tile), the FD gradient case (N = 64, 32 x 32), with the host's
+    core count and CPU model.  Long (minutes): run on its own with --oracle-frames."""
+    from oracle import render as orender
+    out = {"nproc": os.cpu_count(), "cpu_model": cpu_model(), "torch_threads": torch.get_num_threads()}
+    for cfg in (0, 1):
+        frames = OracleFrames(cfg)
+        try:
+            cam = frames.cams[0]
+            t0 = time.perf_counter()
+            t_stage = frames.stage(0)
+            pixels, t_tiles = frames.tiles(0, range(cam.tiles_x * cam.tiles_y))
+            t = time.perf_counter() - t0
+        finally:
+            frames.close()
+        out[f"config{cfg}_frame"] = {"seconds": t, "stage_s": t_stage, "composite_s": t_tiles, "pixels": pixels,
+                                     "mpix_s": pixels / t / 1e6, "processes": frames.procs,
+                                     "n_gaussians": frames.scene.n, "width": cam.width, "height": cam.height}
+    scene = synth.make_scene(64, seed=16, box=0.6)
+    cam = synth.make_camera((0.0, 0.0, -3.0), 32, 32, 60.0, 0.5, bg=(0.3, 0.3, 0.3))
+    dL = np.random.default_rng(17).normal(size=(32, 32, 3))
+    t0 = time.perf_counter()
+    orender.vjp(scene, cam, dL)
+    t_vjp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h = 1e-6
+    for k in range(8):  # central differences of 8 parameters (two renders each)
+        for sgn in (1, -1):
+            s2 = synth.Scene(scene.mean7.astype(np.float64), scene.L28.astype(np.float64), scene.opacity.copy(),
+                             scene.sh, scene.lambda_t, scene.lambda_d, scene.bg)
+            s2.mean7.reshape(-1)[k] += sgn * h
+            orender.render(s2, cam)
+    t_fd = (time.perf_counter() - t0) / 16
+    out["fd_case"] = {"vjp_s": t_vjp, "render_s": t_fd, "n_gaussians": 64, "width": 32, "height": 32}
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -190,13 +335,23 @@ def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
     return 1 + 1 + 1 + 4 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
 
 
-def cpu_baseline(scene, cam) -> dict:
-    est = oracle_frame_estimate(scene, cam, tiles_sample=4, seed=0)
-    return {"value": 800 * 800 / est["frame_s"] / 1e6, "unit": "Mpix/s", "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": ("the oracle's per-Gaussian stage for all 300k Gaussians (%.1f s) plus compositing of 4 "
-                       "random 16x16 tiles (%.1f s) of camera 0, extrapolated to the 2500-tile frame"
-                       % (est["t_gauss"], est["t_tiles"]))}
+def cpu_baseline(cam_index: int) -> dict:
+    """The oracle on the host cores, timed on one whole frame of the headline workload (config 1,
+    800x800, 300k Gaussians): its per-Gaussian stage, then all 2500 tiles composited over one
+    process per core (about 25 s on 16 cores)."""
+    frames = OracleFrames(1)
+    try:
+        cam = frames.cams[cam_index]
+        t_stage = frames.stage(cam_index)
+        pixels, t_tiles = frames.tiles(cam_index, range(cam.tiles_x * cam.tiles_y))
+    finally:
+        frames.close()
+    t = t_stage + t_tiles
+    return {"value": pixels / t / 1e6, "unit": "Mpix/s", "cores": frames.procs, "kind": "oracle",
+            "cpu_model": cpu_model(), "measured_s": t,
+            "sample": ("one whole 800x800 frame of config 1 (orbit camera %d), measured: the oracle's per-Gaussian "
+                       "stage for all 300k Gaussians (%.2f s) plus compositing of all 2500 tiles over %d processes "
+                       "(%.2f s)" % (cam_index, t_stage, frames.procs, t_tiles))}
 
 
 def replica_order(rank: int, n_cams: int, count: int) -> list[int]:
@@ -246,7 +401,7 @@ def run_ours(args, rank: int, world: int):
     del sizing
     r = prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    n_eval = torch.zeros(1, dtype=torch.int64, device=dev)
+    n_eval = torch.zeros(2, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(v, ev=None):
@@ -301,7 +456,7 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     step_ms = phase.sum(1)
     ms = max_over_ranks(float(step_ms.mean()), world, dev)
-    evals = int(n_eval.item())
+    evals, contribs = (int(x) for x in n_eval.tolist())
     k_inst = int(r.bins.num_instances.item())
     visible = int(((r.proj.rect[:, 2] > r.proj.rect[:, 0]) & (r.proj.rect[:, 3] > r.proj.rect[:, 1])).sum())
 
@@ -352,10 +507,13 @@ def run_ours(args, rank: int, world: int):
     pix = W * H
     value = job_mpix_s(world, pix, ms)
     raster_ms = float(phase[:, 2].mean())
-    achieved_tflops = (evals / steps) * FLOP_PER_EVAL / (raster_ms * 1e-3) / 1e12
+    achieved_tflops = ((evals * FLOP_PER_EVAL + contribs * FLOP_PER_CONTRIB) / steps) / (raster_ms * 1e-3) / 1e12
     clocks = clk.summary()
-    sm_for_peak = peaks["sm_max_mhz"]
-    peak_tflops = fp32_peak_tflops(sm_for_peak)
+    with ClockSampler(dev.index) as clk_alu:
+        alu = measure_alu_peaks(dev)
+    alu["clocks"] = clk_alu.summary()
+    peak_tflops = alu["fp32_tflops"]
+    ex2_rate = (evals / steps) / (raster_ms * 1e-3) / 1e12
     slice_gbs = (scene.n * 148 + visible * (192 + 60)) / (float(phase[:, 0].mean()) * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": steps, "warmup": warm,
@@ -367,7 +525,8 @@ def run_ours(args, rank: int, world: int):
                    "l2": "flushed (256 MiB write) between steps, outside the per-step CUDA events"},
         "phases_ms": {"slice_project": float(phase[:, 0].mean()), "bin_sort": float(phase[:, 1].mean()),
                       "render_fwd": raster_ms},
-        "workload_stats": {"instances": k_inst, "visible": visible, "evaluations_per_frame": evals // steps},
+        "workload_stats": {"instances": k_inst, "visible": visible, "evaluations_per_frame": evals // steps,
+                           "contributions_per_frame": contribs // steps},
         "large_scene_frames": large,
         "pipelined_frames": pipe,
         "fwd_bwd_it_s": fb,
@@ -381,15 +540,19 @@ def run_ours(args, rank: int, world: int):
         "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
                      "traffic": RENDER_FWD_TRAFFIC_BYTES,
-                     "note": "FP32 FMA peak 152 SM x 128 lanes x 2 x %.0f MHz (max clock); %d FLOP per "
-                             "evaluated (pixel, Gaussian) pair" % (sm_for_peak, FLOP_PER_EVAL)},
+                     "peak_source": "measured (FP32 FMA probe, faster of scalar and paired forms)",
+                     "note": "%d FLOP per evaluated and %d per blended (pixel, Gaussian) pair, counted by the "
+                             "kernel's counting variant over the timed frames" % (FLOP_PER_EVAL, FLOP_PER_CONTRIB),
+                     "mufu": {"achieved": ex2_rate, "peak": alu["ex2_tera_per_s"], "unit": "T ex2/s",
+                              "frac": ex2_rate / alu["ex2_tera_per_s"]}},
+        "alu_peaks": alu,
         "slice_project_hbm": {"achieved": slice_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": slice_gbs / peaks["hbm_gbs"], "peak_source": peaks["source"]},
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene, cams[order[0]])
+        line["cpu_baseline"] = cpu_baseline(order[0])
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -698,11 +861,16 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency benchmark")
     ap.add_argument("--frames-only", action="store_true",
                     help="time the forward frames only (no e2e, fwd+bwd or CPU baseline); for profiling")
+    ap.add_argument("--oracle-frames", action="store_true",
+                    help="time whole oracle frames on the host (config 0, config 1 camera 0, the FD case); minutes")
     ap.add_argument("--fwd-bwd-only", action="store_true",
                     help="time the fwd+bwd iterations only (config 3 workload); for profiling the backward")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.oracle_frames:
+        print(json.dumps({"oracle_frames": oracle_frames_report()}), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":

@@ -52,6 +52,7 @@ class Renderer:
         self.final_T = torch.empty(height, width, dtype=torch.float32, device=device)
         self.n_contrib = torch.empty(height, width, dtype=torch.int32, device=device)
         self.num_instances = 0
+        self.frames = 0  # forwards so far: a backward needs the lists of its own frame
 
     def grow(self, k: int):
         self.bins = sdgs.BinBuffers(self.n, int(k * 1.25) + 1024, self.width, self.height, self.device,
@@ -100,6 +101,7 @@ class Renderer:
         self._k_capacity = self.bins.capacity
 
     def forward(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
+        self.frames += 1
         sdgs.slice_project(scene, view, self.proj, stream)
         if self.deferred_check:
             self._bin_deferred(view, stream)
@@ -110,6 +112,7 @@ class Renderer:
 
     def forward_async(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
         """Same three calls without the host read of the instance count (capacity must suffice)."""
+        self.frames += 1
         sdgs.slice_project(scene, view, self.proj, stream)
         sdgs.bin_sort(self.proj, view, self.bins, sync=False, stream=stream)
         sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream)
@@ -131,6 +134,7 @@ class Render7DGS(torch.autograd.Function):
         scene = sdgs.scene_struct(t, lam_t, lam_d, dir_mode)
         image = renderer.forward(scene, view).clone()
         ctx.renderer, ctx.view, ctx.lam, ctx.dir_mode = renderer, view, (lam_t, lam_d), dir_mode
+        ctx.frame = renderer.frames
         ctx.lam_device = lam.device
         ctx.final_T = renderer.final_T.clone()
         ctx.n_contrib = renderer.n_contrib.clone()
@@ -147,6 +151,10 @@ class Render7DGS(torch.autograd.Function):
         if want_lam:  # otherwise no dlambda: the kernel skips that reduction
             grads["lam"] = torch.zeros(2, dtype=torch.float32, device=mean7.device)
         r = ctx.renderer
+        if r.frames != ctx.frame:  # its projected records and tile lists now belong to a later frame
+            raise RuntimeError("Render7DGS.backward: the Renderer has rendered %d more frame(s) since this image; "
+                               "take the gradient before rendering again with it, or render each image whose "
+                               "gradient is needed with its own Renderer" % (r.frames - ctx.frame))
         ws = torch.empty(max(sdgs.bwd_workspace_size(r.n), 256), dtype=torch.uint8, device=mean7.device)
         sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, ctx.final_T, ctx.n_contrib,
                         grad_image.contiguous(), ws, grads)

@@ -100,3 +100,23 @@ def test_host_lambda_matches_device_lambda(lam_kind):
         ref = runs[0][1][k]
         # the same sums, added by atomics in another order
         assert float((g - ref).abs().max()) <= 1e-4 * float(ref.abs().max()), k
+
+
+def test_backward_after_another_forward_on_the_same_renderer_raises():
+    """The backward replays the renderer's lists of its own frame: after a second forward on the
+    same Renderer (another view, a target image) those lists are gone, so it must refuse."""
+    scene, cam = _case("small")
+    dev = prender.scene_to_device(scene)
+    params = {k: v.clone().requires_grad_(True) for k, v in dev.items()}
+    r = prender.Renderer(scene.n, cam.width, cam.height)
+    view = sdgs.view_struct(cam)
+    img = prender.render_image(params["mean7"], params["L28"], params["opacity"], params["sh"], view,
+                               scene.lambda_t, scene.lambda_d, r)
+    with torch.no_grad():
+        r.forward(sdgs.scene_struct(dev, scene.lambda_t, scene.lambda_d), view)  # e.g. a target render
+    with pytest.raises(RuntimeError, match="rendered 1 more frame"):
+        img.sum().backward()
+    img2 = prender.render_image(params["mean7"], params["L28"], params["opacity"], params["sh"], view,
+                                scene.lambda_t, scene.lambda_d, r)
+    img2.sum().backward()  # its own frame: fine
+    assert float(params["opacity"].grad.abs().sum()) > 0

@@ -44,7 +44,7 @@ def test_radix_pass_is_a_stable_sort_by_the_low_digit():
 
 @pytest.mark.parametrize("first_ticket", [1, 2])
 def test_lookback_wait_gives_up_reports_and_stays_in_bounds(first_ticket):
-    n = 4 * 1024  # four sort tiles of 1024 keys; tiles before first_ticket never run
+    n = 16 * 1024  # several sort tiles (1024-3072 keys each); tiles before first_ticket never run
     keys, kin, vin, kout, vout = _pass_inputs(n, 2)
     with pytest.raises(sdgs.SdgsError) as e:
         sdgs.lookback_selftest(kin, vin, kout, vout, n, first_ticket=first_ticket, spin_limit=2000)
