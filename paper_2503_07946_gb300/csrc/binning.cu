@@ -218,7 +218,7 @@ constexpr uint32_t kStatusAggregate = 1u << 30;  // this tile's own count of the
 constexpr uint32_t kStatusInclusive = 2u << 30;  // count of the digit in tiles 0 .. this one
 constexpr uint32_t kStatusCount = (1u << 30) - 1u;
 constexpr int kLookbackSpins = 1 << 20;
-constexpr int kLookbackWindow = 16;
+constexpr int kLookbackWindow = 8;
 constexpr int kMaxPasses = 4;
 
 __global__ void __launch_bounds__(kRadixThreads)
@@ -428,13 +428,13 @@ int radix_pass_count(int bits) {
   return k;
 }
 
-// Keys per sort block for `cap` slots: the largest tile (12, 8 or 4 keys per thread) that still
-// gives two blocks per SM, so that small sorts are not latency-bound on a few blocks.
+// Keys per sort block for `cap` slots: 12 per thread when that still gives two blocks per SM, else
+// 8.  Fewer, larger blocks shorten the look-back chains of small sorts (a 300k-key depth pass:
+// 147 blocks of 2048 keys run faster than 293 of 1024).
 int sort_items(int64_t cap) {
   const int64_t want = 2 * (int64_t)device_sm_count();
   if ((cap + 12 * kRadixThreads - 1) / (12 * kRadixThreads) >= want) return 12;
-  if ((cap + 8 * kRadixThreads - 1) / (8 * kRadixThreads) >= want) return 8;
-  return 4;
+  return 8;
 }
 
 int64_t sort_blocks(int64_t cap) {
@@ -511,7 +511,7 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
   for (int p = 0; p < passes; ++p) {
     uint32_t* stp = status + (size_t)p * nblocks * kBins;
     const int shift = p * width;
-    auto* kern = items == 12 ? onesweep_kernel<12> : items == 8 ? onesweep_kernel<8> : onesweep_kernel<4>;
+    auto* kern = items == 12 ? onesweep_kernel<12> : onesweep_kernel<8>;
     launch_pdl(kern, dim3((unsigned)nblocks), dim3(kRadixThreads), 0, st, keys[cur], vals[cur], keys[cur ^ 1],
                vals[cur ^ 1], nptr, n_static, cap, shift, width, hist + p * kBins, stp, tickets + p, err,
                1u << (first_pass + p), spin_limit);

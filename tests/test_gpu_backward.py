@@ -120,3 +120,52 @@ def test_backward_after_another_forward_on_the_same_renderer_raises():
                                 scene.lambda_t, scene.lambda_d, r)
     img2.sum().backward()  # its own frame: fine
     assert float(params["opacity"].grad.abs().sum()) > 0
+
+
+def test_fp32_adjoint_matches_central_differences_of_the_fp32_render():
+    """The CUDA adjoint against central differences of the CUDA forward itself (both FP32), on the
+    N = 64, 32 x 32 differentiation case: no oracle in the loop.  A parameter whose step flips a
+    discrete decision (visibility, a rectangle, the 1/255 skip, the 0.99 clamp, the stop rule)
+    shows up as a jump: its two one-sided differences disagree, and it is set aside (counted)."""
+    scene, cam = _case("small")
+    rng = np.random.default_rng(23)
+    dL = rng.normal(size=(cam.height, cam.width, 3))
+    got, _ = _gpu_grads(scene, cam, dL)
+    dev = prender.scene_to_device(scene)
+    view = sdgs.view_struct(cam)
+    r = prender.Renderer(scene.n, cam.width, cam.height)
+    dLt = torch.as_tensor(dL, dtype=torch.float64)
+
+    def loss(t):
+        st = sdgs.scene_struct(t, scene.lambda_t, scene.lambda_d)
+        img = r.forward(st, view).double().cpu()
+        return float((img * dLt).sum())
+
+    base = loss(dev)
+    vis = (r.proj.rect[:, 2] > r.proj.rect[:, 0]).cpu().numpy()
+    checked = jumps = 0
+    worst = 0.0
+    for name in ("mean7", "L28", "opacity", "sh"):
+        flat = dev[name].reshape(-1)
+        per = flat.numel() // scene.n
+        g = got[name].reshape(-1)
+        scale = float(np.abs(g).max())
+        cand = [i for i in rng.permutation(flat.numel()) if vis[i // per]][:30]
+        for i in cand:
+            x0 = float(flat[i])
+            h = 2e-3 * max(1.0, abs(x0)) if name != "opacity" else 2e-3
+            vals = []
+            for s in (1, -1):
+                t = {k: v.clone() for k, v in dev.items()}
+                t[name].reshape(-1)[i] = x0 + s * h
+                vals.append(loss(t))
+            fwd, bwd = (vals[0] - base) / h, (base - vals[1]) / h
+            if abs(fwd - bwd) > 0.05 * max(abs(fwd), abs(bwd), 1e-3 * scale):
+                jumps += 1
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            err = abs(fd - float(g[i])) / max(abs(fd), abs(float(g[i])), 1e-2 * scale)
+            worst = max(worst, err)
+            checked += 1
+    assert checked >= 80, (checked, jumps)
+    assert worst < 0.05, worst

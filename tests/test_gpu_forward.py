@@ -61,12 +61,14 @@ def _random_bin_cases():
         (20000, 1352, 1014, 4),  # two tile passes (5440 tiles), K spans many blocks
         (3000, 1920, 1080, 5),   # 8160 tiles
         (600_000, 800, 800, 6),  # hundreds of sort tiles in both sorts
+        (16000, 48, 32, 9),      # tile lists of 8.8k-10k instances: per-tile sorts through global memory
+        (20000, 2048, 2048, 8),  # 16384 tiles: the tile radix passes of large grids
     ]
 
 
 @pytest.mark.parametrize("n,W,H,seed", _random_bin_cases())
 def test_bin_sort_bit_exact_on_random_records(n, W, H, seed):
-    rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=12 if n < 100_000 else 2)
+    rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=3 if W < 100 else (12 if n < 100_000 else 2))
     proj = U.sdgs.ProjectedBuffers.from_host(rec)
     view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5))
     okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], (W + 15) // 16,
