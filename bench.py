@@ -502,7 +502,7 @@ def run_ours(args, rank: int, world: int):
     fb_agr = fwd_bwd_its(scene, cams[0], min(steps, 200), warm, dev, agr=True)
     agr = agr_frames(scene, t_scene, views, flush, min(steps, 300), warm, dev)
     dens = densify_ms(t_scene, scene, views[0], flush, 20, dev)
-    serving = None if args.no_serving else serving_bench(dev)
+    serving = None if args.no_serving else serving_bench(dev, count=args.serve_requests)
 
     pix = W * H
     value = job_mpix_s(world, pix, ms)
@@ -582,10 +582,13 @@ def serving_trace(rate: float, count: int, seed: int, radii) -> list:
     return out
 
 
-def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: int = 8) -> dict:
-    """p50/p99 latency and Mpix/s of the render server on Poisson traces, against serving the same
-    trace one request at a time through the plain path (FIFO; the measured service times of the
-    plain path are replayed against the arrival times)."""
+def serving_bench(dev, rates=(100.0, 200.0, 500.0, 1000.0, 2000.0), count: int = 4000, slots: int = 8,
+                  budget: int = 8 << 30) -> dict:
+    """p50/p99 latency and Mpix/s of the render server on Poisson traces (the serving stream
+    workload: 4 resident scenes, 4000 requests per rate, an 8 GiB budget for per-request memory),
+    against serving the same trace one request at a time through the plain path: each request's
+    plain-path service time is measured, then replayed through a FIFO queue against the arrival
+    times (exact for a single FIFO server whose service times do not depend on arrivals)."""
     from paper_2503_07946_gb300 import render as prender
     from paper_2503_07946_gb300 import sdgs
     scenes = synth.serving_scenes()
@@ -595,7 +598,9 @@ def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: i
     bufs = {wh: [torch.empty(wh[1], wh[0], 3, dtype=torch.float32, device=dev) for _ in range(ring)]
             for wh in SERVE_SIZES}
     result = {"scenes": [s.n for s in scenes], "resolutions": SERVE_SIZES, "requests_per_rate": count,
-              "slots": slots, "output": "device buffers"}
+              "slots": slots, "budget_bytes": budget, "output": "device buffers",
+              "one_at_a_time_method": "measured plain-path service time of every request, replayed through a "
+                                      "FIFO queue against the same arrival times"}
     renderers = {}
 
     def plain(sid, cam):
@@ -608,7 +613,7 @@ def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: i
         bufs[(cam.width, cam.height)][0].copy_(img)
         torch.cuda.synchronize()
 
-    with sdgs.Server(budget_bytes=16 << 30, slots=slots) as srv:
+    with sdgs.Server(budget_bytes=budget, slots=slots) as srv:
         ids = [srv.add_scene(t, s.lambda_t, s.lambda_d) for t, s in zip(tens, scenes)]
         warm = serving_trace(100.0, 16, 99, radii)
         for _, sid, cam in warm:  # allocate slot buffers and learn instance counts
@@ -646,7 +651,8 @@ def serving_bench(dev, rates=(200.0, 1000.0, 2000.0), count: int = 200, slots: i
                 "mpix_s": pix / (done.max() - trace[0][0]) / 1e6,
                 "one_at_a_time": {"p50_ms": float(np.percentile(lat1, 50) * 1e3),
                                   "p99_ms": float(np.percentile(lat1, 99) * 1e3),
-                                  "mpix_s": pix / (finish - trace[0][0]) / 1e6}}
+                                  "mpix_s": pix / (finish - trace[0][0]) / 1e6},
+                "server_stats_so_far": srv.stats()}
         result["server_stats"] = srv.stats()
     return result
 
@@ -859,6 +865,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency benchmark")
+    ap.add_argument("--serve-requests", type=int, default=4000, help="requests per arrival rate (serving)")
     ap.add_argument("--frames-only", action="store_true",
                     help="time the forward frames only (no e2e, fwd+bwd or CPU baseline); for profiling")
     ap.add_argument("--oracle-frames", action="store_true",

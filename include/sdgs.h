@@ -193,6 +193,19 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
                   size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                   void* stream);
 
+/* Binning of `count` (1 to 8) independent problems at once: sdgs_bin_sort of each (projs[j],
+ * views[j]) into outs[j] with workspaces[j] (workspace_bytes[j] >= sdgs_bin_workspace_size of that
+ * problem), issued as one launch per binning step, each kernel serving every problem (the render
+ * server bins the requests it admits together this way).  The results are those of sdgs_bin_sort
+ * on each problem alone.  With num_instances_host (host int64[count]) the call synchronises,
+ * stores every K and returns the first problem's error if any (SDGS_ERR_OVERFLOW,
+ * SDGS_ERR_TIMEOUT); otherwise it only enqueues.  No counterpart in the paper (the serving layer).
+ * Errors: SDGS_ERR_INVALID_ARG (count outside [1, 8], a NULL array or a bad problem),
+ * SDGS_ERR_WORKSPACE, SDGS_ERR_OVERFLOW, SDGS_ERR_TIMEOUT, SDGS_ERR_CUDA. */
+int sdgs_bin_sort_batch(const sdgs_projected* projs, const sdgs_view* views, void* const* workspaces,
+                        const size_t* workspace_bytes, const sdgs_bins* outs, int32_t count,
+                        int64_t* num_instances_host, void* stream);
+
 /* sdgs_bin_sort without a workspace argument, for callers that cannot allocate device memory --
  * for example a plugin whose host application owns every device allocation, or a latency-bound
  * loop where cudaMalloc's implicit device synchronisation is not acceptable.  The paper has no

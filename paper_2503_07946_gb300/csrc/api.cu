@@ -206,6 +206,38 @@ int sdgs_bin_sort(const sdgs_projected* proj, const sdgs_view* view, void* works
   return bin_sort_impl(proj, view, workspace, workspace_bytes, out, num_instances_host, stream, 0u);
 }
 
+int sdgs_bin_sort_batch(const sdgs_projected* projs, const sdgs_view* views, void* const* workspaces,
+                        const size_t* workspace_bytes, const sdgs_bins* outs, int32_t count,
+                        int64_t* num_instances_host, void* stream) {
+  g_error[0] = 0;
+  if (count < 1 || count > kMaxBinBatch || !projs || !views || !workspaces || !workspace_bytes || !outs) {
+    set_error("bin_sort_batch: count must be in [1, %d] and the arrays non-NULL", kMaxBinBatch);
+    return SDGS_ERR_INVALID_ARG;
+  }
+  BinRequest reqs[kMaxBinBatch];
+  for (int j = 0; j < count; ++j) {
+    SDGS_TRY(check_projected(&projs[j]));
+    SDGS_TRY(check_view(&views[j]));
+    SDGS_TRY(check_bins(&outs[j]));
+    const BinPlan plan = plan_bins(projs[j].n, outs[j].capacity, views[j].width, views[j].height);
+    if (workspaces[j] == nullptr || workspace_bytes[j] < plan.total || !aligned(workspaces[j], 256)) {
+      set_error("bin_sort_batch: workspace %d needs %zu bytes, 256-byte aligned (got %zu)", j, plan.total,
+                workspace_bytes[j]);
+      return SDGS_ERR_WORKSPACE;
+    }
+    reqs[j] = BinRequest{projs[j], views[j], plan, (char*)workspaces[j], outs[j], 0u};
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  SDGS_TRY(cuda_status(launch_bin_sort_batch(reqs, count, st), "bin_sort_batch launch"));
+  if (num_instances_host == nullptr) return SDGS_OK;
+  int rc = SDGS_OK;
+  for (int j = 0; j < count; ++j) {  // (the first synchronises; the rest are complete)
+    const int r = finish_bin_sort(reqs[j].plan, reqs[j].ws, &outs[j], num_instances_host + j, st);
+    if (r != SDGS_OK && rc == SDGS_OK) rc = r;
+  }
+  return rc;
+}
+
 int sdgs_bin_sort_failure_selftest(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
                                    size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                                    void* stream) {

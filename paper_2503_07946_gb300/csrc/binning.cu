@@ -77,50 +77,93 @@ __device__ __forceinline__ T block_inclusive_scan(T x, T* total) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Batches.  Every binning kernel takes the arguments of up to kMaxBatch independent problems by
+// value (kernel parameter space, no device table) and serves problem blockIdx.y; a problem's
+// blocks past its own grid size return at once.  One problem is a batch of one.
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxBatch = kMaxBinBatch;
+
+template <typename T>
+struct Batch {
+  T a[kMaxBatch];
+};
+
+template <typename T>
+struct BatchLaunch {
+  Batch<T> b;
+  int count = 0;
+  unsigned grid = 0;  // the largest grid of the batch's problems
+  void add(const T& a) {
+    b.a[count++] = a;
+    grid = a.grid > grid ? a.grid : grid;
+  }
+};
+
+template <typename K, typename T>
+cudaError_t launch_batch(K kernel, const BatchLaunch<T>& L, unsigned threads, size_t smem, cudaStream_t st) {
+  if (L.count == 0 || L.grid == 0) return cudaSuccess;
+  return launch_pdl(kernel, dim3(L.grid, (unsigned)L.count), dim3(threads), smem, st, L.b);
+}
+
+// ------------------------------------------------------------------------------------------
 // Device-wide exclusive scan: reduce per chunk, scan the chunk sums in one block, scan chunks.
 // ------------------------------------------------------------------------------------------
 
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const TIn* in, int64_t n,
-                                                                    TOut* partials) {
+struct ScanArgs {
+  const TIn* in;
+  int64_t n;
+  TOut* out;
+  TOut* partials;
+  int64_t* total_out;  // may be NULL
+  unsigned grid;
+};
+
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const Batch<ScanArgs<TIn, TOut>> b) {
+  const ScanArgs<TIn, TOut>& a = b.a[blockIdx.y];
+  if (blockIdx.x >= a.grid) return;
   griddep_wait();
   const int64_t base = (int64_t)blockIdx.x * kScanChunk;
   TOut sum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const int64_t i = base + k * kScanThreads + threadIdx.x;
-    if (i < n) sum += (TOut)in[i];
+    if (i < a.n) sum += (TOut)a.in[i];
   }
   TOut total;
   block_inclusive_scan<TOut, kScanThreads>(sum, &total);
-  if (threadIdx.x == 0) partials[blockIdx.x] = total;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(1024) scan_partials_kernel(T* partials, int64_t nb, int64_t* total_out) {
-  griddep_wait();
-  T carry = 0;
-  for (int64_t base = 0; base < nb; base += 1024) {
-    const int64_t i = base + threadIdx.x;
-    const T x = i < nb ? partials[i] : T(0);
-    T tot;
-    const T incl = block_inclusive_scan<T, 1024>(x, &tot);
-    if (i < nb) partials[i] = carry + incl - x;
-    carry += tot;
-  }
-  if (threadIdx.x == 0 && total_out != nullptr) *total_out = (int64_t)carry;
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = total;
 }
 
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const TIn* in, int64_t n,
-                                                                  const TOut* partials, TOut* out) {
+__global__ void __launch_bounds__(1024) scan_partials_kernel(const Batch<ScanArgs<TIn, TOut>> b) {
+  const ScanArgs<TIn, TOut>& a = b.a[blockIdx.y];
+  griddep_wait();
+  const int64_t nb = (a.n + kScanChunk - 1) / kScanChunk;
+  TOut carry = 0;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const TOut x = i < nb ? a.partials[i] : TOut(0);
+    TOut tot;
+    const TOut incl = block_inclusive_scan<TOut, 1024>(x, &tot);
+    if (i < nb) a.partials[i] = carry + incl - x;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && a.total_out != nullptr) *a.total_out = (int64_t)carry;
+}
+
+template <typename TIn, typename TOut>
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const Batch<ScanArgs<TIn, TOut>> b) {
+  const ScanArgs<TIn, TOut>& a = b.a[blockIdx.y];
+  if (blockIdx.x >= a.grid) return;
   griddep_wait();
   __shared__ TOut s[kScanChunk];
   const int64_t base = (int64_t)blockIdx.x * kScanChunk;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const int j = k * kScanThreads + threadIdx.x;
-    s[j] = (base + j < n) ? (TOut)in[base + j] : TOut(0);
+    s[j] = (base + j < a.n) ? (TOut)a.in[base + j] : TOut(0);
   }
   __syncthreads();
   TOut v[kScanItems];
@@ -132,14 +175,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const TIn* in, 
   }
   TOut tot;
   const TOut incl = block_inclusive_scan<TOut, kScanThreads>(local, &tot);
-  const TOut off = partials[blockIdx.x] + incl - local;
+  const TOut off = a.partials[blockIdx.x] + incl - local;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) s[threadIdx.x * kScanItems + k] = off + v[k];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const int j = k * kScanThreads + threadIdx.x;
-    if (base + j < n) out[base + j] = s[j];
+    if (base + j < a.n) a.out[base + j] = s[j];
   }
 }
 
@@ -148,40 +191,59 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const TIn* in, 
 constexpr int kSingleScanItems = 16;
 
 template <typename TIn, typename TOut>
-__global__ void __launch_bounds__(1024) scan_single_kernel(const TIn* in, int64_t n, TOut* out, int64_t* total_out) {
+__global__ void __launch_bounds__(1024) scan_single_kernel(const Batch<ScanArgs<TIn, TOut>> b) {
+  const ScanArgs<TIn, TOut>& a = b.a[blockIdx.y];
   griddep_wait();
+  const int64_t n = a.n;
   const int64_t per = (n + 1023) / 1024;  // <= kSingleScanItems
   const int64_t base = (int64_t)threadIdx.x * per;
   TIn v[kSingleScanItems];
   TOut local = 0;
 #pragma unroll
   for (int k = 0; k < kSingleScanItems; ++k) {
-    v[k] = (k < per && base + k < n) ? in[base + k] : TIn(0);
+    v[k] = (k < per && base + k < n) ? a.in[base + k] : TIn(0);
     local += (TOut)v[k];
   }
   TOut tot;
   TOut run = block_inclusive_scan<TOut, 1024>(local, &tot) - local;
 #pragma unroll
   for (int k = 0; k < kSingleScanItems; ++k) {
-    if (k < per && base + k < n) out[base + k] = run;
+    if (k < per && base + k < n) a.out[base + k] = run;
     run += (TOut)v[k];
   }
-  if (threadIdx.x == 0 && total_out != nullptr) *total_out = (int64_t)tot;
+  if (threadIdx.x == 0 && a.total_out != nullptr) *a.total_out = (int64_t)tot;
+}
+
+// Exclusive scans of a batch of arrays (one problem each, in[i] -> out[i], total in *total_out).
+template <typename TIn, typename TOut>
+cudaError_t exclusive_scan(const ScanArgs<TIn, TOut>* jobs, int count, cudaStream_t st) {
+  BatchLaunch<ScanArgs<TIn, TOut>> small, big;
+  for (int j = 0; j < count; ++j) {
+    ScanArgs<TIn, TOut> a = jobs[j];
+    if (a.n <= (int64_t)kSingleScanItems * 1024) {
+      a.grid = 1;
+      small.add(a);
+    } else {
+      a.grid = (unsigned)((a.n + kScanChunk - 1) / kScanChunk);
+      big.add(a);
+    }
+  }
+  cudaError_t e = launch_batch(scan_single_kernel<TIn, TOut>, small, 1024, 0, st);
+  if (e == cudaSuccess) e = launch_batch(scan_reduce_kernel<TIn, TOut>, big, kScanThreads, 0, st);
+  if (e == cudaSuccess && big.count > 0) {
+    BatchLaunch<ScanArgs<TIn, TOut>> one = big;
+    one.grid = 1;
+    e = launch_batch(scan_partials_kernel<TIn, TOut>, one, 1024, 0, st);
+  }
+  if (e == cudaSuccess) e = launch_batch(scan_down_kernel<TIn, TOut>, big, kScanThreads, 0, st);
+  return e;
 }
 
 template <typename TIn, typename TOut>
-cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partials,
-                           int64_t* total_out, cudaStream_t st) {
-  if (n <= (int64_t)kSingleScanItems * 1024)
-    return launch_pdl(scan_single_kernel<TIn, TOut>, dim3(1), dim3(1024), 0, st, in, n, out, total_out);
-  const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-  TOut* part = reinterpret_cast<TOut*>(partials);
-  cudaError_t e = cudaSuccess;
-  if (nb > 0) e = launch_pdl(scan_reduce_kernel<TIn, TOut>, dim3((unsigned)nb), dim3(kScanThreads), 0, st, in, n, part);
-  if (e == cudaSuccess) e = launch_pdl(scan_partials_kernel<TOut>, dim3(1), dim3(1024), 0, st, part, nb, total_out);
-  if (e == cudaSuccess && nb > 0)
-    e = launch_pdl(scan_down_kernel<TIn, TOut>, dim3((unsigned)nb), dim3(kScanThreads), 0, st, in, n, part, out);
-  return e;
+cudaError_t exclusive_scan(const TIn* in, int64_t n, TOut* out, uint64_t* partials, int64_t* total_out,
+                           cudaStream_t st) {
+  const ScanArgs<TIn, TOut> a{in, n, out, reinterpret_cast<TOut*>(partials), total_out, 0};
+  return exclusive_scan(&a, 1, st);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -319,12 +381,41 @@ __device__ __forceinline__ uint32_t lookback(const uint32_t* status, int64_t til
   return before;
 }
 
+// One radix pass of one problem (keys_in, vals_in -> keys_out, vals_out by the digit at shift).
+struct PassArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  const int64_t* nptr;  // element count on the device (clipped to cap), or NULL for n_static
+  int64_t n_static, cap;
+  int shift, width;
+  const uint32_t* digit_hist;
+  uint32_t* status;
+  uint32_t* ticket;
+  uint32_t* err;
+  uint32_t pass_bit;
+  int spin_limit;
+  unsigned grid;
+};
+
 template <int ITEMS>
-__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 6)
-onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const int64_t* nptr,
-                int64_t n_static, int64_t cap, int shift, int width, const uint32_t* __restrict__ digit_hist,
-                uint32_t* status, uint32_t* ticket, uint32_t* err, uint32_t pass_bit, int spin_limit) {
+__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_kernel(const Batch<PassArgs> batch) {
+  const PassArgs& pa = batch.a[blockIdx.y];
+  if (blockIdx.x >= pa.grid) return;
+  const uint32_t* __restrict__ keys_in = pa.keys_in;
+  const uint32_t* __restrict__ vals_in = pa.vals_in;
+  uint32_t* __restrict__ keys_out = pa.keys_out;
+  uint32_t* __restrict__ vals_out = pa.vals_out;
+  const int64_t* nptr = pa.nptr;
+  const int64_t n_static = pa.n_static, cap = pa.cap;
+  const int shift = pa.shift, width = pa.width;
+  const uint32_t* __restrict__ digit_hist = pa.digit_hist;
+  uint32_t* status = pa.status;
+  uint32_t* ticket = pa.ticket;
+  uint32_t* err = pa.err;
+  const uint32_t pass_bit = pa.pass_bit;
+  const int spin_limit = pa.spin_limit;
   griddep_wait();
   constexpr int TILE = kRadixThreads * ITEMS;
   __shared__ uint32_t s_keys[TILE];
@@ -490,34 +581,72 @@ __device__ __forceinline__ void flush_digits(const uint32_t (*s_hist)[kBins], in
 
 // With hist_ready, the caller has cleared the scratch (sort_clear) and accumulated the digit
 // histograms of all keys into its first kMaxPasses * kBins words while producing them.
-int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_t n_static,
-               int64_t cap, int bits, uint32_t* scratch, uint32_t* err, int first_pass, bool hist_ready,
-               cudaStream_t st, int spin_limit = kLookbackSpins) {
-  int cur = 0;
-  if (cap <= 0 || bits <= 0) return cur;
-  const int width = radix_digit_width(bits);
-  const int passes = radix_pass_count(bits);
-  const int items = sort_items(cap);
-  const int64_t nblocks = sort_blocks(cap);
-  uint32_t* hist = scratch;
-  uint32_t* tickets = hist + kMaxPasses * kBins;
-  uint32_t* status = tickets + kMaxPasses;
-  if (!hist_ready) {
-    sort_clear(scratch, cap, bits, st);
-    const int64_t hist_blocks = std::min<int64_t>((cap + kRadixThreads - 1) / kRadixThreads, 4 * device_sm_count());
-    digit_hist_kernel<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys[0], nptr, n_static, cap, passes,
-                                                                       width, hist);
+// One radix sort (keys, vals ping-pong) of a batch of problems.
+struct SortJob {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  const int64_t* nptr;
+  int64_t n_static, cap;
+  int bits;
+  uint32_t* scratch;  // sort_scratch_bytes(cap, bits)
+  uint32_t* err;
+  int first_pass;     // the error bit of pass p is 1 << (first_pass + p)
+};
+
+// Sorts every job by bits [0, bits) in ceil(bits / 8) passes of equal digit width, ping-ponging
+// between buffers 0 and 1 (a job whose passes are over sits out the later launches); returns in
+// cur[j] the buffer holding job j's result.  With hist_ready the caller has cleared the scratch
+// (sort_clear) and accumulated the digit histograms of all keys into its first kMaxPasses * kBins
+// words while producing them.
+cudaError_t radix_sort(const SortJob* jobs, int count, bool hist_ready, cudaStream_t st, int* cur,
+                       int spin_limit = kLookbackSpins) {
+  int max_passes = 0;
+  for (int j = 0; j < count; ++j) {
+    cur[j] = 0;
+    if (jobs[j].cap > 0 && jobs[j].bits > 0) max_passes = std::max(max_passes, radix_pass_count(jobs[j].bits));
   }
-  for (int p = 0; p < passes; ++p) {
-    uint32_t* stp = status + (size_t)p * nblocks * kBins;
-    const int shift = p * width;
-    auto* kern = items == 12 ? onesweep_kernel<12> : onesweep_kernel<8>;
-    launch_pdl(kern, dim3((unsigned)nblocks), dim3(kRadixThreads), 0, st, keys[cur], vals[cur], keys[cur ^ 1],
-               vals[cur ^ 1], nptr, n_static, cap, shift, width, hist + p * kBins, stp, tickets + p, err,
-               1u << (first_pass + p), spin_limit);
-    cur ^= 1;
+  cudaError_t e = cudaSuccess;
+  if (!hist_ready) {  // (single jobs only: the test support path)
+    for (int j = 0; j < count && e == cudaSuccess; ++j) {
+      const SortJob& J = jobs[j];
+      if (J.cap <= 0 || J.bits <= 0) continue;
+      sort_clear(J.scratch, J.cap, J.bits, st);
+      const int64_t hist_blocks = std::min<int64_t>((J.cap + kRadixThreads - 1) / kRadixThreads, 4 * device_sm_count());
+      digit_hist_kernel<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(J.keys[0], J.nptr, J.n_static, J.cap,
+                                                                         radix_pass_count(J.bits),
+                                                                         radix_digit_width(J.bits), J.scratch);
+      e = cudaGetLastError();
+    }
   }
-  return cur;
+  for (int p = 0; p < max_passes && e == cudaSuccess; ++p) {
+    BatchLaunch<PassArgs> l12, l8;  // the two tile sizes launch separately
+    for (int j = 0; j < count; ++j) {
+      const SortJob& J = jobs[j];
+      if (J.cap <= 0 || J.bits <= 0 || p >= radix_pass_count(J.bits)) continue;
+      const int width = radix_digit_width(J.bits);
+      const int64_t nblocks = sort_blocks(J.cap);
+      uint32_t* hist = J.scratch;
+      uint32_t* tickets = hist + kMaxPasses * kBins;
+      uint32_t* status = tickets + kMaxPasses;
+      PassArgs a;
+      a.keys_in = J.keys[cur[j]]; a.vals_in = J.vals[cur[j]];
+      a.keys_out = J.keys[cur[j] ^ 1]; a.vals_out = J.vals[cur[j] ^ 1];
+      a.nptr = J.nptr; a.n_static = J.n_static; a.cap = J.cap;
+      a.shift = p * width; a.width = width;
+      a.digit_hist = hist + p * kBins;
+      a.status = status + (size_t)p * nblocks * kBins;
+      a.ticket = tickets + p;
+      a.err = J.err;
+      a.pass_bit = 1u << (J.first_pass + p);
+      a.spin_limit = spin_limit;
+      a.grid = (unsigned)nblocks;
+      (sort_items(J.cap) == 12 ? l12 : l8).add(a);
+      cur[j] ^= 1;
+    }
+    e = launch_batch(onesweep_kernel<12>, l12, kRadixThreads, 0, st);
+    if (e == cudaSuccess) e = launch_batch(onesweep_kernel<8>, l8, kRadixThreads, 0, st);
+  }
+  return e;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -530,11 +659,14 @@ int radix_sort(uint32_t* keys[2], uint32_t* vals[2], const int64_t* nptr, int64_
 struct ClearJob {
   uint32_t* ptr[5];
   size_t words[5];
+  unsigned grid;
 };
 
-__global__ void __launch_bounds__(256) clear_kernel(const ClearJob job) {
+__global__ void __launch_bounds__(256) clear_kernel(const Batch<ClearJob> b) {
+  const ClearJob& job = b.a[blockIdx.y];
+  if (blockIdx.x >= job.grid) return;
   griddep_wait();
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t stride = (size_t)job.grid * blockDim.x;
   for (int k = 0; k < 5; ++k) {
     uint32_t* p = job.ptr[k];
     if (p == nullptr) continue;
@@ -544,16 +676,32 @@ __global__ void __launch_bounds__(256) clear_kernel(const ClearJob job) {
 
 // Depth keys of the Gaussians (culled ones last) and their digit histograms for the depth sort.  A
 // few blocks per SM stride over the Gaussians, so that few block histograms are added globally.
-__global__ void __launch_bounds__(kRadixThreads)
-depth_keys_kernel(const float* __restrict__ depth, const ushort4* __restrict__ rect, int64_t n,
-                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ hist) {
+struct DepthKeysArgs {
+  const float* depth;
+  const ushort4* rect;
+  int64_t n;
+  uint32_t* keys;
+  uint32_t* vals;
+  uint32_t* hist;
+  unsigned grid;
+};
+
+__global__ void __launch_bounds__(kRadixThreads) depth_keys_kernel(const Batch<DepthKeysArgs> b) {
+  const DepthKeysArgs& a = b.a[blockIdx.y];
+  if (blockIdx.x >= a.grid) return;
+  const float* __restrict__ depth = a.depth;
+  const ushort4* __restrict__ rect = a.rect;
+  const int64_t n = a.n;
+  uint32_t* __restrict__ keys = a.keys;
+  uint32_t* __restrict__ vals = a.vals;
+  uint32_t* __restrict__ hist = a.hist;
   griddep_wait();
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * kRadixThreads;
-  for (int64_t b = (int64_t)blockIdx.x * kRadixThreads; b < n; b += stride) {  // uniform over the block
-    const int64_t i = b + threadIdx.x;
+  const int64_t stride = (int64_t)a.grid * kRadixThreads;
+  for (int64_t i0 = (int64_t)blockIdx.x * kRadixThreads; i0 < n; i0 += stride) {  // uniform over the block
+    const int64_t i = i0 + threadIdx.x;
     uint32_t k = 0;
     if (i < n) {
       const ushort4 r = rect[i];
@@ -653,10 +801,36 @@ __device__ __forceinline__ void walk_row(const WalkWarp& w, uint32_t row_incl, i
 }
 
 // Kept-tile count of each warp's 32 depth-ordered Gaussians (wcount[warp]).
-__global__ void __launch_bounds__(kWalkThreads)
-walk_count_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                  const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
-                  int tiles_x, int tiles_y, const uint32_t* err, uint32_t* __restrict__ wcount) {
+// Arguments of the span walks of one problem.
+struct WalkArgs {
+  const uint32_t* order;  // depth-ordered Gaussian ids
+  const ushort4* rect;
+  const float2* mean2d;
+  const float4* conic_opacity;
+  int64_t n;
+  int tiles_x, tiles_y;
+  const uint32_t* err;
+  uint32_t* wcount;       // count walk: kept tiles per warp chunk
+  const uint64_t* wfirst; // emit: first instance of each warp chunk
+  int64_t cap;
+  uint32_t* keys;
+  uint32_t* vals;
+  int passes, width;      // tile-digit passes whose histograms the emit accumulates into hist
+  uint32_t* hist;
+  unsigned grid;
+};
+
+__global__ void __launch_bounds__(kWalkThreads) walk_count_kernel(const Batch<WalkArgs> b) {
+  const WalkArgs& A = b.a[blockIdx.y];
+  if (blockIdx.x >= A.grid) return;
+  const uint32_t* __restrict__ order = A.order;
+  const ushort4* __restrict__ rect = A.rect;
+  const float2* __restrict__ mean2d = A.mean2d;
+  const float4* __restrict__ conic_opacity = A.conic_opacity;
+  const int64_t n = A.n;
+  const int tiles_x = A.tiles_x, tiles_y = A.tiles_y;
+  const uint32_t* err = A.err;
+  uint32_t* __restrict__ wcount = A.wcount;
   griddep_wait();
   __shared__ WalkWarp s_walk[kWalkWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -728,12 +902,22 @@ __device__ __forceinline__ void count_span_digits(const DigitAcc& acc, uint32_t 
 // histograms of what it writes.  The warp walks its row sequence 32 rows at a time (one row per
 // lane, as in walk_count_kernel); a warp scan places the rows' spans, and the lanes then store the
 // chunk's instances 32 consecutive ones at a time (coalesced).  Positions >= cap are dropped.
-__global__ void __launch_bounds__(kWalkThreads)
-walk_emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                 const float2* __restrict__ mean2d, const float4* __restrict__ conic_opacity, int64_t n,
-                 int tiles_x, int tiles_y, const uint64_t* __restrict__ wfirst, int64_t cap,
-                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int passes, int width,
-                 const uint32_t* err, uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(const Batch<WalkArgs> b) {
+  const WalkArgs& A = b.a[blockIdx.y];
+  if (blockIdx.x >= A.grid) return;
+  const uint32_t* __restrict__ order = A.order;
+  const ushort4* __restrict__ rect = A.rect;
+  const float2* __restrict__ mean2d = A.mean2d;
+  const float4* __restrict__ conic_opacity = A.conic_opacity;
+  const int64_t n = A.n;
+  const int tiles_x = A.tiles_x, tiles_y = A.tiles_y;
+  const uint64_t* __restrict__ wfirst = A.wfirst;
+  const int64_t cap = A.cap;
+  uint32_t* __restrict__ keys = A.keys;
+  uint32_t* __restrict__ vals = A.vals;
+  const int passes = A.passes, width = A.width;
+  const uint32_t* err = A.err;
+  uint32_t* __restrict__ hist = A.hist;
   griddep_wait();
   __shared__ WalkWarp s_walk[kWalkWarps];
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
@@ -825,9 +1009,25 @@ __device__ __forceinline__ int64_t warp_lower_bound(const uint32_t* __restrict__
 // that no later kernel reads the lists and every reader of the count sees the failure.
 constexpr int kRangeTiles = 8;
 
-__global__ void __launch_bounds__((kRangeTiles + 1) * 32)
-ranges_kernel(const uint32_t* __restrict__ keys, int64_t* nptr, int64_t cap, int num_tiles, const uint32_t* err,
-              uint2* __restrict__ ranges) {
+struct RangesArgs {
+  const uint32_t* keys;
+  int64_t* nptr;
+  int64_t cap;
+  int num_tiles;
+  const uint32_t* err;
+  uint2* ranges;
+  unsigned grid;
+};
+
+__global__ void __launch_bounds__((kRangeTiles + 1) * 32) ranges_kernel(const Batch<RangesArgs> b) {
+  const RangesArgs& A = b.a[blockIdx.y];
+  if (blockIdx.x >= A.grid) return;
+  const uint32_t* __restrict__ keys = A.keys;
+  int64_t* nptr = A.nptr;
+  const int64_t cap = A.cap;
+  const int num_tiles = A.num_tiles;
+  const uint32_t* err = A.err;
+  uint2* __restrict__ ranges = A.ranges;
   griddep_wait();
   __shared__ uint32_t s_start[kRangeTiles + 1];
   const int warp = threadIdx.x >> 5;
@@ -877,8 +1077,10 @@ cudaError_t launch_lookback_selftest(const uint32_t* keys, const uint32_t* vals,
   const int64_t hist_blocks = std::min<int64_t>((n + kRadixThreads - 1) / kRadixThreads, 4 * device_sm_count());
   digit_hist_kernel<<<(unsigned)hist_blocks, kRadixThreads, 0, st>>>(keys, nullptr, n, n, 1, 8, scratch);
   set_word_kernel<<<1, 1, 0, st>>>(scratch + kMaxPasses * kBins, first_ticket);
-  radix_sort(kin, vin, nullptr, n, n, 8, scratch, err, 0, true, st, spin_limit);
-  return cudaGetLastError();
+  SortJob job{{kin[0], kin[1]}, {vin[0], vin[1]}, nullptr, n, n, 8, scratch, err, 0};
+  int cur = 0;
+  cudaError_t e2 = radix_sort(&job, 1, true, st, &cur, spin_limit);
+  return e2 != cudaSuccess ? e2 : cudaGetLastError();
 }
 
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
@@ -905,81 +1107,140 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   return p;
 }
 
-cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, const BinPlan& plan,
-                            char* ws, const sdgs_bins& out, cudaStream_t st, uint32_t inject_err) {
-  const int64_t n = plan.n;
-  const int tiles_x = tiles_of(v.width), tiles_y = tiles_of(v.height);
-  uint32_t* dkeys[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[0]),
-                        reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[1])};
-  uint32_t* dvals[2] = {reinterpret_cast<uint32_t*>(ws + plan.off_dvals[0]),
-                        reinterpret_cast<uint32_t*>(ws + plan.off_dvals[1])};
-  uint64_t* first = reinterpret_cast<uint64_t*>(ws + plan.off_first);
-  uint32_t* sort_d = reinterpret_cast<uint32_t*>(ws + plan.off_sort_d);
-  uint32_t* sort_t = reinterpret_cast<uint32_t*>(ws + plan.off_sort_t);
-  uint32_t* err = reinterpret_cast<uint32_t*>(ws + plan.off_err);
-  uint64_t* partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
-  const ushort4* rect = reinterpret_cast<const ushort4*>(proj.rect);
-  const float2* m2 = reinterpret_cast<const float2*>(proj.mean2d);
-  const float4* co = reinterpret_cast<const float4*>(proj.conic_opacity);
-
-  ClearJob clear;
-  // (with Gaussians, the ranges kernel writes every tile's range)
-  clear.ptr[0] = n == 0 ? out.ranges : nullptr; clear.words[0] = 2 * (size_t)plan.num_tiles;
-  clear.ptr[1] = err; clear.words[1] = 1;
-  clear.ptr[2] = n == 0 ? reinterpret_cast<uint32_t*>(out.num_instances) : nullptr; clear.words[2] = 2;
-  clear.ptr[3] = n > 0 ? sort_d : nullptr; clear.words[3] = sort_scratch_bytes(n, 32) / 4;
-  clear.ptr[4] = n > 0 ? sort_t : nullptr; clear.words[4] = sort_scratch_bytes(plan.capacity, plan.tile_bits) / 4;
-  size_t most = 0;
-  for (int k = 0; k < 5; ++k) most = std::max(most, clear.ptr[k] ? clear.words[k] : 0);
-  const unsigned gc = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * (size_t)device_sm_count()));
-  cudaError_t e = launch_pdl(clear_kernel, dim3(gc), dim3(256), 0, st, clear);
-  if (e == cudaSuccess && inject_err != 0u) {  // test support: as if a pass had given up waiting
-    set_word_kernel<<<1, 1, 0, st>>>(err, inject_err);
-    e = cudaGetLastError();
+cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_t st) {
+  if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
+  // Workspace carve-up of every request.
+  struct Work {
+    int64_t n;
+    int tiles_x, tiles_y;
+    uint32_t *dkeys[2], *dvals[2], *sort_d, *sort_t, *err, *out_keys, *ikeys[2], *ivals[2];
+    uint64_t *first, *partials;
+    const ushort4* rect;
+    const float2* m2;
+    const float4* co;
+    const uint32_t* order;
+  } W[kMaxBatch];
+  cudaError_t e = cudaSuccess;
+  BatchLaunch<ClearJob> clears;
+  for (int j = 0; j < count; ++j) {
+    const BinRequest& R = reqs[j];
+    const BinPlan& plan = R.plan;
+    char* ws = R.ws;
+    Work& w = W[j];
+    w.n = plan.n;
+    w.tiles_x = tiles_of(R.view.width);
+    w.tiles_y = tiles_of(R.view.height);
+    for (int k = 0; k < 2; ++k) {
+      w.dkeys[k] = reinterpret_cast<uint32_t*>(ws + plan.off_dkeys[k]);
+      w.dvals[k] = reinterpret_cast<uint32_t*>(ws + plan.off_dvals[k]);
+    }
+    w.first = reinterpret_cast<uint64_t*>(ws + plan.off_first);
+    w.sort_d = reinterpret_cast<uint32_t*>(ws + plan.off_sort_d);
+    w.sort_t = reinterpret_cast<uint32_t*>(ws + plan.off_sort_t);
+    w.err = reinterpret_cast<uint32_t*>(ws + plan.off_err);
+    w.partials = reinterpret_cast<uint64_t*>(ws + plan.off_partials);
+    w.rect = reinterpret_cast<const ushort4*>(R.proj.rect);
+    w.m2 = reinterpret_cast<const float2*>(R.proj.mean2d);
+    w.co = reinterpret_cast<const float4*>(R.proj.conic_opacity);
+    // the instance buffers, ordered so that the tile passes end in the outputs
+    const int passes = radix_pass_count(plan.tile_bits);
+    w.out_keys = R.out.tile_keys ? R.out.tile_keys : reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[1]);
+    uint32_t* wk0 = reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[0]);
+    uint32_t* wv0 = reinterpret_cast<uint32_t*>(ws + plan.off_ivals);
+    const bool even = passes % 2 == 0;
+    w.ikeys[0] = even ? w.out_keys : wk0;
+    w.ivals[0] = even ? R.out.point_list : wv0;
+    w.ikeys[1] = even ? wk0 : w.out_keys;
+    w.ivals[1] = even ? wv0 : R.out.point_list;
+    ClearJob c;
+    // (with Gaussians, the ranges kernel writes every tile's range)
+    c.ptr[0] = w.n == 0 ? R.out.ranges : nullptr; c.words[0] = 2 * (size_t)plan.num_tiles;
+    c.ptr[1] = w.err; c.words[1] = 1;
+    c.ptr[2] = w.n == 0 ? reinterpret_cast<uint32_t*>(R.out.num_instances) : nullptr; c.words[2] = 2;
+    c.ptr[3] = w.n > 0 ? w.sort_d : nullptr; c.words[3] = sort_scratch_bytes(w.n, 32) / 4;
+    c.ptr[4] = w.n > 0 ? w.sort_t : nullptr; c.words[4] = sort_scratch_bytes(plan.capacity, plan.tile_bits) / 4;
+    size_t most = 0;
+    for (int k = 0; k < 5; ++k) most = std::max(most, c.ptr[k] ? c.words[k] : 0);
+    c.grid = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * (size_t)device_sm_count()));
+    clears.add(c);
   }
-  if (e != cudaSuccess || n == 0) return e;
-  const unsigned gb = (unsigned)std::min<int64_t>((n + kRadixThreads - 1) / kRadixThreads, 2 * device_sm_count());
+  e = launch_batch(clear_kernel, clears, 256, 0, st);
+  for (int j = 0; j < count && e == cudaSuccess; ++j)
+    if (reqs[j].inject_err != 0u) {  // test support: as if a pass had given up waiting
+      set_word_kernel<<<1, 1, 0, st>>>(W[j].err, reqs[j].inject_err);
+      e = cudaGetLastError();
+    }
+  if (e != cudaSuccess) return e;
+  // Only the requests with Gaussians go on (the others are complete: no instances, empty ranges).
+  int live[kMaxBatch], nl = 0;
+  for (int j = 0; j < count; ++j)
+    if (W[j].n > 0) live[nl++] = j;
+  if (nl == 0) return cudaSuccess;
   // 1. Gaussians by float32 depth (stable; culled ones last).
-  e = launch_pdl(depth_keys_kernel, dim3(gb), dim3(kRadixThreads), 0, st, proj.depth, rect, n, dkeys[0], dvals[0],
-                 sort_d);
-  if (e != cudaSuccess) return e;
-  const int dcur = radix_sort(dkeys, dvals, nullptr, n, n, 32, sort_d, err, 0, true, st);
-  const uint32_t* order = dvals[dcur];
+  BatchLaunch<DepthKeysArgs> keys;
+  SortJob dsort[kMaxBatch];
+  int dcur[kMaxBatch];
+  for (int i = 0; i < nl; ++i) {
+    Work& w = W[live[i]];
+    DepthKeysArgs a{reqs[live[i]].proj.depth, w.rect, w.n, w.dkeys[0], w.dvals[0], w.sort_d,
+                    (unsigned)std::min<int64_t>((w.n + kRadixThreads - 1) / kRadixThreads, 2 * device_sm_count())};
+    keys.add(a);
+    dsort[i] = SortJob{{w.dkeys[0], w.dkeys[1]}, {w.dvals[0], w.dvals[1]}, nullptr, w.n, w.n, 32, w.sort_d, w.err, 0};
+  }
+  if ((e = launch_batch(depth_keys_kernel, keys, kRadixThreads, 0, st)) != cudaSuccess) return e;
+  if ((e = radix_sort(dsort, nl, true, st, dcur)) != cudaSuccess) return e;
   // 2. Kept tiles per warp of 32 depth-ordered Gaussians (row spans); first instance of each warp; K.
-  uint32_t* wcount = dkeys[dcur ^ 1];
-  const int64_t nwarps = (n + 31) / 32;
-  const unsigned gw = (unsigned)((nwarps + kWalkWarps - 1) / kWalkWarps);
-  e = launch_pdl(walk_count_kernel, dim3(gw), dim3(kWalkThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
-                 (const uint32_t*)err, wcount);
-  if (e != cudaSuccess) return e;
-  e = exclusive_scan<uint32_t, uint64_t>(wcount, nwarps, first, partials, out.num_instances, st);
-  if (e != cudaSuccess) return e;
-  // 3. Instances in depth order, into the buffer that makes the tile passes end in `out`.
-  const int passes = radix_pass_count(plan.tile_bits);
-  uint32_t* out_keys = out.tile_keys ? out.tile_keys : reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[1]);
-  uint32_t* ikeys[2];
-  uint32_t* ivals[2];
-  uint32_t* wk0 = reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[0]);
-  uint32_t* wv0 = reinterpret_cast<uint32_t*>(ws + plan.off_ivals);
-  if (passes % 2 == 0) {
-    ikeys[0] = out_keys; ivals[0] = out.point_list; ikeys[1] = wk0; ivals[1] = wv0;
-  } else {
-    ikeys[0] = wk0; ivals[0] = wv0; ikeys[1] = out_keys; ivals[1] = out.point_list;
+  BatchLaunch<WalkArgs> walks;
+  ScanArgs<uint32_t, uint64_t> scans[kMaxBatch];
+  for (int i = 0; i < nl; ++i) {
+    Work& w = W[live[i]];
+    const BinRequest& R = reqs[live[i]];
+    w.order = w.dvals[dcur[i]];
+    const int64_t nwarps = (w.n + 31) / 32;
+    WalkArgs a{};
+    a.order = w.order; a.rect = w.rect; a.mean2d = w.m2; a.conic_opacity = w.co; a.n = w.n;
+    a.tiles_x = w.tiles_x; a.tiles_y = w.tiles_y; a.err = w.err;
+    a.wcount = w.dkeys[dcur[i] ^ 1];
+    a.wfirst = w.first; a.cap = R.plan.capacity;
+    a.keys = w.ikeys[0]; a.vals = w.ivals[0];
+    a.passes = radix_pass_count(R.plan.tile_bits); a.width = radix_digit_width(R.plan.tile_bits);
+    a.hist = w.sort_t;
+    a.grid = (unsigned)((nwarps + kWalkWarps - 1) / kWalkWarps);
+    walks.add(a);
+    scans[i] = ScanArgs<uint32_t, uint64_t>{a.wcount, nwarps, w.first, reinterpret_cast<uint64_t*>(w.partials),
+                                            R.out.num_instances, 0};
   }
-  e = launch_pdl(walk_emit_kernel, dim3(gw), dim3(kWalkThreads), 0, st, order, rect, m2, co, n, tiles_x, tiles_y,
-                 (const uint64_t*)first, plan.capacity, ikeys[0], ivals[0], passes,
-                 radix_digit_width(plan.tile_bits), (const uint32_t*)err, sort_t);
-  if (e != cudaSuccess) return e;
-  // 4. Stable sort by tile id; 5. tile ranges.
-  radix_sort(ikeys, ivals, out.num_instances, 0, plan.capacity, plan.tile_bits, sort_t, err, kMaxPasses, true, st);
-  {
-    const unsigned gr = (unsigned)((plan.num_tiles + kRangeTiles - 1) / kRangeTiles);
-    e = launch_pdl(ranges_kernel, dim3(gr), dim3((kRangeTiles + 1) * 32), 0, st, (const uint32_t*)out_keys,
-                   out.num_instances, plan.capacity, (int)plan.num_tiles, (const uint32_t*)err,
-                   reinterpret_cast<uint2*>(out.ranges));
-    if (e != cudaSuccess) return e;
+  if ((e = launch_batch(walk_count_kernel, walks, kWalkThreads, 0, st)) != cudaSuccess) return e;
+  if ((e = exclusive_scan(scans, nl, st)) != cudaSuccess) return e;
+  // 3. Instances in depth order (with the tile-digit histograms); 4. stable sort by tile id.
+  if ((e = launch_batch(walk_emit_kernel, walks, kWalkThreads, 0, st)) != cudaSuccess) return e;
+  SortJob tsort[kMaxBatch];
+  int tcur[kMaxBatch];
+  for (int i = 0; i < nl; ++i) {
+    Work& w = W[live[i]];
+    const BinRequest& R = reqs[live[i]];
+    tsort[i] = SortJob{{w.ikeys[0], w.ikeys[1]}, {w.ivals[0], w.ivals[1]}, R.out.num_instances, 0,
+                       R.plan.capacity, R.plan.tile_bits, w.sort_t, w.err, kMaxPasses};
   }
+  if ((e = radix_sort(tsort, nl, true, st, tcur)) != cudaSuccess) return e;
+  // 5. Tile ranges.
+  BatchLaunch<RangesArgs> ranges;
+  for (int i = 0; i < nl; ++i) {
+    Work& w = W[live[i]];
+    const BinRequest& R = reqs[live[i]];
+    RangesArgs a{w.out_keys, R.out.num_instances, R.plan.capacity, (int)R.plan.num_tiles, w.err,
+                 reinterpret_cast<uint2*>(R.out.ranges),
+                 (unsigned)((R.plan.num_tiles + kRangeTiles - 1) / kRangeTiles)};
+    ranges.add(a);
+  }
+  if ((e = launch_batch(ranges_kernel, ranges, (kRangeTiles + 1) * 32, 0, st)) != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, const BinPlan& plan, char* ws,
+                            const sdgs_bins& out, cudaStream_t st, uint32_t inject_err) {
+  const BinRequest r{proj, v, plan, ws, out, inject_err};
+  return launch_bin_sort_batch(&r, 1, st);
 }
 
 }  // namespace sdgs

@@ -74,6 +74,19 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);
 // inject_err != 0 (test support only) starts the sort's error word at that value.
 cudaError_t launch_bin_sort(const sdgs_projected& p, const sdgs_view& v, const BinPlan& plan,
                             char* ws, const sdgs_bins& out, cudaStream_t st, uint32_t inject_err = 0);
+
+// Binning of up to kMaxBinBatch requests with one launch per step (each kernel serves request
+// blockIdx.y); the same results as binning each request on its own.
+constexpr int kMaxBinBatch = 8;
+struct BinRequest {
+  sdgs_projected proj;
+  sdgs_view view;
+  BinPlan plan;
+  char* ws;
+  sdgs_bins out;
+  uint32_t inject_err;
+};
+cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_t st);
 size_t lookback_selftest_bytes(int64_t n);
 cudaError_t launch_lookback_selftest(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                                      uint32_t* vals_out, int64_t n, uint32_t first_ticket, int spin_limit, char* ws,

@@ -232,17 +232,23 @@ sdgs_bins slot_bins(const Slot& sl, int64_t cap) {
   return b;
 }
 
-// Binning, compositing, the instance count and the image copy on the slot's stream, then the
-// completion host function.
-cudaError_t enqueue_tail(sdgs_server* s, int slot_index) {
+// The binning arguments of a slot's request.
+BinRequest slot_bin_request(const sdgs_server* s, const Slot& sl) {
+  const Request* r = sl.req;
+  const sdgs_scene& sc = s->scenes[r->scene];
+  return BinRequest{slot_projected(sl, sc.n), r->view, plan_bins(sc.n, r->capacity, r->view.width, r->view.height),
+                    (char*)sl.ws, slot_bins(sl, r->capacity), 0u};
+}
+
+// The instance count, compositing and the image copy on the slot's stream (after its binning),
+// then the completion host function.
+cudaError_t enqueue_render(sdgs_server* s, int slot_index) {
   Slot& sl = s->slots[slot_index];
   Request* r = sl.req;
   const sdgs_scene& sc = s->scenes[r->scene];
   const sdgs_projected p = slot_projected(sl, sc.n);
   const sdgs_bins b = slot_bins(sl, r->capacity);
-  const BinPlan plan = plan_bins(sc.n, r->capacity, r->view.width, r->view.height);
   cudaError_t e;
-  if ((e = launch_bin_sort(p, r->view, plan, (char*)sl.ws, b, sl.st))) return e;
   if ((e = cudaMemcpyAsync(sl.pinned_k, sl.num_instances, sizeof(int64_t), cudaMemcpyDeviceToHost, sl.st)))
     return e;
   if ((e = launch_render_fwd(p, b, r->view, sl.image, sl.final_T, sl.n_contrib, nullptr, sl.st))) return e;
@@ -253,6 +259,14 @@ cudaError_t enqueue_tail(sdgs_server* s, int slot_index) {
   e = cudaLaunchHostFunc(sl.st, host_done, arg);
   if (e != cudaSuccess) delete arg;
   return e;
+}
+
+// Binning of one request on its slot's stream, then its render (a retry after an overflow).
+cudaError_t enqueue_tail(sdgs_server* s, int slot_index) {
+  Slot& sl = s->slots[slot_index];
+  const BinRequest br = slot_bin_request(s, sl);
+  cudaError_t e = launch_bin_sort(br.proj, br.view, br.plan, br.ws, br.out, sl.st);
+  return e != cudaSuccess ? e : enqueue_render(s, slot_index);
 }
 
 void host_done(void* p) {
@@ -370,6 +384,14 @@ void admit(sdgs_server* s) {
                                   cudaMemcpyHostToDevice, s->batch_stream);
   if (e == cudaSuccess) e = cudaEventRecord(s->jobs_copied, s->batch_stream);
   if (e == cudaSuccess) e = launch_slice_project_batched(s->jobs_device, (int)started.size(), max_n, s->batch_stream);
+  // binning of the same requests, kMaxBinBatch per launch sequence, on the batch stream
+  for (size_t j0 = 0; j0 < started.size() && e == cudaSuccess; j0 += kMaxBinBatch) {
+    BinRequest reqs[kMaxBinBatch];
+    int count = 0;
+    for (size_t j = j0; j < started.size() && count < kMaxBinBatch; ++j)
+      reqs[count++] = slot_bin_request(s, s->slots[started[j]]);
+    e = launch_bin_sort_batch(reqs, count, s->batch_stream);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(s->batch_event, s->batch_stream);
   s->stats.batches++;
   s->stats.max_batch = std::max<uint64_t>(s->stats.max_batch, started.size());
@@ -377,7 +399,7 @@ void admit(sdgs_server* s) {
     Slot& sl = s->slots[idx];
     cudaError_t e2 = e;
     if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(sl.st, s->batch_event, 0);
-    if (e2 == cudaSuccess) e2 = enqueue_tail(s, idx);
+    if (e2 == cudaSuccess) e2 = enqueue_render(s, idx);
     if (e2 != cudaSuccess) {
       set_error("server launch: %s", cudaGetErrorString(e2));
       fail_request(s, sl.req, SDGS_ERR_CUDA);

@@ -100,6 +100,9 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sdgs_bin_sort": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p, ctypes.c_size_t,
                        ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
+    "sdgs_bin_sort_batch": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.POINTER(ctypes.c_void_p),
+                             ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(Bins), ctypes.c_int32,
+                             ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
     "sdgs_bin_sort_failure_selftest": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.c_void_p], ctypes.c_int),
@@ -290,6 +293,20 @@ def bin_sort(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = 
                                bins.ws_bytes, ctypes.byref(bins.struct()),
                                ctypes.byref(k) if sync else None, _stream(stream)))
     return int(k.value) if sync else None
+
+
+def bin_sort_batch(projs: list, views: list, bins: list, sync: bool = True, stream=None):
+    """sdgs_bin_sort_batch: bins several problems with one launch per step; returns the list of
+    instance counts when sync=True."""
+    n = len(projs)
+    P = (Projected * n)(*[p.struct() for p in projs])
+    V = (View * n)(*views)
+    B = (Bins * n)(*[b.struct() for b in bins])
+    W = (ctypes.c_void_p * n)(*[_ptr(b.workspace) for b in bins])
+    S = (ctypes.c_size_t * n)(*[b.ws_bytes for b in bins])
+    K = (ctypes.c_int64 * n)()
+    _check(lib().sdgs_bin_sort_batch(P, V, W, S, B, n, K if sync else None, _stream(stream)))
+    return [int(k) for k in K] if sync else None
 
 
 def bin_sort_failure_selftest(proj: ProjectedBuffers, view: View, bins: BinBuffers, sync: bool = True,

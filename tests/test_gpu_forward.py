@@ -231,3 +231,44 @@ def test_renderer_deferred_check_matches_and_grows(scene0):
     assert small.overflowed_frames == 1 and small.bins.capacity >= k
     assert torch.equal(img, ref)
     assert not small.check_deferred() and small.num_instances == k
+
+
+def test_bin_sort_batch_equals_binning_each_problem_alone():
+    """sdgs_bin_sort_batch (one launch per step for several problems, as the render server bins
+    the requests it admits together) gives every problem exactly the lists, ranges and count of
+    sdgs_bin_sort on its own: mixed sizes and tile grids, an empty problem, a single-tile image,
+    and an overflowing capacity."""
+    cases = [(5000, 256, 256, 3), (20000, 1352, 1014, 4), (0, 64, 64, 0), (1, 16, 16, 1),
+             (3000, 1920, 1080, 5), (16000, 48, 32, 9), (300, 100, 70, 2), (20000, 1352, 1014, 11)]
+    projs, views, alone, batch = [], [], [], []
+    for n, W, H, seed in cases:
+        rec = synth.random_projected(n, W, H, seed=seed, max_half_tiles=3 if W < 100 else 12)
+        projs.append(U.sdgs.ProjectedBuffers.from_host(rec))
+        views.append(U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5)))
+    for j, (p, v) in enumerate(zip(projs, views)):
+        cap = max(1024, 64 * max(p.n, 1))
+        if j == len(cases) - 1:
+            cap = 20000  # far below K: the lists keep the nearest `cap` instances
+        for dst in (alone, batch):
+            dst.append(U.sdgs.BinBuffers(p.n, cap, v.width, v.height))
+    ks = []
+    for p, v, b in zip(projs, views, alone):
+        try:
+            ks.append(U.sdgs.bin_sort(p, v, b, sync=True))
+        except U.sdgs.SdgsError as e:
+            assert e.code == 3
+            ks.append(int(b.num_instances.item()))
+    with pytest.raises(U.sdgs.SdgsError) as e:  # the last problem overflows
+        U.sdgs.bin_sort_batch(projs, views, batch, sync=True)
+    assert e.value.code == 3
+    torch.cuda.synchronize()
+    for j, (a, b) in enumerate(zip(alone, batch)):
+        k = int(b.num_instances.item())
+        assert k == ks[j], j
+        m = min(k, a.capacity)
+        assert torch.equal(a.ranges, b.ranges), j
+        assert torch.equal(a.point_list[:m], b.point_list[:m]), j
+        assert torch.equal(a.tile_keys[:m], b.tile_keys[:m]), j
+    # and without the overflow the batch call returns every K
+    ks2 = U.sdgs.bin_sort_batch(projs[:-1], views[:-1], batch[:-1], sync=True)
+    assert ks2 == ks[:-1]
