@@ -259,6 +259,7 @@ int sdgs_alu_peak_probe(int32_t kind, int32_t iters, float* sink, int64_t sink_l
 /* Front-to-back compositing of each 16x16 tile's sorted instances.
  * Per pixel: alpha_i = min(0.99, alpha_cond exp(-1/2 (a dx^2 + c dy^2) - b dx dy)), skipped when
  * below 1/255; the pixel stops before the Gaussian that would take its transmittance below 1e-4.
+ * A record whose conic is not positive definite (a <= 0 or ac - b^2 <= 0) is skipped everywhere.
  * Writes image [height][width][3] = sum c_i alpha_i T_i + T_final bg, final_T [height][width] and
  * n_contrib [height][width] (1 + position in the tile list of the last Gaussian blended, 0 if
  * none).  All outputs are device float32 / uint32.  If n_evaluated (device uint64[2]) is not

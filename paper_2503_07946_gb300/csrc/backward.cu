@@ -81,8 +81,8 @@ __device__ __forceinline__ bool unblend2(BwdPair& px, const float4& q, const flo
   const float2 G = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
   const float2 raw = __fmul2_rn(make_float2(q.w, q.w), G);
   const float2 al = make_float2(fminf(kAlphaMax, raw.x), fminf(kAlphaMax, raw.y));
-  const bool h0 = pos < px.last0 && p2.x <= 0.f && al.x >= kAlphaMin;
-  const bool h1 = pos < px.last1 && p2.y <= 0.f && al.y >= kAlphaMin;
+  const bool h0 = pos < px.last0 && al.x >= kAlphaMin;
+  const bool h1 = pos < px.last1 && al.y >= kAlphaMin;
   const float2 ae = make_float2(h0 ? al.x : 0.f, h1 ? al.y : 0.f);  // alpha taken (0: skipped)
   const float2 om = make_float2(1.f - ae.x, 1.f - ae.y);
   px.T = make_float2(__fdividef(px.T.x, om.x), __fdividef(px.T.y, om.y));
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kBwdThreads, 16) raster_bwd_kernel(const Raste
       if (j < top) {
         const uint32_t gid = a.point_list[range.x + j];
         const bool ok = gid < a.n;
-        const float4 co = ok ? a.conic_opacity[gid] : make_float4(0.f, 0.f, 0.f, 0.f);  // alpha 0: skipped
+        const float4 co = ok ? pd_or_transparent(a.conic_opacity[gid]) : make_float4(0.f, 0.f, 0.f, 0.f);
         s_xy[e] = ok ? a.mean2d[gid] : make_float2(0.f, 0.f);
         s_co[e] = co;
         s_q[e] = scaled_conic(co);

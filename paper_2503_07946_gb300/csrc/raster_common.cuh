@@ -19,6 +19,14 @@ __device__ __forceinline__ float4 scaled_conic(float4 co) {
                      __fmul_rn(kNegHalfLog2e, co.z), co.w);
 }
 
+// A record whose conic is not positive definite (only caller-made records can be) is staged with
+// opacity 0, so that every pixel skips it; the rasterisers then need no per-pixel sign test of
+// the exponent.
+__device__ __forceinline__ float4 pd_or_transparent(float4 co) {
+  const bool pd = co.x > 0.f && __fsub_rn(__fmul_rn(co.x, co.z), __fmul_rn(co.y, co.y)) > 0.f;
+  return pd ? co : make_float4(co.x, co.y, co.z, 0.f);
+}
+
 __device__ __forceinline__ float splat_power2(const float4& q, float dx, float dy) {
   const float a = __fmul_rn(__fmul_rn(q.x, dx), dx);
   const float t = __fmaf_rn(q.z, dy, __fmul_rn(q.y, dx));

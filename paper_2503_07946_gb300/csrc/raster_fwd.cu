@@ -39,9 +39,10 @@ struct PixelPair {
 };
 
 // One Gaussian evaluated at both pixels, without branches: a pixel takes the Gaussian iff it is
-// still running, the exponent is <= 0 and alpha >= 1/255; if that would take T below 1e-4 the
-// pixel stops instead (without blending).  The exponent is qa dx^2 + dy (qc dy + qb dx), as in
-// splat_power2.
+// still running and alpha >= 1/255; if that would take T below 1e-4 the pixel stops instead
+// (without blending).  The exponent is qa dx^2 + dy (qc dy + qb dx), as in splat_power2; staged
+// conics are positive definite (others get opacity 0), so it is <= 0 but for FP32 rounding at a
+// pixel on the centre, where alpha is then alpha_cond (the FP64 oracle takes the Gaussian there).
 template <bool kCount>
 __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const float4& c, float dx, float2 dy,
                                        uint32_t pos1) {
@@ -54,8 +55,8 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
   const float2 al = make_float2(fminf(kAlphaMax, m.x), fminf(kAlphaMax, m.y));
   const float2 aT = __fmul2_rn(al, px.T);
   const float2 Tn = __fadd2_rn(px.T, make_float2(-aT.x, -aT.y));  // T (1 - alpha) as T - alpha T
-  const bool hit0 = !px.done0 && p2.x <= 0.f && al.x >= kAlphaMin;
-  const bool hit1 = !px.done1 && p2.y <= 0.f && al.y >= kAlphaMin;
+  const bool hit0 = !px.done0 && al.x >= kAlphaMin;
+  const bool hit1 = !px.done1 && al.y >= kAlphaMin;
   const bool stop0 = hit0 && Tn.x < kTMin, stop1 = hit1 && Tn.y < kTMin;
   const bool take0 = hit0 && !stop0, take1 = hit1 && !stop1;
   if (kCount) {
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
       const uint32_t g = a.point_list[range.x + j];
       if (g < a.n) {
         s_xy[threadIdx.x] = a.mean2d[g];
-        s_q[threadIdx.x] = scaled_conic(a.conic_opacity[g]);
+        s_q[threadIdx.x] = scaled_conic(pd_or_transparent(a.conic_opacity[g]));
         s_rgb[threadIdx.x] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
       } else {  // opacity 0: every pixel skips it
         s_xy[threadIdx.x] = make_float2(0.f, 0.f);

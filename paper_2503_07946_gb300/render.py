@@ -107,7 +107,7 @@ class Renderer:
             self._bin_deferred(view, stream)
         else:
             self.bin(view, stream)
-        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream)
+        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream=stream)
         return self.image
 
     def forward_async(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
@@ -115,7 +115,7 @@ class Renderer:
         self.frames += 1
         sdgs.slice_project(scene, view, self.proj, stream)
         sdgs.bin_sort(self.proj, view, self.bins, sync=False, stream=stream)
-        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream)
+        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream=stream)
         return self.image
 
 
@@ -136,8 +136,8 @@ class Render7DGS(torch.autograd.Function):
         ctx.renderer, ctx.view, ctx.lam, ctx.dir_mode = renderer, view, (lam_t, lam_d), dir_mode
         ctx.frame = renderer.frames
         ctx.lam_device = lam.device
-        ctx.final_T = renderer.final_T.clone()
-        ctx.n_contrib = renderer.n_contrib.clone()
+        # the backward reads the renderer's final_T and n_contrib of this frame; it refuses to run
+        # once the renderer has rendered another frame, so they need no copy
         ctx.save_for_backward(t["mean7"], t["L28"], t["opacity"], t["sh"])
         return image
 
@@ -156,8 +156,7 @@ class Render7DGS(torch.autograd.Function):
                                "take the gradient before rendering again with it, or render each image whose "
                                "gradient is needed with its own Renderer" % (r.frames - ctx.frame))
         ws = torch.empty(max(sdgs.bwd_workspace_size(r.n), 256), dtype=torch.uint8, device=mean7.device)
-        sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, ctx.final_T, ctx.n_contrib,
-                        grad_image.contiguous(), ws, grads)
+        sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, r.final_T, r.n_contrib, grad_image.contiguous(), ws, grads)
         dlam = grads["lam"].to(ctx.lam_device) if want_lam else None
         return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], dlam, None, None, None
 

@@ -272,3 +272,20 @@ def test_bin_sort_batch_equals_binning_each_problem_alone():
     # and without the overflow the batch call returns every K
     ks2 = U.sdgs.bin_sort_batch(projs[:-1], views[:-1], batch[:-1], sync=True)
     assert ks2 == ks[:-1]
+
+
+def test_renderer_on_a_side_stream_matches_the_default_stream(scene0):
+    """Renderer.forward(..., stream) runs every call on that stream and gives the same image."""
+    from paper_2503_07946_gb300 import render as prender
+    cam = _cams()[1]
+    dev = prender.scene_to_device(scene0)
+    st = U.sdgs.scene_struct(dev, scene0.lambda_t, scene0.lambda_d)
+    view = U.sdgs.view_struct(cam)
+    ref = prender.Renderer(scene0.n, cam.width, cam.height).forward(st, view).clone()
+    side = torch.cuda.Stream()
+    r = prender.Renderer(scene0.n, cam.width, cam.height, deferred_check=True)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            img = r.forward(st, view, side)
+    side.synchronize()
+    assert torch.equal(img, ref)
