@@ -39,7 +39,7 @@ FLOP_PER_CONTRIB = 6
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one
 # `ncu --set full` capture of render_fwd_kernel.  Set to None whenever render_fwd_kernel changes
 # until it is captured again.
-RENDER_FWD_TRAFFIC_BYTES = 12.836864e6
+RENDER_FWD_TRAFFIC_BYTES = 12.835584e6
 
 
 def load_peaks() -> dict:
@@ -327,12 +327,13 @@ def oracle_frames_report() -> dict:
 def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
     """Kernels libsdgs launches for one render: slice_project; the binning clear kernel; the
     depth keys (with the depth digit histograms); 4 depth radix passes; the kept-tile count per
-    Gaussian; its 3-kernel scan; the emit (with the tile digit histograms); ceil(tile bits / 8)
-    tile radix passes; tile ranges; the rasteriser."""
+    warp of 32 Gaussians; its scan (one kernel up to 11264 warps, else three); the emit (with the
+    tile digit histograms); ceil(tile bits / 8) tile radix passes; tile ranges; the rasteriser."""
     tiles = ((width + 15) // 16) * ((height + 15) // 16)
     bits = max(0, (tiles - 1).bit_length())
     tile_passes = (bits + 7) // 8 if capacity > 0 else 0
-    return 1 + 1 + 1 + 4 + 1 + 3 + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
+    scan = 1 if (n + 31) // 32 <= 11 * 1024 else 3
+    return 1 + 1 + 1 + 4 + 1 + scan + 1 + tile_passes + (1 if capacity > 0 else 0) + 1
 
 
 def cpu_baseline(cam_index: int) -> dict:
@@ -436,13 +437,30 @@ def run_ours(args, rank: int, world: int):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    def roll(seconds):
+        """Untimed frames of the same workload for `seconds`, so that the clock sampler (50 ms
+        period) has samples on both sides of a short timed region."""
+        t, k = time.perf_counter(), 0
+        while time.perf_counter() - t < seconds:
+            step(views[k % len(views)])
+            flush.zero_()
+            k += 1
+            if k % 20 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+
     with ClockSampler(dev.index) as clk:
+        roll(0.25)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         t_wall = time.perf_counter()
         for i in range(steps):
             step(views[warm + i], evs[i])
             flush.zero_()  # outside the step's events: every step starts with a cold L2
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        roll(0.25)
     if world > 1:
         torch.distributed.barrier()
     phase = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
@@ -486,10 +504,43 @@ def run_ours(args, rank: int, world: int):
         re_.forward(st, views[warm + i])
         host_img.copy_(re_.image, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
+    e2e_one_s = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     re_.check_deferred()
     assert re_.overflowed_frames == overflowed, "a timed end-to-end frame exceeded the bins' capacity"
     del re_
+    # the same with two frames in flight, as a streaming client runs: two renderers on two
+    # streams; every frame's image is copied to pinned host memory and waited for (by the host)
+    # before its renderer takes the frame after next
+    rs = [prender.Renderer(scene.n, W, H, capacity=r.bins.capacity, deferred_check=True) for _ in range(2)]
+    sts = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    hosts = [torch.empty(H, W, 3, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+
+    def stream_frames(count, first):
+        done = [None, None]
+        for i in range(count):
+            j = i % 2
+            if done[j] is not None:
+                done[j].synchronize()  # frame i - 2's image is on the host
+            with torch.cuda.stream(sts[j]):
+                rs[j].forward(st, views[first + i], sts[j])
+                hosts[j].copy_(rs[j].image, non_blocking=True)
+                done[j] = torch.cuda.Event()
+                done[j].record(sts[j])
+        for ev in done:
+            if ev is not None:
+                ev.synchronize()
+
+    stream_frames(warm, 0)
+    for q in rs:
+        q.check_deferred()
+    overflowed = [q.overflowed_frames for q in rs]
+    t0 = time.perf_counter()
+    stream_frames(steps, warm)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
+    for q, o in zip(rs, overflowed):
+        q.check_deferred()
+        assert q.overflowed_frames == o, "a timed end-to-end frame exceeded the bins' capacity"
+    del rs
 
     # ---- fwd + bwd (L2 loss against a target from perturbed parameters, camera 0) ----
     big_scene = synth.config_scene(2)
@@ -509,6 +560,7 @@ def run_ours(args, rank: int, world: int):
     raster_ms = float(phase[:, 2].mean())
     achieved_tflops = ((evals * FLOP_PER_EVAL + contribs * FLOP_PER_CONTRIB) / steps) / (raster_ms * 1e-3) / 1e12
     clocks = clk.summary()
+    clocks["window"] = "the timed steps and 0.25 s of the same frames right before and after them"
     with ClockSampler(dev.index) as clk_alu:
         alu = measure_alu_peaks(dev)
     alu["clocks"] = clk_alu.summary()
@@ -535,7 +587,8 @@ def run_ours(args, rank: int, world: int):
         "densify_stats": dens,
         "serving": serving,
         "e2e": {"value": job_mpix_s(world, pix, e2e_s * 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
-                "d2h_bytes_per_step": pix * 3 * 4 + 8},
+                "d2h_bytes_per_step": pix * 3 * 4 + 8, "frames_in_flight": 2,
+                "one_frame_in_flight": job_mpix_s(world, pix, e2e_one_s * 1e3)},
         "gpu_launches": steps * launches_per_frame(scene.n, r.bins.capacity, W, H),
         "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops,
@@ -613,6 +666,38 @@ def serving_bench(dev, rates=(100.0, 200.0, 500.0, 1000.0, 2000.0), count: int =
         bufs[(cam.width, cam.height)][0].copy_(img)
         torch.cuda.synchronize()
 
+    def live(srv, ids, trace):
+        """Submits the trace at its arrival times; returns latencies (s) and completion times."""
+        rids, subs = [], []
+        t0 = time.perf_counter()
+        for i, (ta, sid, cam) in enumerate(trace):
+            while time.perf_counter() - t0 < ta:
+                pass
+            if i >= ring:
+                srv.wait(rids[i - ring], 60_000)  # its output buffer is reused now
+            rids.append(srv.submit(ids[sid], sdgs.view_struct(cam), bufs[(cam.width, cam.height)][i % ring]))
+            subs.append(time.perf_counter() - t0)
+        lat = np.array([srv.wait(r, 60_000) for r in rids]) * 1e-3
+        srv.release()
+        return lat, np.array(subs) + lat
+
+    def one_at_a_time(trace):
+        service = []
+        for _, sid, cam in trace:
+            a = time.perf_counter()
+            plain(sid, cam)
+            service.append(time.perf_counter() - a)
+        finish, lat1 = 0.0, []
+        for (ta, _, _), sv in zip(trace, service):
+            finish = max(finish, ta) + sv
+            lat1.append(finish - ta)
+        return np.array(lat1), finish
+
+    def stats_line(lat, span, pix):
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mpix_s": pix / span / 1e6}
+
+    plain_at = {}
     with sdgs.Server(budget_bytes=budget, slots=slots) as srv:
         ids = [srv.add_scene(t, s.lambda_t, s.lambda_d) for t, s in zip(tens, scenes)]
         warm = serving_trace(100.0, 16, 99, radii)
@@ -621,39 +706,53 @@ def serving_bench(dev, rates=(100.0, 200.0, 500.0, 1000.0, 2000.0), count: int =
             plain(sid, cam)
         for rate in rates:
             trace = serving_trace(rate, count, int(rate), radii)
-            # server, live
-            rids, subs = [], []
-            t0 = time.perf_counter()
-            for i, (ta, sid, cam) in enumerate(trace):
-                while time.perf_counter() - t0 < ta:
-                    pass
-                if i >= ring:
-                    srv.wait(rids[i - ring], 60_000)  # its output buffer is reused now
-                rids.append(srv.submit(ids[sid], sdgs.view_struct(cam), bufs[(cam.width, cam.height)][i % ring]))
-                subs.append(time.perf_counter() - t0)
-            lat = np.array([srv.wait(r, 60_000) for r in rids]) * 1e-3
-            srv.release()
-            done = np.array(subs) + lat
+            lat, done = live(srv, ids, trace)
             pix = sum(c.width * c.height for _, _, c in trace)
-            # one at a time, plain path
-            service = []
-            for _, sid, cam in trace:
-                a = time.perf_counter()
-                plain(sid, cam)
-                service.append(time.perf_counter() - a)
-            finish, lat1 = 0.0, []
-            for (ta, _, _), sv in zip(trace, service):
-                finish = max(finish, ta) + sv
-                lat1.append(finish - ta)
-            lat1 = np.array(lat1)
-            result[f"rate_{int(rate)}"] = {
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mpix_s": pix / (done.max() - trace[0][0]) / 1e6,
-                "one_at_a_time": {"p50_ms": float(np.percentile(lat1, 50) * 1e3),
-                                  "p99_ms": float(np.percentile(lat1, 99) * 1e3),
-                                  "mpix_s": pix / (finish - trace[0][0]) / 1e6},
-                "server_stats_so_far": srv.stats()}
+            lat1, finish = one_at_a_time(trace)
+            plain_at[rate] = (lat1, finish)
+            result[f"rate_{int(rate)}"] = dict(stats_line(lat, done.max() - trace[0][0], pix),
+                                               one_at_a_time=stats_line(lat1, finish - trace[0][0], pix),
+                                               server_stats_so_far=srv.stats())
         result["server_stats"] = srv.stats()
+    # the two highest rates again with a batching window: the server waits up to 300 us for more
+    # requests while slots are free, trading latency for larger batches
+    with sdgs.Server(budget_bytes=budget, slots=slots, batch_window_us=300) as srv:
+        ids = [srv.add_scene(t, s.lambda_t, s.lambda_d) for t, s in zip(tens, scenes)]
+        for _, sid, cam in serving_trace(100.0, 16, 99, radii):
+            srv.wait(srv.submit(ids[sid], sdgs.view_struct(cam), bufs[(cam.width, cam.height)][1]), 60_000)
+        for rate in rates[-2:]:
+            trace = serving_trace(rate, count, int(rate), radii)
+            lat, done = live(srv, ids, trace)
+            pix = sum(c.width * c.height for _, _, c in trace)
+            lat1, finish = plain_at[rate]
+            result[f"window300us_rate_{int(rate)}"] = dict(stats_line(lat, done.max() - trace[0][0], pix),
+                                                           one_at_a_time=stats_line(lat1, finish - trace[0][0], pix),
+                                                           server_stats_so_far=srv.stats())
+        # bursts: 8 requests (one per slot) submitted at once, 50 times, against the same 8 one at a time
+        rng = np.random.default_rng(7)
+        burst_lat, burst_plain = [], []
+        for b in range(50):
+            reqs = []
+            for k in range(slots):
+                sid = int(rng.integers(0, len(scenes)))
+                w, h = SERVE_SIZES[int(rng.integers(0, len(SERVE_SIZES)))]
+                d = rng.normal(size=3)
+                reqs.append((sid, synth.make_camera(radii[sid] * d / np.linalg.norm(d), w, h, 60.0,
+                                                    float(rng.uniform()))))
+            t0 = time.perf_counter()
+            rids = [srv.submit(ids[sid], sdgs.view_struct(cam), bufs[(cam.width, cam.height)][2 + k])
+                    for k, (sid, cam) in enumerate(reqs)]
+            for r in rids:
+                srv.wait(r, 60_000)
+            burst_lat.append(time.perf_counter() - t0)
+            srv.release()
+            t0 = time.perf_counter()
+            for sid, cam in reqs:
+                plain(sid, cam)
+            burst_plain.append(time.perf_counter() - t0)
+        result["bursts_of_8"] = {"server_ms_per_burst": float(np.median(burst_lat) * 1e3),
+                                 "one_at_a_time_ms_per_burst": float(np.median(burst_plain) * 1e3),
+                                 "bursts": 50, "server_stats": srv.stats()}
     return result
 
 

@@ -186,30 +186,34 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const Batch<Sca
   }
 }
 
-// The whole scan in one block, for up to kSingleScanItems * 1024 elements: each thread sums its
-// run of consecutive elements, the block scans the sums, and each thread writes its run.
-constexpr int kSingleScanItems = 16;
+// The whole scan in one block, for up to kSingleScanItems * 1024 elements: the block stages the
+// input in shared memory with coalesced loads, each thread sums its run of consecutive elements,
+// the block scans the sums, and each thread writes its run.
+constexpr int kSingleScanItems = 11;
 
 template <typename TIn, typename TOut>
 __global__ void __launch_bounds__(1024) scan_single_kernel(const Batch<ScanArgs<TIn, TOut>> b) {
   const ScanArgs<TIn, TOut>& a = b.a[blockIdx.y];
+  __shared__ TIn s_in[kSingleScanItems * 1024];
   griddep_wait();
-  const int64_t n = a.n;
-  const int64_t per = (n + 1023) / 1024;  // <= kSingleScanItems
-  const int64_t base = (int64_t)threadIdx.x * per;
-  TIn v[kSingleScanItems];
+  const int n = (int)a.n;  // <= kSingleScanItems * 1024
+  for (int i = threadIdx.x; i < n; i += 1024) s_in[i] = a.in[i];
+  __syncthreads();
+  const int per = (n + 1023) / 1024;  // <= kSingleScanItems
+  const int base = threadIdx.x * per;
   TOut local = 0;
 #pragma unroll
-  for (int k = 0; k < kSingleScanItems; ++k) {
-    v[k] = (k < per && base + k < n) ? a.in[base + k] : TIn(0);
-    local += (TOut)v[k];
-  }
+  for (int k = 0; k < kSingleScanItems; ++k)
+    if (k < per && base + k < n) local += (TOut)s_in[base + k];
   TOut tot;
   TOut run = block_inclusive_scan<TOut, 1024>(local, &tot) - local;
 #pragma unroll
   for (int k = 0; k < kSingleScanItems; ++k) {
-    if (k < per && base + k < n) a.out[base + k] = run;
-    run += (TOut)v[k];
+    if (k < per && base + k < n) {
+      const TOut v = (TOut)s_in[base + k];
+      a.out[base + k] = run;
+      run += v;
+    }
   }
   if (threadIdx.x == 0 && a.total_out != nullptr) *a.total_out = (int64_t)tot;
 }
