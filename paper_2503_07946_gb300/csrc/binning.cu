@@ -197,7 +197,19 @@ __global__ void __launch_bounds__(1024) scan_single_kernel(const Batch<ScanArgs<
   __shared__ TIn s_in[kSingleScanItems * 1024];
   griddep_wait();
   const int n = (int)a.n;  // <= kSingleScanItems * 1024
-  for (int i = threadIdx.x; i < n; i += 1024) s_in[i] = a.in[i];
+  {
+    TIn v[kSingleScanItems];  // every load in flight before any is used
+#pragma unroll
+    for (int k = 0; k < kSingleScanItems; ++k) {
+      const int i = k * 1024 + threadIdx.x;
+      v[k] = i < n ? a.in[i] : TIn(0);
+    }
+#pragma unroll
+    for (int k = 0; k < kSingleScanItems; ++k) {
+      const int i = k * 1024 + threadIdx.x;
+      if (i < n) s_in[i] = v[k];
+    }
+  }
   __syncthreads();
   const int per = (n + 1023) / 1024;  // <= kSingleScanItems
   const int base = threadIdx.x * per;
@@ -703,18 +715,29 @@ __global__ void __launch_bounds__(kRadixThreads) depth_keys_kernel(const Batch<D
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
   for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t stride = (int64_t)a.grid * kRadixThreads;
-  for (int64_t i0 = (int64_t)blockIdx.x * kRadixThreads; i0 < n; i0 += stride) {  // uniform over the block
-    const int64_t i = i0 + threadIdx.x;
-    uint32_t k = 0;
-    if (i < n) {
-      const ushort4 r = rect[i];
-      const bool vis = r.z > r.x && r.w > r.y;
-      k = vis ? __float_as_uint(depth[i]) : 0xffffffffu;  // visible depths are positive
-      keys[i] = k;
-      vals[i] = (uint32_t)i;
+  constexpr int U = 4;  // elements per thread per round, their loads issued together
+  const int64_t stride = (int64_t)a.grid * kRadixThreads * U;
+  for (int64_t i0 = (int64_t)blockIdx.x * kRadixThreads * U; i0 < n; i0 += stride) {  // uniform over the block
+    ushort4 r[U];
+    float z[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * kRadixThreads + threadIdx.x;
+      r[u] = i < n ? rect[i] : make_ushort4(0, 0, 0, 0);
+      z[u] = i < n ? depth[i] : 0.f;
     }
-    count_digits(s_hist, k, i < n, 4, 8);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * kRadixThreads + threadIdx.x;
+      uint32_t k = 0;
+      if (i < n) {
+        const bool vis = r[u].z > r[u].x && r[u].w > r[u].y;
+        k = vis ? __float_as_uint(z[u]) : 0xffffffffu;  // visible depths are positive
+        keys[i] = k;
+        vals[i] = (uint32_t)i;
+      }
+      count_digits(s_hist, k, i < n, 4, 8);
+    }
   }
   __syncthreads();
   flush_digits(s_hist, 4, hist);
@@ -1187,7 +1210,8 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     DepthKeysArgs a{reqs[live[i]].proj.depth, w.rect, w.n, w.dkeys[0], w.dvals[0], w.sort_d,
-                    (unsigned)std::min<int64_t>((w.n + kRadixThreads - 1) / kRadixThreads, 2 * device_sm_count())};
+                    (unsigned)std::min<int64_t>((w.n + 4 * kRadixThreads - 1) / (4 * kRadixThreads),
+                                                2 * device_sm_count())};
     keys.add(a);
     dsort[i] = SortJob{{w.dkeys[0], w.dkeys[1]}, {w.dvals[0], w.dvals[1]}, nullptr, w.n, w.n, 32, w.sort_d, w.err, 0};
   }
