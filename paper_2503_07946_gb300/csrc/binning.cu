@@ -7,14 +7,17 @@
 // give the same order as a stable radix sort of the n Gaussians by depth (ties keep ascending id)
 // followed by emission in that order.  That sort runs over n keys, not K.
 //
-// Tile digit: the instances, emitted in depth order, are radix-sorted stably by tile id
-// (ceil(log2 tiles) bits, in passes of equal width <= 8 bits).  Instances exist only inside the
-// per-row spans of tiles a Gaussian may reach (tile_reach.cuh).
+// Tile digit: instances exist only inside the per-row spans of tiles a Gaussian may reach
+// (tile_reach.cuh).  For images of at most 256 tiles per side, the row spans themselves are
+// emitted in depth order, sorted stably by row in one radix pass, and expanded into the tiles'
+// lists per row (span binning, below).  Otherwise the instances, emitted in depth order, are
+// radix-sorted stably by tile id (ceil(log2 tiles) bits, in passes of equal width <= 8 bits).
 //
 // Each radix pass is one kernel (digit histograms of all passes are accumulated while the keys are
 // produced): a block ranks its tile of keys stably, finds the keys of each digit in earlier tiles
 // by a decoupled look-back (bounded waits), and writes each digit's run contiguously.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "tile_reach.cuh"
@@ -844,6 +847,9 @@ struct WalkArgs {
   uint32_t* vals;
   int passes, width;      // tile-digit passes whose histograms the emit accumulates into hist
   uint32_t* hist;
+  uint32_t* scount;       // span binning: count walk writes the kept row spans per warp chunk
+  const uint64_t* sfirst; // span emit: first span of each warp chunk
+  int64_t* span_n;        // span emit: spans kept (lowered from the total when cap cuts them)
   unsigned grid;
 };
 
@@ -864,23 +870,35 @@ __global__ void __launch_bounds__(kWalkThreads) walk_count_kernel(const Batch<Wa
   const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
   if (wg * 32 >= n) return;  // whole warps
   if (*err != 0u) {  // the depth sort gave up: `order` may hold any value, so emit nothing
-    if (lane == 0) wcount[wg] = 0;
+    if (lane == 0) {
+      wcount[wg] = 0;
+      if (A.scount != nullptr) A.scount[wg] = 0;
+    }
     return;
   }
   WalkWarp& w = s_walk[warp];
   const int nr = walk_setup(w, order, rect, mean2d, conic_opacity, wg * 32 + lane, n, tiles_x, tiles_y);
   const uint32_t row_incl = warp_inclusive_scan((uint32_t)nr);
   const uint32_t rows = __shfl_sync(0xffffffffu, row_incl, 31);
-  uint32_t sum = 0;
+  uint32_t sum = 0, spans = 0;
   for (uint32_t rb = 0; rb < rows; rb += 32) {
     const uint32_t k = rb + lane;
     int o, ty, x0, x1;
     walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
-    if (k < rows) sum += (uint32_t)(x1 - x0);
+    if (k < rows) {
+      sum += (uint32_t)(x1 - x0);
+      spans += x1 > x0 ? 1u : 0u;
+    }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-  if (lane == 0) wcount[wg] = sum;
+  for (int off = 16; off > 0; off >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    spans += __shfl_xor_sync(0xffffffffu, spans, off);
+  }
+  if (lane == 0) {
+    wcount[wg] = sum;
+    if (A.scount != nullptr) A.scount[wg] = spans;
+  }
 }
 
 // Digit histograms of the tile ids of a row span id0 .. id0 + len - 1 for the tile sort.  Pass 0
@@ -1010,6 +1028,343 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(const Batch<Wal
   flush_digits(s_hist, passes, hist);
 }
 
+// ------------------------------------------------------------------------------------------
+// Span binning (images of at most kSpanMaxTiles tiles per side).  Instead of one record per
+// (tile, Gaussian) instance, the emit walk writes one record per kept row span of a Gaussian, in
+// depth order: key = row | x0 << 8 | (len - 1) << 16, value = Gaussian id.  One stable radix
+// pass over the row puts each row's spans together (still in depth order), and the expansion then
+// writes every span's instances into its tiles' lists: each chunk of a row's spans counts its
+// instances per column (span_count_kernel), and each chunk then finds where its instances go from
+// those counts, places them in (column, depth) order through shared memory and writes every
+// column's run contiguously (span_expand_kernel).  The lists, ranges and instance count are those of the
+// instance path: the tile sort is stable, so a tile's list is its instances in depth order.
+// ------------------------------------------------------------------------------------------
+constexpr int kSpanMaxTiles = 256;   // tiles per side: row and x0 fit 8 bits, len - 1 16 bits
+constexpr int kSpanThreads = 256;
+constexpr int kSpanPer = 4;          // spans per thread per expansion chunk, at most
+constexpr int kSpanWindow = 4096;    // instances staged per round of a chunk's output
+
+__device__ __forceinline__ uint32_t span_key(int row, int x0, int len) {
+  return (uint32_t)row | ((uint32_t)x0 << 8) | ((uint32_t)(len - 1) << 16);
+}
+__device__ __forceinline__ int span_x0(uint32_t k) { return (int)((k >> 8) & 0xffu); }
+__device__ __forceinline__ int span_len(uint32_t k) { return (int)(k >> 16) + 1; }
+
+// Writes the row spans of each warp's 32 depth-ordered Gaussians from the warp's first span
+// sfirst[warp]: a span whose first instance lies at depth-order position >= cap is dropped (and
+// *span_n lowered to its index, so that the spans kept are a prefix), one that crosses cap is cut
+// there.  Accumulates the row histogram for the row sort.  Lanes take one row each (as in
+// walk_count_kernel), so consecutive lanes write consecutive spans.
+__global__ void __launch_bounds__(kWalkThreads) span_emit_kernel(const Batch<WalkArgs> b) {
+  const WalkArgs& A = b.a[blockIdx.y];
+  if (blockIdx.x >= A.grid) return;
+  const uint32_t* __restrict__ order = A.order;
+  const ushort4* __restrict__ rect = A.rect;
+  const float2* __restrict__ mean2d = A.mean2d;
+  const float4* __restrict__ conic_opacity = A.conic_opacity;
+  const int64_t n = A.n;
+  const int tiles_x = A.tiles_x, tiles_y = A.tiles_y;
+  const uint64_t* __restrict__ wfirst = A.wfirst;
+  const uint64_t* __restrict__ sfirst = A.sfirst;
+  const int64_t cap = A.cap;
+  uint32_t* __restrict__ keys = A.keys;
+  uint32_t* __restrict__ vals = A.vals;
+  const uint32_t* err = A.err;
+  griddep_wait();
+  __shared__ WalkWarp s_walk[kWalkWarps];
+  __shared__ uint32_t s_rows[kSpanMaxTiles];
+  for (int i = threadIdx.x; i < kSpanMaxTiles; i += kWalkThreads) s_rows[i] = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
+  if (wg * 32 < n && *err == 0u) {  // uniform over the warp
+    uint64_t pos = wfirst[wg], spos = sfirst[wg];
+    if (pos >= (uint64_t)cap) {
+      if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(A.span_n), (unsigned long long)spos);
+    } else {
+      WalkWarp& w = s_walk[warp];
+      const int nr = walk_setup(w, order, rect, mean2d, conic_opacity, wg * 32 + lane, n, tiles_x, tiles_y);
+      const uint32_t row_incl = warp_inclusive_scan((uint32_t)nr);
+      const uint32_t rows = __shfl_sync(0xffffffffu, row_incl, 31);
+      for (uint32_t rb = 0; rb < rows && pos < (uint64_t)cap; rb += 32) {  // uniform
+        const uint32_t k = rb + lane;
+        int o, ty, x0, x1;
+        walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
+        const uint32_t len = k < rows ? (uint32_t)(x1 - x0) : 0u;
+        const uint32_t incl = warp_inclusive_scan(len);
+        const unsigned has = __ballot_sync(0xffffffffu, len > 0u);
+        if (len > 0u) {
+          const uint64_t ipos = pos + (incl - len);  // depth-order position of the span's first instance
+          const uint64_t sidx = spos + (uint64_t)__popc(has & lt);
+          if (ipos < (uint64_t)cap) {
+            const int keep = (int)min((uint64_t)len, (uint64_t)cap - ipos);
+            keys[sidx] = span_key(ty, x0, keep);
+            vals[sidx] = w.g[o];
+            atomicAdd(&s_rows[ty], 1u);
+          } else {
+            atomicMin(reinterpret_cast<unsigned long long*>(A.span_n), (unsigned long long)sidx);
+          }
+        }
+        pos += __shfl_sync(0xffffffffu, incl, 31);
+        spos += (uint64_t)__popc(has);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tiles_y; i += kWalkThreads) {
+    const uint32_t c = s_rows[i];
+    if (c) atomicAdd(&A.hist[i], c);
+  }
+}
+
+// Words of the expansion's counter table: ceil(tiles_x / 2) lanes of packed 16-bit counters
+// (column c: lane c mod L, half c / L), made odd so that the raking runs hit no bank twice, times
+// the block's threads.
+__host__ __device__ inline int span_lanes(int tiles_x) { return ((tiles_x + 1) / 2) | 1; }
+// Spans per chunk: kSpanThreads times 4, 2 or 1, so that a chunk has fewer than 2^16 instances in
+// either half of the table (at most spans x L).
+__host__ __device__ inline int span_chunk(int tiles_x) {
+  const int L = span_lanes(tiles_x);
+  return kSpanThreads * (L * kSpanThreads * 4 < 65536 ? 4 : (L * kSpanThreads * 2 < 65536 ? 2 : 1));
+}
+inline size_t span_expand_smem(int tiles_x) {
+  return sizeof(uint32_t) * ((size_t)span_lanes(tiles_x) * kSpanThreads + kSpanWindow + 2 * (kSpanMaxTiles + 1));
+}
+
+// One problem's span expansion.  A row's spans are cut into chunks of span_chunk(tiles_x) spans
+// (the last one shorter); chunk b of the whole frame is chunk b - first(row) of its row, where
+// first(row) counts the chunks of the rows before it.
+struct SpanArgs {
+  const uint32_t* keys;       // spans sorted by row
+  const uint32_t* vals;
+  const uint32_t* row_count;  // spans per row (the row sort's digit histogram)
+  const int64_t* span_n;      // spans kept
+  const uint32_t* err;
+  int64_t* nptr;              // instance count: -1 when a sort gave up
+  uint32_t* ctab;             // [chunks][tiles_x]: instances per column of each chunk
+  uint32_t* row_total;        // [tiles_y] instances per row (zeroed before binning)
+  uint2* ranges;
+  uint32_t* point_list;
+  uint32_t* tile_keys;        // optional
+  int tiles_x, tiles_y;
+  unsigned grid;
+};
+
+// Where chunk b lies: its row, its index in the row, its spans [s0, s1), and the instances of the
+// rows before it (when row_total is given).  Returns false (for every thread) when b is past the
+// frame's last chunk.  Synchronises the block; blockDim.x >= tiles_y.
+struct ChunkPos {
+  int row, index, chunks;  // chunks: the row's chunk count
+  int64_t first, s0, s1;   // first: the frame index of the row's first chunk
+  uint32_t row_base;
+};
+
+__device__ __forceinline__ bool locate_chunk(const uint32_t* __restrict__ row_count,
+                                             const uint32_t* __restrict__ row_total, int tiles_y, int chunk,
+                                             int64_t b, ChunkPos* pos) {
+  __shared__ ChunkPos s_pos;
+  __shared__ int s_found;
+  if (threadIdx.x == 0) s_found = 0;
+  const int r = threadIdx.x;
+  const uint32_t cnt = r < tiles_y ? row_count[r] : 0u;
+  const uint32_t nch = (cnt + (uint32_t)chunk - 1u) / (uint32_t)chunk;
+  const uint32_t tot = (row_total != nullptr && r < tiles_y) ? row_total[r] : 0u;
+  uint32_t all;
+  const uint32_t ch_incl = block_inclusive_scan<uint32_t, kSpanThreads>(nch, &all);
+  const uint32_t sp_incl = block_inclusive_scan<uint32_t, kSpanThreads>(cnt, &all);
+  const uint32_t in_incl = block_inclusive_scan<uint32_t, kSpanThreads>(tot, &all);
+  const int64_t first = (int64_t)(ch_incl - nch);
+  if (r < tiles_y && b >= first && b < first + (int64_t)nch) {
+    const int idx = (int)(b - first);
+    const int64_t a = (int64_t)(sp_incl - cnt);
+    s_pos.row = r;
+    s_pos.index = idx;
+    s_pos.chunks = (int)nch;
+    s_pos.first = first;
+    s_pos.s0 = a + (int64_t)idx * chunk;
+    s_pos.s1 = min(a + (int64_t)cnt, s_pos.s0 + chunk);
+    s_pos.row_base = in_incl - tot;
+    s_found = 1;
+  }
+  __syncthreads();
+  *pos = s_pos;
+  return s_found != 0;
+}
+
+// Instances per column of one chunk (a difference array over the columns), and the row's total.
+// If a sort gave up waiting, the instance count becomes -1 and nothing else is written, so that no
+// later kernel reads the lists and every reader of the count sees the failure.
+__global__ void __launch_bounds__(kSpanThreads) span_count_kernel(const Batch<SpanArgs> b) {
+  const SpanArgs& A = b.a[blockIdx.y];
+  if (blockIdx.x >= A.grid) return;
+  griddep_wait();
+  const int tx = A.tiles_x;
+  const int chunk = span_chunk(tx);
+  if (*A.err != 0u) {  // a sort gave up: the instance count becomes -1 (the ranges stay empty)
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.nptr = -1;
+    return;
+  }
+  // chunks never exceed ceil(spans / chunk) + rows: skip the launch's spare blocks at once
+  if ((int64_t)blockIdx.x >= (*A.span_n + chunk - 1) / chunk + A.tiles_y) return;
+  __shared__ int s_diff[kSpanMaxTiles + 1];
+  for (int c = threadIdx.x; c <= tx; c += kSpanThreads) s_diff[c] = 0;
+  ChunkPos pos;
+  if (!locate_chunk(A.row_count, nullptr, A.tiles_y, chunk, blockIdx.x, &pos)) return;
+  for (int64_t i = pos.s0 + threadIdx.x; i < pos.s1; i += kSpanThreads) {
+    const uint32_t k = A.keys[i];
+    const int x0 = span_x0(k);
+    atomicAdd(&s_diff[x0], 1);
+    atomicAdd(&s_diff[min(x0 + span_len(k), tx)], -1);
+  }
+  __syncthreads();
+  int tot;
+  const int c = threadIdx.x;
+  const int incl = block_inclusive_scan<int, kSpanThreads>(c < tx ? s_diff[c] : 0, &tot);
+  if (c < tx) A.ctab[(size_t)blockIdx.x * tx + c] = (uint32_t)incl;
+  int all;
+  block_inclusive_scan<int, kSpanThreads>(c < tx ? incl : 0, &all);
+  if (c == 0 && all > 0) atomicAdd(&A.row_total[pos.row], (uint32_t)all);
+}
+
+// Expands one chunk into its tiles' lists.  Thread t takes per = chunk / kSpanThreads consecutive
+// spans and writes, in its own column of the counter table, how many of them cover each column (a
+// difference array summed along the column).  An exclusive scan of the table in (column, thread)
+// order then gives each (column, thread) its first position among the chunk's instances ordered by
+// (column, depth); a span's instance at column c goes there plus the thread's earlier spans
+// covering c.  The instances are staged in shared memory (kSpanWindow at a time) and each
+// column's run is written contiguously at its place in the tile's list: after the instances of the
+// rows before, of the row's tiles to the left, and of the row's earlier chunks at that column (all
+// from the chunks' column counts).  The row's first chunk also writes the row's tile ranges.
+__global__ void __launch_bounds__(kSpanThreads) span_expand_kernel(const Batch<SpanArgs> b) {
+  const SpanArgs& A = b.a[blockIdx.y];
+  if (blockIdx.x >= A.grid) return;
+  griddep_wait();
+  const int tx = A.tiles_x;
+  const int chunk = span_chunk(tx), per = chunk / kSpanThreads;
+  if ((int64_t)blockIdx.x >= (*A.span_n + chunk - 1) / chunk + A.tiles_y || *A.err != 0u) return;
+  ChunkPos pos;
+  if (!locate_chunk(A.row_count, A.row_total, A.tiles_y, chunk, blockIdx.x, &pos)) return;
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  const int L = span_lanes(tx);
+  uint32_t* s_tab = s_dyn;                          // [L][kSpanThreads]
+  uint32_t* s_stage = s_tab + L * kSpanThreads;     // [kSpanWindow]
+  uint32_t* s_cpos = s_stage + kSpanWindow;         // [tx + 1] chunk position of each column's run
+  uint32_t* s_goff = s_cpos + (kSpanMaxTiles + 1);  // [tx] list position of each column's run
+  const int row = pos.row;
+  const uint32_t tile0 = (uint32_t)row * (uint32_t)tx;
+  const int t = threadIdx.x;
+  {  // per column: the instances of the row's chunks before this one, and of all of them
+    __shared__ uint32_t s_bp[kSpanThreads], s_tp[kSpanThreads];
+    const int g = kSpanThreads / tx;  // threads per column
+    const int c = t % tx, k = t / tx;
+    uint32_t before = 0, all = 0;
+    if (k < g)
+      for (int j = k; j < pos.chunks; j += g) {
+        const uint32_t v = A.ctab[(size_t)(pos.first + j) * tx + c];
+        all += v;
+        before += j < pos.index ? v : 0u;
+      }
+    s_bp[t] = before;
+    s_tp[t] = all;
+    __syncthreads();
+    before = all = 0;
+    if (t < tx)
+      for (int kk = 0; kk < g; ++kk) {
+        before += s_bp[kk * tx + t];
+        all += s_tp[kk * tx + t];
+      }
+    uint32_t row_all;
+    const uint32_t start = pos.row_base + block_inclusive_scan<uint32_t, kSpanThreads>(all, &row_all) - all;
+    if (t < tx) {
+      s_goff[t] = start + before;
+      if (pos.index == 0) A.ranges[tile0 + t] = make_uint2(start, start + all);
+    }
+  }
+  int x0[kSpanPer], len[kSpanPer];
+  uint32_t gid[kSpanPer];
+  uint32_t carry = 0;  // my spans covering column L - 1 (the low half's last column)
+#pragma unroll
+  for (int i = 0; i < kSpanPer; ++i) {
+    const int64_t s = pos.s0 + (int64_t)t * per + i;
+    const bool in = i < per && s < pos.s1;
+    const uint32_t k = in ? A.keys[s] : 0u;
+    gid[i] = in ? A.vals[s] : 0u;
+    x0[i] = span_x0(k);
+    len[i] = in ? span_len(k) : 0;
+    carry += (len[i] > 0 && x0[i] <= L - 1 && x0[i] + len[i] > L - 1) ? 1u : 0u;
+  }
+  // my column of the table: +1 where a span starts, -1 after it ends, then summed along the column
+  for (int k = 0; k < L; ++k) s_tab[k * kSpanThreads + t] = 0u;
+#pragma unroll
+  for (int i = 0; i < kSpanPer; ++i) {
+    if (len[i] == 0) continue;
+    const int c0 = x0[i], c1 = x0[i] + len[i];
+    const int h0 = c0 >= L;
+    s_tab[(c0 - h0 * L) * kSpanThreads + t] += 1u << (16 * h0);
+    if (c1 < 2 * L) {  // (columns tx .. 2L - 1 do not exist: they must count nothing)
+      const int h1 = c1 >= L;
+      s_tab[(c1 - h1 * L) * kSpanThreads + t] -= 1u << (16 * h1);
+    }
+  }
+  {
+    uint32_t run = carry << 16;  // the high half continues from column L - 1
+    for (int k = 0; k < L; ++k) {
+      run += s_tab[k * kSpanThreads + t];
+      s_tab[k * kSpanThreads + t] = run;
+    }
+  }
+  __syncthreads();
+  uint32_t tot;
+  {
+    uint32_t* seg = s_tab + t * L;
+    uint32_t sum = 0;
+    for (int k = 0; k < L; ++k) sum += seg[k];
+    uint32_t pre = block_inclusive_scan<uint32_t, kSpanThreads>(sum, &tot) - sum;
+    for (int k = 0; k < L; ++k) {
+      const uint32_t v = seg[k];
+      seg[k] = pre;
+      pre += v;
+    }
+  }
+  __syncthreads();
+  const uint32_t low = tot & 0xffffu, total = low + (tot >> 16);
+  for (int c = t; c <= tx; c += kSpanThreads) {
+    if (c == tx) {
+      s_cpos[c] = total;
+    } else {
+      const int h = c >= L;
+      s_cpos[c] = ((s_tab[(c - h * L) * kSpanThreads] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
+    }
+  }
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+  uint32_t* __restrict__ out = A.point_list;
+  uint32_t* __restrict__ out_keys = A.tile_keys;
+  for (uint32_t w0 = 0; w0 < total; w0 += kSpanWindow) {  // uniform
+#pragma unroll
+    for (int i = 0; i < kSpanPer; ++i)
+      for (int c = x0[i]; c < x0[i] + len[i]; ++c) {
+        const int h = c >= L;
+        uint32_t q = ((s_tab[(c - h * L) * kSpanThreads + t] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
+#pragma unroll
+        for (int j = 0; j < i; ++j) q += (c >= x0[j] && c < x0[j] + len[j]) ? 1u : 0u;
+        if (q >= w0 && q < w0 + kSpanWindow) s_stage[q - w0] = gid[i];
+      }
+    __syncthreads();
+    const uint32_t wend = min(total, w0 + (uint32_t)kSpanWindow);
+    for (int c = warp; c < tx; c += kSpanThreads / 32) {  // a warp per column run
+      const uint32_t q0 = max(s_cpos[c], w0), q1 = min(s_cpos[c + 1], wend);
+      const uint32_t g0 = s_goff[c] + (q0 - s_cpos[c]);
+      for (uint32_t q = q0 + lane; q < q1; q += 32) {
+        out[g0 + (q - q0)] = s_stage[q - w0];
+        if (out_keys != nullptr) out_keys[g0 + (q - q0)] = tile0 + (uint32_t)c;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // First position in keys[0, n) (sorted) whose key is >= t, found by the calling warp: each round
 // probes 32 evenly spaced positions of [lo, hi) and keeps the part between the last probe below t
 // and the first probe at or above it (32 times shorter), until [lo, hi) is empty.  All 32 lanes
@@ -1110,6 +1465,26 @@ cudaError_t launch_lookback_selftest(const uint32_t* keys, const uint32_t* vals,
   return e2 != cudaSuccess ? e2 : cudaGetLastError();
 }
 
+// The expansion's dynamic shared memory goes past the 48 KB default for wide images: opt in to
+// the largest size it uses, once per device.
+cudaError_t allow_span_expand_smem() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(span_expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)span_expand_smem(kSpanMaxTiles));
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   BinPlan p;
   p.n = n;
@@ -1118,7 +1493,12 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   int bits = 0;
   while ((int64_t(1) << bits) < p.num_tiles) ++bits;
   p.tile_bits = bits;
+  const int tx = tiles_of(width), ty = tiles_of(height);
+  p.spans = tx <= kSpanMaxTiles && ty <= kSpanMaxTiles;
+  p.row_bits = 0;
+  while ((1 << p.row_bits) < ty) ++p.row_bits;
   p.partial_cap = (n + kScanChunk - 1) / kScanChunk + 1;
+  const int64_t nwarps = (n + 31) / 32;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) { p.off_dkeys[k] = off; off += align256(sizeof(uint32_t) * n); }
   for (int k = 0; k < 2; ++k) { p.off_dvals[k] = off; off += align256(sizeof(uint32_t) * n); }
@@ -1128,8 +1508,18 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   p.off_ivals = off; off += align256(sizeof(uint32_t) * capacity);
   p.off_err = off; off += 256;
   p.off_sort_d = off; off += align256(sort_scratch_bytes(n, 32));
-  p.off_sort_t = off; off += align256(sort_scratch_bytes(capacity, bits));
+  p.off_sort_t = off; off += align256(sort_scratch_bytes(capacity, p.spans ? p.row_bits : bits));
   p.off_partials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
+  p.off_svals = p.off_sfirst = p.off_span_n = p.off_spartials = p.off_ctab = p.off_rowtot = 0;
+  if (p.spans) {
+    p.off_svals = off; off += align256(sizeof(uint32_t) * capacity);
+    p.off_sfirst = off; off += align256(sizeof(uint64_t) * nwarps);
+    p.off_span_n = off; off += 256;
+    p.off_spartials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
+    const int64_t chunks = (capacity + span_chunk(tx) - 1) / span_chunk(tx) + ty;  // at most
+    p.off_ctab = off; off += align256(sizeof(uint32_t) * (size_t)chunks * tx);
+    p.off_rowtot = off; off += align256(sizeof(uint32_t) * (size_t)ty);
+  }
   p.total = off;
   return p;
 }
@@ -1142,6 +1532,9 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     int tiles_x, tiles_y;
     uint32_t *dkeys[2], *dvals[2], *sort_d, *sort_t, *err, *out_keys, *ikeys[2], *ivals[2];
     uint64_t *first, *partials;
+    uint32_t *skeys[2], *svals[2], *ctab, *rowtot;  // span binning
+    uint64_t *sfirst, *spartials;
+    int64_t* span_n;
     const ushort4* rect;
     const float2* m2;
     const float4* co;
@@ -1179,13 +1572,26 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     w.ivals[0] = even ? R.out.point_list : wv0;
     w.ikeys[1] = even ? wk0 : w.out_keys;
     w.ivals[1] = even ? wv0 : R.out.point_list;
+    if (plan.spans) {  // spans ping-pong in the workspace; the expansion writes the outputs
+      w.skeys[0] = wk0;
+      w.skeys[1] = reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[1]);
+      w.svals[0] = wv0;
+      w.svals[1] = reinterpret_cast<uint32_t*>(ws + plan.off_svals);
+      w.sfirst = reinterpret_cast<uint64_t*>(ws + plan.off_sfirst);
+      w.span_n = reinterpret_cast<int64_t*>(ws + plan.off_span_n);
+      w.spartials = reinterpret_cast<uint64_t*>(ws + plan.off_spartials);
+      w.ctab = reinterpret_cast<uint32_t*>(ws + plan.off_ctab);
+      w.rowtot = reinterpret_cast<uint32_t*>(ws + plan.off_rowtot);
+    }
     ClearJob c;
-    // (with Gaussians, the ranges kernel writes every tile's range)
-    c.ptr[0] = w.n == 0 ? R.out.ranges : nullptr; c.words[0] = 2 * (size_t)plan.num_tiles;
+    // (with Gaussians, the ranges or span starts kernel writes every tile's range)
+    c.ptr[0] = (w.n == 0 || plan.spans) ? R.out.ranges : nullptr; c.words[0] = 2 * (size_t)plan.num_tiles;
     c.ptr[1] = w.err; c.words[1] = 1;
-    c.ptr[2] = w.n == 0 ? reinterpret_cast<uint32_t*>(R.out.num_instances) : nullptr; c.words[2] = 2;
+    c.ptr[2] = w.n == 0 ? reinterpret_cast<uint32_t*>(R.out.num_instances) : (plan.spans ? w.rowtot : nullptr);
+    c.words[2] = w.n == 0 ? 2 : (size_t)w.tiles_y;
     c.ptr[3] = w.n > 0 ? w.sort_d : nullptr; c.words[3] = sort_scratch_bytes(w.n, 32) / 4;
-    c.ptr[4] = w.n > 0 ? w.sort_t : nullptr; c.words[4] = sort_scratch_bytes(plan.capacity, plan.tile_bits) / 4;
+    c.ptr[4] = w.n > 0 ? w.sort_t : nullptr;
+    c.words[4] = sort_scratch_bytes(plan.capacity, plan.spans ? plan.row_bits : plan.tile_bits) / 4;
     size_t most = 0;
     for (int k = 0; k < 5; ++k) most = std::max(most, c.ptr[k] ? c.words[k] : 0);
     c.grid = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * (size_t)device_sm_count()));
@@ -1217,9 +1623,11 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
   }
   if ((e = launch_batch(depth_keys_kernel, keys, kRadixThreads, 0, st)) != cudaSuccess) return e;
   if ((e = radix_sort(dsort, nl, true, st, dcur)) != cudaSuccess) return e;
-  // 2. Kept tiles per warp of 32 depth-ordered Gaussians (row spans); first instance of each warp; K.
+  // 2. Kept tiles per warp of 32 depth-ordered Gaussians (row spans), and for span binning the
+  //    kept row spans per warp; first instance (and first span) of each warp; K.
   BatchLaunch<WalkArgs> walks;
-  ScanArgs<uint32_t, uint64_t> scans[kMaxBatch];
+  ScanArgs<uint32_t, uint64_t> scans[2 * kMaxBatch];
+  int nscan = 0;
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     const BinRequest& R = reqs[live[i]];
@@ -1230,38 +1638,73 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     a.tiles_x = w.tiles_x; a.tiles_y = w.tiles_y; a.err = w.err;
     a.wcount = w.dkeys[dcur[i] ^ 1];
     a.wfirst = w.first; a.cap = R.plan.capacity;
-    a.keys = w.ikeys[0]; a.vals = w.ivals[0];
-    a.passes = radix_pass_count(R.plan.tile_bits); a.width = radix_digit_width(R.plan.tile_bits);
     a.hist = w.sort_t;
+    if (R.plan.spans) {
+      a.scount = w.dvals[dcur[i] ^ 1];
+      a.sfirst = w.sfirst;
+      a.span_n = w.span_n;
+      a.keys = w.skeys[0]; a.vals = w.svals[0];
+    } else {
+      a.keys = w.ikeys[0]; a.vals = w.ivals[0];
+      a.passes = radix_pass_count(R.plan.tile_bits); a.width = radix_digit_width(R.plan.tile_bits);
+    }
     a.grid = (unsigned)((nwarps + kWalkWarps - 1) / kWalkWarps);
     walks.add(a);
-    scans[i] = ScanArgs<uint32_t, uint64_t>{a.wcount, nwarps, w.first, reinterpret_cast<uint64_t*>(w.partials),
-                                            R.out.num_instances, 0};
+    scans[nscan++] = ScanArgs<uint32_t, uint64_t>{a.wcount, nwarps, w.first, reinterpret_cast<uint64_t*>(w.partials),
+                                                  R.out.num_instances, 0};
+    if (R.plan.spans)
+      scans[nscan++] = ScanArgs<uint32_t, uint64_t>{a.scount, nwarps, w.sfirst, w.spartials, w.span_n, 0};
   }
   if ((e = launch_batch(walk_count_kernel, walks, kWalkThreads, 0, st)) != cudaSuccess) return e;
-  if ((e = exclusive_scan(scans, nl, st)) != cudaSuccess) return e;
-  // 3. Instances in depth order (with the tile-digit histograms); 4. stable sort by tile id.
-  if ((e = launch_batch(walk_emit_kernel, walks, kWalkThreads, 0, st)) != cudaSuccess) return e;
+  for (int s0 = 0; s0 < nscan; s0 += kMaxBatch)
+    if ((e = exclusive_scan(scans + s0, std::min(kMaxBatch, nscan - s0), st)) != cudaSuccess) return e;
+  // 3. Instances (or row spans) in depth order, with the digit histograms of the sort that follows;
+  // 4. stable sort by tile id (or by row).
+  BatchLaunch<WalkArgs> iemit, semit;
+  for (int i = 0; i < nl; ++i) (reqs[live[i]].plan.spans ? semit : iemit).add(walks.b.a[i]);
+  if ((e = launch_batch(walk_emit_kernel, iemit, kWalkThreads, 0, st)) != cudaSuccess) return e;
+  if ((e = launch_batch(span_emit_kernel, semit, kWalkThreads, 0, st)) != cudaSuccess) return e;
   SortJob tsort[kMaxBatch];
   int tcur[kMaxBatch];
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     const BinRequest& R = reqs[live[i]];
-    tsort[i] = SortJob{{w.ikeys[0], w.ikeys[1]}, {w.ivals[0], w.ivals[1]}, R.out.num_instances, 0,
-                       R.plan.capacity, R.plan.tile_bits, w.sort_t, w.err, kMaxPasses};
+    if (R.plan.spans)
+      tsort[i] = SortJob{{w.skeys[0], w.skeys[1]}, {w.svals[0], w.svals[1]}, w.span_n, 0,
+                         R.plan.capacity, R.plan.row_bits, w.sort_t, w.err, kMaxPasses};
+    else
+      tsort[i] = SortJob{{w.ikeys[0], w.ikeys[1]}, {w.ivals[0], w.ivals[1]}, R.out.num_instances, 0,
+                         R.plan.capacity, R.plan.tile_bits, w.sort_t, w.err, kMaxPasses};
   }
   if ((e = radix_sort(tsort, nl, true, st, tcur)) != cudaSuccess) return e;
-  // 5. Tile ranges.
+  // 5. Tile ranges (instance records), or the span expansion into the tile lists.
   BatchLaunch<RangesArgs> ranges;
+  BatchLaunch<SpanArgs> scnt, sexp;
+  size_t sexp_smem = 0;
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     const BinRequest& R = reqs[live[i]];
-    RangesArgs a{w.out_keys, R.out.num_instances, R.plan.capacity, (int)R.plan.num_tiles, w.err,
-                 reinterpret_cast<uint2*>(R.out.ranges),
-                 (unsigned)((R.plan.num_tiles + kRangeTiles - 1) / kRangeTiles)};
-    ranges.add(a);
+    if (R.plan.spans) {
+      const int64_t chunks = (R.plan.capacity + span_chunk(w.tiles_x) - 1) / span_chunk(w.tiles_x) + w.tiles_y;
+      SpanArgs a{w.skeys[tcur[i]], w.svals[tcur[i]], w.sort_t, w.span_n, w.err, R.out.num_instances, w.ctab,
+                 w.rowtot, reinterpret_cast<uint2*>(R.out.ranges), R.out.point_list, R.out.tile_keys,
+                 w.tiles_x, w.tiles_y, (unsigned)chunks};
+      scnt.add(a);
+      sexp.add(a);
+      sexp_smem = std::max(sexp_smem, span_expand_smem(w.tiles_x));
+    } else {
+      const int64_t blocks = (R.plan.num_tiles + kRangeTiles - 1) / kRangeTiles;
+      RangesArgs a{w.out_keys, R.out.num_instances, R.plan.capacity, (int)R.plan.num_tiles, w.err,
+                   reinterpret_cast<uint2*>(R.out.ranges), (unsigned)blocks};
+      ranges.add(a);
+    }
   }
   if ((e = launch_batch(ranges_kernel, ranges, (kRangeTiles + 1) * 32, 0, st)) != cudaSuccess) return e;
+  if (sexp.count > 0) {
+    if ((e = allow_span_expand_smem()) != cudaSuccess) return e;
+    if ((e = launch_batch(span_count_kernel, scnt, kSpanThreads, 0, st)) != cudaSuccess) return e;
+    if ((e = launch_batch(span_expand_kernel, sexp, kSpanThreads, sexp_smem, st)) != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

@@ -65,9 +65,12 @@ struct BinPlan {
   int64_t capacity;
   int num_tiles;
   int tile_bits;
+  bool spans;    // row-span binning (both tile counts <= 256); else instance records and a tile sort
+  int row_bits;  // span binning: bits of the row sort
   // workspace carve-up (byte offsets)
   size_t off_dkeys[2], off_dvals[2], off_first, off_ikeys[2], off_ivals, off_err, off_sort_d, off_sort_t,
       off_partials, total;
+  size_t off_svals, off_sfirst, off_span_n, off_spartials, off_ctab, off_rowtot;  // span binning only
   int64_t partial_cap;  // entries available for scan partials
 };
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);

@@ -55,14 +55,18 @@ def test_slice_project_records(scene0, ci, dir_mode):
 def _random_bin_cases():
     return [
         (0, 64, 64, 0),          # no Gaussians
-        (1, 16, 16, 1),          # one tile: zero tile bits, no tile pass
+        (1, 16, 16, 1),          # one tile: one row, no row pass
         (300, 100, 70, 2),       # ragged image, 7 x 5 tiles
-        (5000, 256, 256, 3),     # one tile pass, several radix blocks of Gaussians
-        (20000, 1352, 1014, 4),  # two tile passes (5440 tiles), K spans many blocks
+        (5000, 256, 256, 3),     # several radix blocks of Gaussians
+        (20000, 1352, 1014, 4),  # 85 x 64 tiles, the row spans of many sort blocks
         (3000, 1920, 1080, 5),   # 8160 tiles
         (600_000, 800, 800, 6),  # hundreds of sort tiles in both sorts
-        (16000, 48, 32, 9),      # tile lists of 8.8k-10k instances: per-tile sorts through global memory
-        (20000, 2048, 2048, 8),  # 16384 tiles: the tile radix passes of large grids
+        (16000, 48, 32, 9),      # tile lists of 8.8k-10k instances
+        (20000, 2048, 2048, 8),  # 128 x 128 tiles
+        (2000, 16, 600, 12),     # one tile column
+        (3000, 4096, 48, 13),    # 256 tiles per row: the widest rows of span binning
+        (4000, 4224, 64, 10),    # 264 tiles per row: instance records and the tile radix sort
+        (4000, 64, 4224, 11),    # 264 tile rows: instance records and the tile radix sort
     ]
 
 

@@ -41,12 +41,12 @@ def test_static_scratch_binning_matches_workspace_binning(case):
         rec = synth.random_projected(20000, 1352, 1014, seed=4, max_half_tiles=12)
         proj = sdgs.ProjectedBuffers.from_host(rec)
         view = sdgs.view_struct(synth.make_camera((0, 0, -3), 1352, 1014, 60.0, 0.5))
-    ref_bins = sdgs.BinBuffers(proj.n, 4_000_000, view.width, view.height)
+    ref_bins = sdgs.BinBuffers(proj.n, 2_000_000, view.width, view.height)
     k_ref = sdgs.bin_sort(proj, view, ref_bins, sync=True)
     want = _bins_host(ref_bins, k_ref)
     assert k_ref > 0
     for _ in range(2):  # two calls in a row share the scratch array
-        out = sdgs.BinBuffers(proj.n, 4_000_000, view.width, view.height)
+        out = sdgs.BinBuffers(proj.n, 2_000_000, view.width, view.height)
         out.point_list.fill_(-1)
         k = ctypes.c_int64(-1)
         rc = sdgs.lib().sdgs_bin_sort_static(ctypes.byref(proj.struct()), ctypes.byref(view),
