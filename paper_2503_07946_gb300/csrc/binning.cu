@@ -1042,7 +1042,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(const Batch<Wal
 constexpr int kSpanMaxTiles = 256;   // tiles per side: row and x0 fit 8 bits, len - 1 16 bits
 constexpr int kSpanThreads = 256;
 constexpr int kSpanPer = 4;          // spans per thread per expansion chunk, at most
-constexpr int kSpanWindow = 4096;    // instances staged per round of a chunk's output
+constexpr int kSpanWindow = 8192;    // instances staged per round of a chunk's output
 
 __device__ __forceinline__ uint32_t span_key(int row, int x0, int len) {
   return (uint32_t)row | ((uint32_t)x0 << 8) | ((uint32_t)(len - 1) << 16);
@@ -1143,7 +1143,7 @@ struct SpanArgs {
   const uint32_t* err;
   int64_t* nptr;              // instance count: -1 when a sort gave up
   uint32_t* ctab;             // [chunks][tiles_x]: instances per column of each chunk
-  uint32_t* row_total;        // [tiles_y] instances per row (zeroed before binning)
+  uint32_t* row_total;        // [tiles_y] instances per row, then [tiles_y][tiles_x] per tile (zeroed first)
   uint2* ranges;
   uint32_t* point_list;
   uint32_t* tile_keys;        // optional
@@ -1192,7 +1192,8 @@ __device__ __forceinline__ bool locate_chunk(const uint32_t* __restrict__ row_co
   return s_found != 0;
 }
 
-// Instances per column of one chunk (a difference array over the columns), and the row's total.
+// Instances per column of each chunk (a difference array over the columns), summed into the
+// row's and the tiles' totals.
 // If a sort gave up waiting, the instance count becomes -1 and nothing else is written, so that no
 // later kernel reads the lists and every reader of the count sees the failure.
 __global__ void __launch_bounds__(kSpanThreads) span_count_kernel(const Batch<SpanArgs> b) {
@@ -1205,26 +1206,32 @@ __global__ void __launch_bounds__(kSpanThreads) span_count_kernel(const Batch<Sp
     if (blockIdx.x == 0 && threadIdx.x == 0) *A.nptr = -1;
     return;
   }
-  // chunks never exceed ceil(spans / chunk) + rows: skip the launch's spare blocks at once
-  if ((int64_t)blockIdx.x >= (*A.span_n + chunk - 1) / chunk + A.tiles_y) return;
+  // chunks never exceed ceil(spans / chunk) + rows; the blocks stride over them
+  const int64_t bound = (*A.span_n + chunk - 1) / chunk + A.tiles_y;
+  uint32_t* tile_total = A.row_total + A.tiles_y;
   __shared__ int s_diff[kSpanMaxTiles + 1];
-  for (int c = threadIdx.x; c <= tx; c += kSpanThreads) s_diff[c] = 0;
-  ChunkPos pos;
-  if (!locate_chunk(A.row_count, nullptr, A.tiles_y, chunk, blockIdx.x, &pos)) return;
-  for (int64_t i = pos.s0 + threadIdx.x; i < pos.s1; i += kSpanThreads) {
-    const uint32_t k = A.keys[i];
-    const int x0 = span_x0(k);
-    atomicAdd(&s_diff[x0], 1);
-    atomicAdd(&s_diff[min(x0 + span_len(k), tx)], -1);
+  for (int64_t b = blockIdx.x; b < bound; b += A.grid) {  // uniform over the block
+    for (int c = threadIdx.x; c <= tx; c += kSpanThreads) s_diff[c] = 0;
+    ChunkPos pos;
+    if (!locate_chunk(A.row_count, nullptr, A.tiles_y, chunk, b, &pos)) return;
+    for (int64_t i = pos.s0 + threadIdx.x; i < pos.s1; i += kSpanThreads) {
+      const uint32_t k = A.keys[i];
+      const int x0 = span_x0(k);
+      atomicAdd(&s_diff[x0], 1);
+      atomicAdd(&s_diff[min(x0 + span_len(k), tx)], -1);
+    }
+    __syncthreads();
+    int tot;
+    const int c = threadIdx.x;
+    const int incl = block_inclusive_scan<int, kSpanThreads>(c < tx ? s_diff[c] : 0, &tot);
+    if (c < tx) {
+      A.ctab[(size_t)b * tx + c] = (uint32_t)incl;
+      if (incl > 0) atomicAdd(&tile_total[pos.row * tx + c], (uint32_t)incl);
+    }
+    int all;
+    block_inclusive_scan<int, kSpanThreads>(c < tx ? incl : 0, &all);
+    if (c == 0 && all > 0) atomicAdd(&A.row_total[pos.row], (uint32_t)all);
   }
-  __syncthreads();
-  int tot;
-  const int c = threadIdx.x;
-  const int incl = block_inclusive_scan<int, kSpanThreads>(c < tx ? s_diff[c] : 0, &tot);
-  if (c < tx) A.ctab[(size_t)blockIdx.x * tx + c] = (uint32_t)incl;
-  int all;
-  block_inclusive_scan<int, kSpanThreads>(c < tx ? incl : 0, &all);
-  if (c == 0 && all > 0) atomicAdd(&A.row_total[pos.row], (uint32_t)all);
 }
 
 // Expands one chunk into its tiles' lists.  Thread t takes per = chunk / kSpanThreads consecutive
@@ -1242,124 +1249,123 @@ __global__ void __launch_bounds__(kSpanThreads) span_expand_kernel(const Batch<S
   griddep_wait();
   const int tx = A.tiles_x;
   const int chunk = span_chunk(tx), per = chunk / kSpanThreads;
-  if ((int64_t)blockIdx.x >= (*A.span_n + chunk - 1) / chunk + A.tiles_y || *A.err != 0u) return;
-  ChunkPos pos;
-  if (!locate_chunk(A.row_count, A.row_total, A.tiles_y, chunk, blockIdx.x, &pos)) return;
+  if (*A.err != 0u) return;
+  // chunks never exceed ceil(spans / chunk) + rows; the blocks stride over them
+  const int64_t bound = (*A.span_n + chunk - 1) / chunk + A.tiles_y;
+  const uint32_t* tile_total = A.row_total + A.tiles_y;
   extern __shared__ __align__(16) uint32_t s_dyn[];
   const int L = span_lanes(tx);
   uint32_t* s_tab = s_dyn;                          // [L][kSpanThreads]
   uint32_t* s_stage = s_tab + L * kSpanThreads;     // [kSpanWindow]
   uint32_t* s_cpos = s_stage + kSpanWindow;         // [tx + 1] chunk position of each column's run
   uint32_t* s_goff = s_cpos + (kSpanMaxTiles + 1);  // [tx] list position of each column's run
-  const int row = pos.row;
-  const uint32_t tile0 = (uint32_t)row * (uint32_t)tx;
+  __shared__ uint32_t s_bp[kSpanThreads];
   const int t = threadIdx.x;
-  {  // per column: the instances of the row's chunks before this one, and of all of them
-    __shared__ uint32_t s_bp[kSpanThreads], s_tp[kSpanThreads];
-    const int g = kSpanThreads / tx;  // threads per column
-    const int c = t % tx, k = t / tx;
-    uint32_t before = 0, all = 0;
-    if (k < g)
-      for (int j = k; j < pos.chunks; j += g) {
-        const uint32_t v = A.ctab[(size_t)(pos.first + j) * tx + c];
-        all += v;
-        before += j < pos.index ? v : 0u;
+  for (int64_t bc = blockIdx.x; bc < bound; bc += A.grid) {  // uniform over the block
+    ChunkPos pos;
+    if (!locate_chunk(A.row_count, A.row_total, A.tiles_y, chunk, bc, &pos)) return;
+    const int row = pos.row;
+    const uint32_t tile0 = (uint32_t)row * (uint32_t)tx;
+    {  // per column: the row's instances to the left of the tile, and the row's earlier chunks' at it
+      const int g = kSpanThreads / tx;  // threads per column
+      const int c = t % tx, k = t / tx;
+      uint32_t before = 0;
+      if (k < g)
+        for (int j = k; j < pos.index; j += g) before += A.ctab[(size_t)(pos.first + j) * tx + c];
+      s_bp[t] = before;
+      __syncthreads();
+      before = 0;
+      const uint32_t all = t < tx ? tile_total[tile0 + t] : 0u;
+      if (t < tx)
+        for (int kk = 0; kk < g; ++kk) before += s_bp[kk * tx + t];
+      uint32_t row_all;
+      const uint32_t start = pos.row_base + block_inclusive_scan<uint32_t, kSpanThreads>(all, &row_all) - all;
+      if (t < tx) {
+        s_goff[t] = start + before;
+        if (pos.index == 0) A.ranges[tile0 + t] = make_uint2(start, start + all);
       }
-    s_bp[t] = before;
-    s_tp[t] = all;
+    }
+    int x0[kSpanPer], len[kSpanPer];
+    uint32_t gid[kSpanPer];
+    uint32_t carry = 0;  // my spans covering column L - 1 (the low half's last column)
+#pragma unroll
+    for (int i = 0; i < kSpanPer; ++i) {
+      const int64_t s = pos.s0 + (int64_t)t * per + i;
+      const bool in = i < per && s < pos.s1;
+      const uint32_t k = in ? A.keys[s] : 0u;
+      gid[i] = in ? A.vals[s] : 0u;
+      x0[i] = span_x0(k);
+      len[i] = in ? span_len(k) : 0;
+      carry += (len[i] > 0 && x0[i] <= L - 1 && x0[i] + len[i] > L - 1) ? 1u : 0u;
+    }
+    // my column of the table: +1 where a span starts, -1 after it ends, then summed along the column
+    for (int k = 0; k < L; ++k) s_tab[k * kSpanThreads + t] = 0u;
+#pragma unroll
+    for (int i = 0; i < kSpanPer; ++i) {
+      if (len[i] == 0) continue;
+      const int c0 = x0[i], c1 = x0[i] + len[i];
+      const int h0 = c0 >= L;
+      s_tab[(c0 - h0 * L) * kSpanThreads + t] += 1u << (16 * h0);
+      if (c1 < 2 * L) {  // (columns tx .. 2L - 1 do not exist: they must count nothing)
+        const int h1 = c1 >= L;
+        s_tab[(c1 - h1 * L) * kSpanThreads + t] -= 1u << (16 * h1);
+      }
+    }
+    {
+      uint32_t run = carry << 16;  // the high half continues from column L - 1
+      for (int k = 0; k < L; ++k) {
+        run += s_tab[k * kSpanThreads + t];
+        s_tab[k * kSpanThreads + t] = run;
+      }
+    }
     __syncthreads();
-    before = all = 0;
-    if (t < tx)
-      for (int kk = 0; kk < g; ++kk) {
-        before += s_bp[kk * tx + t];
-        all += s_tp[kk * tx + t];
+    uint32_t tot;
+    {
+      uint32_t* seg = s_tab + t * L;
+      uint32_t sum = 0;
+      for (int k = 0; k < L; ++k) sum += seg[k];
+      uint32_t pre = block_inclusive_scan<uint32_t, kSpanThreads>(sum, &tot) - sum;
+      for (int k = 0; k < L; ++k) {
+        const uint32_t v = seg[k];
+        seg[k] = pre;
+        pre += v;
       }
-    uint32_t row_all;
-    const uint32_t start = pos.row_base + block_inclusive_scan<uint32_t, kSpanThreads>(all, &row_all) - all;
-    if (t < tx) {
-      s_goff[t] = start + before;
-      if (pos.index == 0) A.ranges[tile0 + t] = make_uint2(start, start + all);
     }
-  }
-  int x0[kSpanPer], len[kSpanPer];
-  uint32_t gid[kSpanPer];
-  uint32_t carry = 0;  // my spans covering column L - 1 (the low half's last column)
-#pragma unroll
-  for (int i = 0; i < kSpanPer; ++i) {
-    const int64_t s = pos.s0 + (int64_t)t * per + i;
-    const bool in = i < per && s < pos.s1;
-    const uint32_t k = in ? A.keys[s] : 0u;
-    gid[i] = in ? A.vals[s] : 0u;
-    x0[i] = span_x0(k);
-    len[i] = in ? span_len(k) : 0;
-    carry += (len[i] > 0 && x0[i] <= L - 1 && x0[i] + len[i] > L - 1) ? 1u : 0u;
-  }
-  // my column of the table: +1 where a span starts, -1 after it ends, then summed along the column
-  for (int k = 0; k < L; ++k) s_tab[k * kSpanThreads + t] = 0u;
-#pragma unroll
-  for (int i = 0; i < kSpanPer; ++i) {
-    if (len[i] == 0) continue;
-    const int c0 = x0[i], c1 = x0[i] + len[i];
-    const int h0 = c0 >= L;
-    s_tab[(c0 - h0 * L) * kSpanThreads + t] += 1u << (16 * h0);
-    if (c1 < 2 * L) {  // (columns tx .. 2L - 1 do not exist: they must count nothing)
-      const int h1 = c1 >= L;
-      s_tab[(c1 - h1 * L) * kSpanThreads + t] -= 1u << (16 * h1);
-    }
-  }
-  {
-    uint32_t run = carry << 16;  // the high half continues from column L - 1
-    for (int k = 0; k < L; ++k) {
-      run += s_tab[k * kSpanThreads + t];
-      s_tab[k * kSpanThreads + t] = run;
-    }
-  }
-  __syncthreads();
-  uint32_t tot;
-  {
-    uint32_t* seg = s_tab + t * L;
-    uint32_t sum = 0;
-    for (int k = 0; k < L; ++k) sum += seg[k];
-    uint32_t pre = block_inclusive_scan<uint32_t, kSpanThreads>(sum, &tot) - sum;
-    for (int k = 0; k < L; ++k) {
-      const uint32_t v = seg[k];
-      seg[k] = pre;
-      pre += v;
-    }
-  }
-  __syncthreads();
-  const uint32_t low = tot & 0xffffu, total = low + (tot >> 16);
-  for (int c = t; c <= tx; c += kSpanThreads) {
-    if (c == tx) {
-      s_cpos[c] = total;
-    } else {
-      const int h = c >= L;
-      s_cpos[c] = ((s_tab[(c - h * L) * kSpanThreads] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
-    }
-  }
-  __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
-  uint32_t* __restrict__ out = A.point_list;
-  uint32_t* __restrict__ out_keys = A.tile_keys;
-  for (uint32_t w0 = 0; w0 < total; w0 += kSpanWindow) {  // uniform
-#pragma unroll
-    for (int i = 0; i < kSpanPer; ++i)
-      for (int c = x0[i]; c < x0[i] + len[i]; ++c) {
+    __syncthreads();
+    const uint32_t low = tot & 0xffffu, total = low + (tot >> 16);
+    for (int c = t; c <= tx; c += kSpanThreads) {
+      if (c == tx) {
+        s_cpos[c] = total;
+      } else {
         const int h = c >= L;
-        uint32_t q = ((s_tab[(c - h * L) * kSpanThreads + t] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
-#pragma unroll
-        for (int j = 0; j < i; ++j) q += (c >= x0[j] && c < x0[j] + len[j]) ? 1u : 0u;
-        if (q >= w0 && q < w0 + kSpanWindow) s_stage[q - w0] = gid[i];
+        s_cpos[c] = ((s_tab[(c - h * L) * kSpanThreads] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
       }
+    }
     __syncthreads();
-    const uint32_t wend = min(total, w0 + (uint32_t)kSpanWindow);
-    for (int c = warp; c < tx; c += kSpanThreads / 32) {  // a warp per column run
-      const uint32_t q0 = max(s_cpos[c], w0), q1 = min(s_cpos[c + 1], wend);
-      const uint32_t g0 = s_goff[c] + (q0 - s_cpos[c]);
-      for (uint32_t q = q0 + lane; q < q1; q += 32) {
-        out[g0 + (q - q0)] = s_stage[q - w0];
-        if (out_keys != nullptr) out_keys[g0 + (q - q0)] = tile0 + (uint32_t)c;
+    const int warp = t >> 5, lane = t & 31;
+    uint32_t* __restrict__ out = A.point_list;
+    uint32_t* __restrict__ out_keys = A.tile_keys;
+    for (uint32_t w0 = 0; w0 < total; w0 += kSpanWindow) {  // uniform
+#pragma unroll
+      for (int i = 0; i < kSpanPer; ++i)
+        for (int c = x0[i]; c < x0[i] + len[i]; ++c) {
+          const int h = c >= L;
+          uint32_t q = ((s_tab[(c - h * L) * kSpanThreads + t] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
+#pragma unroll
+          for (int j = 0; j < i; ++j) q += (c >= x0[j] && c < x0[j] + len[j]) ? 1u : 0u;
+          if (q >= w0 && q < w0 + kSpanWindow) s_stage[q - w0] = gid[i];
+        }
+      __syncthreads();
+      const uint32_t wend = min(total, w0 + (uint32_t)kSpanWindow);
+      for (int c = warp; c < tx; c += kSpanThreads / 32) {  // a warp per column run
+        const uint32_t q0 = max(s_cpos[c], w0), q1 = min(s_cpos[c + 1], wend);
+        const uint32_t g0 = s_goff[c] + (q0 - s_cpos[c]);
+        for (uint32_t q = q0 + lane; q < q1; q += 32) {
+          out[g0 + (q - q0)] = s_stage[q - w0];
+          if (out_keys != nullptr) out_keys[g0 + (q - q0)] = tile0 + (uint32_t)c;
+        }
       }
+      __syncthreads();
     }
     __syncthreads();
   }
@@ -1518,7 +1524,7 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
     p.off_spartials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
     const int64_t chunks = (capacity + span_chunk(tx) - 1) / span_chunk(tx) + ty;  // at most
     p.off_ctab = off; off += align256(sizeof(uint32_t) * (size_t)chunks * tx);
-    p.off_rowtot = off; off += align256(sizeof(uint32_t) * (size_t)ty);
+    p.off_rowtot = off; off += align256(sizeof(uint32_t) * (size_t)ty * (1 + tx));
   }
   p.total = off;
   return p;
@@ -1588,7 +1594,7 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     c.ptr[0] = (w.n == 0 || plan.spans) ? R.out.ranges : nullptr; c.words[0] = 2 * (size_t)plan.num_tiles;
     c.ptr[1] = w.err; c.words[1] = 1;
     c.ptr[2] = w.n == 0 ? reinterpret_cast<uint32_t*>(R.out.num_instances) : (plan.spans ? w.rowtot : nullptr);
-    c.words[2] = w.n == 0 ? 2 : (size_t)w.tiles_y;
+    c.words[2] = w.n == 0 ? 2 : (size_t)w.tiles_y * (1 + w.tiles_x);
     c.ptr[3] = w.n > 0 ? w.sort_d : nullptr; c.words[3] = sort_scratch_bytes(w.n, 32) / 4;
     c.ptr[4] = w.n > 0 ? w.sort_t : nullptr;
     c.words[4] = sort_scratch_bytes(plan.capacity, plan.spans ? plan.row_bits : plan.tile_bits) / 4;
@@ -1689,7 +1695,9 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
       SpanArgs a{w.skeys[tcur[i]], w.svals[tcur[i]], w.sort_t, w.span_n, w.err, R.out.num_instances, w.ctab,
                  w.rowtot, reinterpret_cast<uint2*>(R.out.ranges), R.out.point_list, R.out.tile_keys,
                  w.tiles_x, w.tiles_y, (unsigned)chunks};
+      a.grid = (unsigned)std::min<int64_t>(chunks, 8 * (int64_t)device_sm_count());
       scnt.add(a);
+      a.grid = (unsigned)std::min<int64_t>(chunks, 3 * (int64_t)device_sm_count());
       sexp.add(a);
       sexp_smem = std::max(sexp_smem, span_expand_smem(w.tiles_x));
     } else {
