@@ -1042,7 +1042,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(const Batch<Wal
 constexpr int kSpanMaxTiles = 256;   // tiles per side: row and x0 fit 8 bits, len - 1 16 bits
 constexpr int kSpanThreads = 256;
 constexpr int kSpanPer = 4;          // spans per thread per expansion chunk, at most
-constexpr int kSpanWindow = 8192;    // instances staged per round of a chunk's output
+constexpr int kSpanWindow = 8192;    // instances a chunk stages in shared memory
 
 __device__ __forceinline__ uint32_t span_key(int row, int x0, int len) {
   return (uint32_t)row | ((uint32_t)x0 << 8) | ((uint32_t)(len - 1) << 16);
@@ -1239,8 +1239,9 @@ __global__ void __launch_bounds__(kSpanThreads) span_count_kernel(const Batch<Sp
 // difference array summed along the column).  An exclusive scan of the table in (column, thread)
 // order then gives each (column, thread) its first position among the chunk's instances ordered by
 // (column, depth); a span's instance at column c goes there plus the thread's earlier spans
-// covering c.  The instances are staged in shared memory (kSpanWindow at a time) and each
-// column's run is written contiguously at its place in the tile's list: after the instances of the
+// covering c.  The instances are staged in shared memory and each column's run is written
+// contiguously at its place in the tile's list (a chunk with more than kSpanWindow instances
+// writes them in place directly): after the instances of the
 // rows before, of the row's tiles to the left, and of the row's earlier chunks at that column (all
 // from the chunks' column counts).  The row's first chunk also writes the row's tile ranges.
 __global__ void __launch_bounds__(kSpanThreads) span_expand_kernel(const Batch<SpanArgs> b) {
@@ -1345,27 +1346,41 @@ __global__ void __launch_bounds__(kSpanThreads) span_expand_kernel(const Batch<S
     const int warp = t >> 5, lane = t & 31;
     uint32_t* __restrict__ out = A.point_list;
     uint32_t* __restrict__ out_keys = A.tile_keys;
-    for (uint32_t w0 = 0; w0 < total; w0 += kSpanWindow) {  // uniform
+    if (total <= (uint32_t)kSpanWindow) {  // uniform
+      // Staged: each instance takes its (column, thread) entry, which then counts up for my next
+      // span covering that column; then every column's run is copied out contiguously.
 #pragma unroll
       for (int i = 0; i < kSpanPer; ++i)
         for (int c = x0[i]; c < x0[i] + len[i]; ++c) {
           const int h = c >= L;
-          uint32_t q = ((s_tab[(c - h * L) * kSpanThreads + t] >> (16 * h)) & 0xffffu) + (h ? low : 0u);
-#pragma unroll
-          for (int j = 0; j < i; ++j) q += (c >= x0[j] && c < x0[j] + len[j]) ? 1u : 0u;
-          if (q >= w0 && q < w0 + kSpanWindow) s_stage[q - w0] = gid[i];
+          uint32_t* e = s_tab + (c - h * L) * kSpanThreads + t;
+          const uint32_t w = *e;
+          s_stage[((w >> (16 * h)) & 0xffffu) + (h ? low : 0u)] = gid[i];
+          *e = w + (1u << (16 * h));
         }
       __syncthreads();
-      const uint32_t wend = min(total, w0 + (uint32_t)kSpanWindow);
       for (int c = warp; c < tx; c += kSpanThreads / 32) {  // a warp per column run
-        const uint32_t q0 = max(s_cpos[c], w0), q1 = min(s_cpos[c + 1], wend);
-        const uint32_t g0 = s_goff[c] + (q0 - s_cpos[c]);
+        const uint32_t q0 = s_cpos[c], q1 = s_cpos[c + 1];
+        const uint32_t g0 = s_goff[c];
         for (uint32_t q = q0 + lane; q < q1; q += 32) {
-          out[g0 + (q - q0)] = s_stage[q - w0];
+          out[g0 + (q - q0)] = s_stage[q];
           if (out_keys != nullptr) out_keys[g0 + (q - q0)] = tile0 + (uint32_t)c;
         }
       }
-      __syncthreads();
+    } else {
+      // A chunk of long spans, more instances than the stage holds: written in place directly.
+#pragma unroll
+      for (int i = 0; i < kSpanPer; ++i)
+        for (int c = x0[i]; c < x0[i] + len[i]; ++c) {
+          const int h = c >= L;
+          uint32_t* e = s_tab + (c - h * L) * kSpanThreads + t;
+          const uint32_t w = *e;
+          const uint32_t q = ((w >> (16 * h)) & 0xffffu) + (h ? low : 0u);
+          *e = w + (1u << (16 * h));
+          const uint32_t g = s_goff[c] + (q - s_cpos[c]);
+          out[g] = gid[i];
+          if (out_keys != nullptr) out_keys[g] = tile0 + (uint32_t)c;
+        }
     }
     __syncthreads();
   }

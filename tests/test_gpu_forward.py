@@ -85,6 +85,23 @@ def test_bin_sort_bit_exact_on_random_records(n, W, H, seed):
     U.assert_ranges_equal(ranges, binning.tile_ranges(okeys, tiles))
 
 
+def test_bin_sort_bit_exact_with_long_spans():
+    """Gaussians up to 81 tiles wide: chunks of the span expansion with more instances than its
+    shared-memory stage, which write their lists in place."""
+    W, H = 1024, 256
+    rec = synth.random_projected(6000, W, H, seed=15, max_half_tiles=40, empty_frac=0.0)
+    rec["conic"][:] = np.array([1e-4, 0.0, 1e-4], np.float32)  # wide, reaching every tile of the rectangle
+    proj = U.sdgs.ProjectedBuffers.from_host(rec)
+    view = U.sdgs.view_struct(synth.make_camera((0, 0, -3), W, H, 60.0, 0.5))
+    okeys, ovals = binning.sort_keys(rec["depth"], rec["rect"], W // 16,
+                                     cull=(rec["mean2d"], rec["conic"], rec["opacity"]))
+    k, keys, vals, ranges, _ = U.gpu_bin(proj, view, capacity=len(okeys) + 7)
+    assert k == len(okeys)
+    np.testing.assert_array_equal(keys.astype(np.uint64), okeys >> np.uint64(32))
+    np.testing.assert_array_equal(vals, ovals)
+    U.assert_ranges_equal(ranges, binning.tile_ranges(okeys, (W // 16) * (H // 16)))
+
+
 def test_bin_sort_overflow_is_reported_and_safe():
     rec = synth.random_projected(2000, 256, 256, seed=7)
     proj = U.sdgs.ProjectedBuffers.from_host(rec)
