@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(kSpanThreads) span_expand_kernel(const Batch<S
       const uint32_t start = pos.row_base + block_inclusive_scan<uint32_t, kSpanThreads>(all, &row_all) - all;
       if (t < tx) {
         s_goff[t] = start + before;
-        if (pos.index == 0) A.ranges[tile0 + t] = make_uint2(start, start + all);
+        if (pos.index == 0) A.ranges[tile0 + t] = all > 0 ? make_uint2(start, start + all) : make_uint2(0u, 0u);
       }
     }
     int x0[kSpanPer], len[kSpanPer];
