@@ -676,8 +676,9 @@ cudaError_t radix_sort(const SortJob* jobs, int count, bool hist_ready, cudaStre
 // ranges and the instance count (when there are no Gaussians) and both sorts' scratch.  One kernel
 // instead of several memsets keeps the render's launches a chain of kernels.
 struct ClearJob {
-  uint32_t* ptr[5];
-  size_t words[5];
+  static constexpr int kSlots = 7;
+  uint32_t* ptr[kSlots];
+  size_t words[kSlots];
   unsigned grid;
 };
 
@@ -686,7 +687,7 @@ __global__ void __launch_bounds__(256) clear_kernel(const Batch<ClearJob> b) {
   if (blockIdx.x >= job.grid) return;
   griddep_wait();
   const size_t stride = (size_t)job.grid * blockDim.x;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < ClearJob::kSlots; ++k) {
     uint32_t* p = job.ptr[k];
     if (p == nullptr) continue;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < job.words[k]; i += stride) p[i] = 0u;
@@ -702,6 +703,7 @@ struct DepthKeysArgs {
   uint32_t* keys;
   uint32_t* vals;
   uint32_t* hist;
+  uint32_t* visible;  // visible Gaussians are added up here, or NULL
   unsigned grid;
 };
 
@@ -716,8 +718,11 @@ __global__ void __launch_bounds__(kRadixThreads) depth_keys_kernel(const Batch<D
   uint32_t* __restrict__ hist = a.hist;
   griddep_wait();
   __shared__ uint32_t s_hist[kMaxPasses][kBins];
+  __shared__ uint32_t s_vis;
   for (int i = threadIdx.x; i < kMaxPasses * kBins; i += kRadixThreads) (&s_hist[0][0])[i] = 0;
+  if (threadIdx.x == 0) s_vis = 0;
   __syncthreads();
+  uint32_t nvis = 0;
   constexpr int U = 4;  // elements per thread per round, their loads issued together
   const int64_t stride = (int64_t)a.grid * kRadixThreads * U;
   for (int64_t i0 = (int64_t)blockIdx.x * kRadixThreads * U; i0 < n; i0 += stride) {  // uniform over the block
@@ -736,14 +741,21 @@ __global__ void __launch_bounds__(kRadixThreads) depth_keys_kernel(const Batch<D
       if (i < n) {
         const bool vis = r[u].z > r[u].x && r[u].w > r[u].y;
         k = vis ? __float_as_uint(z[u]) : 0xffffffffu;  // visible depths are positive
+        nvis += vis ? 1u : 0u;
         keys[i] = k;
         vals[i] = (uint32_t)i;
       }
       count_digits(s_hist, k, i < n, 4, 8);
     }
   }
+  if (a.visible != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nvis += __shfl_xor_sync(0xffffffffu, nvis, o);
+    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&s_vis, nvis);
+  }
   __syncthreads();
   flush_digits(s_hist, 4, hist);
+  if (a.visible != nullptr && threadIdx.x == 0 && s_vis) atomicAdd(a.visible, s_vis);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -847,9 +859,6 @@ struct WalkArgs {
   uint32_t* vals;
   int passes, width;      // tile-digit passes whose histograms the emit accumulates into hist
   uint32_t* hist;
-  uint32_t* scount;       // span binning: count walk writes the kept row spans per warp chunk
-  const uint64_t* sfirst; // span emit: first span of each warp chunk
-  int64_t* span_n;        // span emit: spans kept (lowered from the total when cap cuts them)
   unsigned grid;
 };
 
@@ -870,35 +879,23 @@ __global__ void __launch_bounds__(kWalkThreads) walk_count_kernel(const Batch<Wa
   const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
   if (wg * 32 >= n) return;  // whole warps
   if (*err != 0u) {  // the depth sort gave up: `order` may hold any value, so emit nothing
-    if (lane == 0) {
-      wcount[wg] = 0;
-      if (A.scount != nullptr) A.scount[wg] = 0;
-    }
+    if (lane == 0) wcount[wg] = 0;
     return;
   }
   WalkWarp& w = s_walk[warp];
   const int nr = walk_setup(w, order, rect, mean2d, conic_opacity, wg * 32 + lane, n, tiles_x, tiles_y);
   const uint32_t row_incl = warp_inclusive_scan((uint32_t)nr);
   const uint32_t rows = __shfl_sync(0xffffffffu, row_incl, 31);
-  uint32_t sum = 0, spans = 0;
+  uint32_t sum = 0;
   for (uint32_t rb = 0; rb < rows; rb += 32) {
     const uint32_t k = rb + lane;
     int o, ty, x0, x1;
     walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
-    if (k < rows) {
-      sum += (uint32_t)(x1 - x0);
-      spans += x1 > x0 ? 1u : 0u;
-    }
+    if (k < rows) sum += (uint32_t)(x1 - x0);
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, off);
-    spans += __shfl_xor_sync(0xffffffffu, spans, off);
-  }
-  if (lane == 0) {
-    wcount[wg] = sum;
-    if (A.scount != nullptr) A.scount[wg] = spans;
-  }
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) wcount[wg] = sum;
 }
 
 // Digit histograms of the tile ids of a row span id0 .. id0 + len - 1 for the tile sort.  Pass 0
@@ -1050,71 +1047,209 @@ __device__ __forceinline__ uint32_t span_key(int row, int x0, int len) {
 __device__ __forceinline__ int span_x0(uint32_t k) { return (int)((k >> 8) & 0xffu); }
 __device__ __forceinline__ int span_len(uint32_t k) { return (int)(k >> 16) + 1; }
 
-// Writes the row spans of each warp's 32 depth-ordered Gaussians from the warp's first span
-// sfirst[warp]: a span whose first instance lies at depth-order position >= cap is dropped (and
-// *span_n lowered to its index, so that the spans kept are a prefix), one that crosses cap is cut
-// there.  Accumulates the row histogram for the row sort.  Lanes take one row each (as in
-// walk_count_kernel), so consecutive lanes write consecutive spans.
-__global__ void __launch_bounds__(kWalkThreads) span_emit_kernel(const Batch<WalkArgs> b) {
-  const WalkArgs& A = b.a[blockIdx.y];
+// Single-pass span emit: the count walk, the scan of its totals and the emit in one kernel.  Each
+// block (8 warps, 256 depth-ordered Gaussians, numbered by a ticket taken when it starts) walks its
+// warps' rows once, keeping up to kWalkKeep spans per warp in shared memory, and publishes its
+// span and instance totals at once; a decoupled look-back over the earlier blocks' totals (32 per
+// round, one per lane) gives its first span and first instance, and it then writes its spans,
+// cutting them at cap (a span whose first instance lies at depth-order position >= cap is dropped,
+// one that crosses cap is cut there).  A warp with more spans than it kept walks its
+// rows again while writing.  The last block to finish sets the kept span count.  Every wait is
+// bounded: a block that gives up sets pass_bit in *err (the row sort then skips and the lists
+// stay empty).
+constexpr int kWalkKeep = 160;                          // spans per warp kept between walk and write
+constexpr uint64_t kWalkAggregate = 1ull << 62;         // the block's own totals
+constexpr uint64_t kWalkInclusive = 2ull << 62;         // totals of blocks 0 .. this one
+constexpr uint64_t kWalkField = (1ull << 31) - 1;       // 31-bit fields: instances << 31 | spans
+
+__device__ __forceinline__ uint64_t walk_pack(uint64_t spans, uint64_t inst) {
+  return (min(inst, kWalkField) << 31) | min(spans, kWalkField);
+}
+
+struct SpanWalkArgs {
+  const uint32_t* order;  // depth-ordered Gaussian ids
+  const ushort4* rect;
+  const float2* mean2d;
+  const float4* conic_opacity;
+  int64_t n;
+  int tiles_x, tiles_y;
+  uint32_t* err;
+  uint32_t pass_bit;
+  int spin_limit;
+  int64_t cap;
+  uint32_t* keys;             // spans out (depth order)
+  uint32_t* vals;
+  uint32_t* hist;             // row histogram (the row sort's digit histogram)
+  int64_t* num_instances;     // K (zeroed before binning)
+  uint32_t* counters;         // [0] ticket, [1] blocks done, [2..3] ~(first dropped span), [4] visible
+                              // Gaussians (from the depth keys), [6..7] spans kept (int64); zeroed first
+  uint64_t* status;           // [grid] (zeroed)
+  unsigned grid;
+};
+
+__global__ void __launch_bounds__(kWalkThreads) span_walk_kernel(const Batch<SpanWalkArgs> b) {
+  const SpanWalkArgs& A = b.a[blockIdx.y];
   if (blockIdx.x >= A.grid) return;
-  const uint32_t* __restrict__ order = A.order;
-  const ushort4* __restrict__ rect = A.rect;
-  const float2* __restrict__ mean2d = A.mean2d;
-  const float4* __restrict__ conic_opacity = A.conic_opacity;
-  const int64_t n = A.n;
-  const int tiles_x = A.tiles_x, tiles_y = A.tiles_y;
-  const uint64_t* __restrict__ wfirst = A.wfirst;
-  const uint64_t* __restrict__ sfirst = A.sfirst;
-  const int64_t cap = A.cap;
-  uint32_t* __restrict__ keys = A.keys;
-  uint32_t* __restrict__ vals = A.vals;
-  const uint32_t* err = A.err;
   griddep_wait();
   __shared__ WalkWarp s_walk[kWalkWarps];
+  __shared__ uint32_t s_key[kWalkWarps][kWalkKeep];
+  __shared__ uint32_t s_gid[kWalkWarps][kWalkKeep];
+  __shared__ uint32_t s_ioff[kWalkWarps][kWalkKeep];
   __shared__ uint32_t s_rows[kSpanMaxTiles];
-  for (int i = threadIdx.x; i < kSpanMaxTiles; i += kWalkThreads) s_rows[i] = 0;
-  __syncthreads();
+  __shared__ uint32_t s_wsp[kWalkWarps], s_win[kWalkWarps];
+  __shared__ uint64_t s_before_sp, s_before_in;
+  __shared__ uint32_t s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  const int64_t wg = (int64_t)blockIdx.x * kWalkWarps + warp;
-  if (wg * 32 < n && *err == 0u) {  // uniform over the warp
-    uint64_t pos = wfirst[wg], spos = sfirst[wg];
-    if (pos >= (uint64_t)cap) {
-      if (lane == 0) atomicMin(reinterpret_cast<unsigned long long*>(A.span_n), (unsigned long long)spos);
-    } else {
-      WalkWarp& w = s_walk[warp];
-      const int nr = walk_setup(w, order, rect, mean2d, conic_opacity, wg * 32 + lane, n, tiles_x, tiles_y);
-      const uint32_t row_incl = warp_inclusive_scan((uint32_t)nr);
-      const uint32_t rows = __shfl_sync(0xffffffffu, row_incl, 31);
-      for (uint32_t rb = 0; rb < rows && pos < (uint64_t)cap; rb += 32) {  // uniform
+  if (threadIdx.x == 0) s_tile = atomicAdd(&A.counters[0], 1u);
+  for (int i = threadIdx.x; i < kSpanMaxTiles; i += kWalkThreads) s_rows[i] = 0;
+  __syncthreads();
+  const int64_t tile = s_tile;
+  // Culled Gaussians come last in depth order: the blocks past the visible ones have nothing to
+  // write and nobody waits on them.
+  const int64_t blocks = ((int64_t)A.counters[4] + kWalkThreads - 1) / kWalkThreads;
+  if (tile >= blocks) return;
+  const bool live = *reinterpret_cast<volatile uint32_t*>(A.err) == 0u;  // the depth sort completed
+  // 1. walk: count this warp's spans and instances, keeping the first kWalkKeep spans
+  const int64_t wg = tile * kWalkWarps + warp;
+  WalkWarp& w = s_walk[warp];
+  int nr = 0;
+  uint32_t row_incl = 0, rows = 0, nsp = 0, ninst = 0;
+  if (live && wg * 32 < A.n) {  // uniform over the warp
+    nr = walk_setup(w, A.order, A.rect, A.mean2d, A.conic_opacity, wg * 32 + lane, A.n, A.tiles_x, A.tiles_y);
+    row_incl = warp_inclusive_scan((uint32_t)nr);
+    rows = __shfl_sync(0xffffffffu, row_incl, 31);
+    for (uint32_t rb = 0; rb < rows; rb += 32) {
+      const uint32_t k = rb + lane;
+      int o, ty, x0, x1;
+      walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
+      const uint32_t len = k < rows ? (uint32_t)(x1 - x0) : 0u;
+      const uint32_t incl = warp_inclusive_scan(len);
+      const unsigned has = __ballot_sync(0xffffffffu, len > 0u);
+      if (len > 0u) {
+        const uint32_t j = nsp + (uint32_t)__popc(has & lt);
+        if (j < (uint32_t)kWalkKeep) {
+          s_key[warp][j] = span_key(ty, x0, (int)len);
+          s_gid[warp][j] = w.g[o];
+          s_ioff[warp][j] = ninst + (incl - len);
+        }
+      }
+      nsp += (uint32_t)__popc(has);
+      ninst += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (lane == 0) {
+    s_wsp[warp] = nsp;
+    s_win[warp] = ninst;
+  }
+  __syncthreads();
+  // 2. block totals (warp prefixes), published at once; then the look-back for the prefix
+  if (warp == 0) {
+    const uint32_t sp = lane < kWalkWarps ? s_wsp[lane] : 0u;
+    const uint32_t in = lane < kWalkWarps ? s_win[lane] : 0u;
+    const uint32_t sp_incl = warp_inclusive_scan(sp), in_incl = warp_inclusive_scan(in);
+    if (lane < kWalkWarps) {
+      s_wsp[lane] = sp_incl - sp;
+      s_win[lane] = in_incl - in;
+    }
+    const uint64_t tot_sp = __shfl_sync(0xffffffffu, sp_incl, 31), tot_in = __shfl_sync(0xffffffffu, in_incl, 31);
+    volatile uint64_t* st = reinterpret_cast<volatile uint64_t*>(A.status);
+    if (lane == 0) {
+      st[tile] = (tile == 0 ? kWalkInclusive : kWalkAggregate) | walk_pack(tot_sp, tot_in);
+      if (tot_in) atomicAdd(reinterpret_cast<unsigned long long*>(A.num_instances), (unsigned long long)tot_in);
+    }
+    uint64_t bsp = 0, bin = 0;
+    int64_t j = tile - 1;
+    int spins = 0;
+    while (j >= 0) {  // uniform over the warp
+      const int64_t idx = j - lane;
+      const uint64_t v = idx >= 0 ? (uint64_t)st[idx] : (uint64_t)kWalkInclusive;  // before block 0: an inclusive zero
+      const uint64_t flags = v & ~((1ull << 62) - 1);
+      const unsigned incl_mask = __ballot_sync(0xffffffffu, flags == kWalkInclusive);
+      const unsigned unready = __ballot_sync(0xffffffffu, flags == 0);
+      const int first = incl_mask ? __ffs(incl_mask) - 1 : 32;  // nearest inclusive entry
+      const unsigned need = first < 31 ? (2u << first) - 1u : 0xffffffffu;
+      if (unready & need) {
+        if (++spins > A.spin_limit) {
+          if (lane == 0) atomicOr(A.err, A.pass_bit);
+          break;
+        }
+        __nanosleep(64);
+        continue;
+      }
+      uint64_t csp = ((need >> lane) & 1u) ? (v & kWalkField) : 0u;
+      uint64_t cin = ((need >> lane) & 1u) ? ((v >> 31) & kWalkField) : 0u;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        csp += __shfl_xor_sync(0xffffffffu, csp, off);
+        cin += __shfl_xor_sync(0xffffffffu, cin, off);
+      }
+      bsp += csp;
+      bin += cin;
+      if (first < 32) break;
+      j -= 32;
+    }
+    if (lane == 0) {
+      if (tile > 0) st[tile] = kWalkInclusive | walk_pack(bsp + tot_sp, bin + tot_in);
+      s_before_sp = bsp;
+      s_before_in = bin;
+    }
+  }
+  __syncthreads();
+  // 3. write the spans (cut at cap), with the row histogram
+  if (live && wg * 32 < A.n) {  // uniform over the warp
+    const uint64_t sbase = s_before_sp + s_wsp[warp], ibase = s_before_in + s_win[warp];
+    const int64_t cap = A.cap;
+    auto put = [&](uint64_t sidx, uint64_t ipos, int ty, int x0, int len, uint32_t gid) {
+      if (ipos < (uint64_t)cap) {
+        const int keep = (int)min((uint64_t)len, (uint64_t)cap - ipos);
+        if (sidx < (uint64_t)cap) {  // (always, unless a look-back gave up)
+          A.keys[sidx] = span_key(ty, x0, keep);
+          A.vals[sidx] = gid;
+          atomicAdd(&s_rows[ty], 1u);
+        }
+      } else {
+        atomicMax(reinterpret_cast<unsigned long long*>(A.counters + 2), ~(unsigned long long)sidx);
+      }
+    };
+    if (nsp <= (uint32_t)kWalkKeep) {
+      for (uint32_t j = lane; j < nsp; j += 32) {
+        const uint32_t k = s_key[warp][j];
+        put(sbase + j, ibase + s_ioff[warp][j], (int)(k & 0xffu), span_x0(k), span_len(k), s_gid[warp][j]);
+      }
+    } else {  // walk again, writing as it goes
+      uint64_t pos = ibase, spos = sbase;
+      for (uint32_t rb = 0; rb < rows; rb += 32) {
         const uint32_t k = rb + lane;
         int o, ty, x0, x1;
         walk_row(w, row_incl, nr, k < rows ? k : rows - 1, &o, &ty, &x0, &x1);
         const uint32_t len = k < rows ? (uint32_t)(x1 - x0) : 0u;
         const uint32_t incl = warp_inclusive_scan(len);
         const unsigned has = __ballot_sync(0xffffffffu, len > 0u);
-        if (len > 0u) {
-          const uint64_t ipos = pos + (incl - len);  // depth-order position of the span's first instance
-          const uint64_t sidx = spos + (uint64_t)__popc(has & lt);
-          if (ipos < (uint64_t)cap) {
-            const int keep = (int)min((uint64_t)len, (uint64_t)cap - ipos);
-            keys[sidx] = span_key(ty, x0, keep);
-            vals[sidx] = w.g[o];
-            atomicAdd(&s_rows[ty], 1u);
-          } else {
-            atomicMin(reinterpret_cast<unsigned long long*>(A.span_n), (unsigned long long)sidx);
-          }
-        }
+        if (len > 0u) put(spos + (uint64_t)__popc(has & lt), pos + (incl - len), ty, x0, (int)len, w.g[o]);
         pos += __shfl_sync(0xffffffffu, incl, 31);
         spos += (uint64_t)__popc(has);
       }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < tiles_y; i += kWalkThreads) {
+  for (int i = threadIdx.x; i < A.tiles_y; i += kWalkThreads) {
     const uint32_t c = s_rows[i];
     if (c) atomicAdd(&A.hist[i], c);
+  }
+  // 4. the last block to finish sets the kept span count: all spans, or up to the first dropped
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&A.counters[1], 1u) == (uint32_t)(blocks - 1);
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const uint64_t last = *reinterpret_cast<volatile uint64_t*>(A.status + (blocks - 1));
+    uint64_t total = last & kWalkField;
+    const unsigned long long d = *reinterpret_cast<volatile unsigned long long*>(A.counters + 2);
+    if (d != 0ull) total = min(total, (uint64_t)~d);
+    *reinterpret_cast<int64_t*>(A.counters + 6) = (int64_t)total;
   }
 }
 
@@ -1506,6 +1641,9 @@ cudaError_t allow_span_expand_smem() {
   return cudaSuccess;
 }
 
+// Words of the single-pass span walk's state: 64 counter words, then a 64-bit status per block.
+size_t span_walk_words(int64_t n) { return 64 + 2 * (size_t)((n + kWalkThreads - 1) / kWalkThreads); }
+
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   BinPlan p;
   p.n = n;
@@ -1519,7 +1657,6 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   p.row_bits = 0;
   while ((1 << p.row_bits) < ty) ++p.row_bits;
   p.partial_cap = (n + kScanChunk - 1) / kScanChunk + 1;
-  const int64_t nwarps = (n + 31) / 32;
   size_t off = 0;
   for (int k = 0; k < 2; ++k) { p.off_dkeys[k] = off; off += align256(sizeof(uint32_t) * n); }
   for (int k = 0; k < 2; ++k) { p.off_dvals[k] = off; off += align256(sizeof(uint32_t) * n); }
@@ -1531,12 +1668,10 @@ BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height) {
   p.off_sort_d = off; off += align256(sort_scratch_bytes(n, 32));
   p.off_sort_t = off; off += align256(sort_scratch_bytes(capacity, p.spans ? p.row_bits : bits));
   p.off_partials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
-  p.off_svals = p.off_sfirst = p.off_span_n = p.off_spartials = p.off_ctab = p.off_rowtot = 0;
+  p.off_svals = p.off_walk = p.off_ctab = p.off_rowtot = 0;
   if (p.spans) {
     p.off_svals = off; off += align256(sizeof(uint32_t) * capacity);
-    p.off_sfirst = off; off += align256(sizeof(uint64_t) * nwarps);
-    p.off_span_n = off; off += 256;
-    p.off_spartials = off; off += align256(sizeof(uint64_t) * p.partial_cap);
+    p.off_walk = off; off += align256(sizeof(uint32_t) * span_walk_words(n));
     const int64_t chunks = (capacity + span_chunk(tx) - 1) / span_chunk(tx) + ty;  // at most
     p.off_ctab = off; off += align256(sizeof(uint32_t) * (size_t)chunks * tx);
     p.off_rowtot = off; off += align256(sizeof(uint32_t) * (size_t)ty * (1 + tx));
@@ -1553,8 +1688,7 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     int tiles_x, tiles_y;
     uint32_t *dkeys[2], *dvals[2], *sort_d, *sort_t, *err, *out_keys, *ikeys[2], *ivals[2];
     uint64_t *first, *partials;
-    uint32_t *skeys[2], *svals[2], *ctab, *rowtot;  // span binning
-    uint64_t *sfirst, *spartials;
+    uint32_t *skeys[2], *svals[2], *ctab, *rowtot, *walk;  // span binning
     int64_t* span_n;
     const ushort4* rect;
     const float2* m2;
@@ -1598,9 +1732,8 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
       w.skeys[1] = reinterpret_cast<uint32_t*>(ws + plan.off_ikeys[1]);
       w.svals[0] = wv0;
       w.svals[1] = reinterpret_cast<uint32_t*>(ws + plan.off_svals);
-      w.sfirst = reinterpret_cast<uint64_t*>(ws + plan.off_sfirst);
-      w.span_n = reinterpret_cast<int64_t*>(ws + plan.off_span_n);
-      w.spartials = reinterpret_cast<uint64_t*>(ws + plan.off_spartials);
+      w.walk = reinterpret_cast<uint32_t*>(ws + plan.off_walk);
+      w.span_n = reinterpret_cast<int64_t*>(w.walk + 6);
       w.ctab = reinterpret_cast<uint32_t*>(ws + plan.off_ctab);
       w.rowtot = reinterpret_cast<uint32_t*>(ws + plan.off_rowtot);
     }
@@ -1613,8 +1746,11 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     c.ptr[3] = w.n > 0 ? w.sort_d : nullptr; c.words[3] = sort_scratch_bytes(w.n, 32) / 4;
     c.ptr[4] = w.n > 0 ? w.sort_t : nullptr;
     c.words[4] = sort_scratch_bytes(plan.capacity, plan.spans ? plan.row_bits : plan.tile_bits) / 4;
+    // span binning: the walk's counters and status words, and K (which the walk adds up)
+    c.ptr[5] = (w.n > 0 && plan.spans) ? w.walk : nullptr; c.words[5] = span_walk_words(w.n);
+    c.ptr[6] = (w.n > 0 && plan.spans) ? reinterpret_cast<uint32_t*>(R.out.num_instances) : nullptr; c.words[6] = 2;
     size_t most = 0;
-    for (int k = 0; k < 5; ++k) most = std::max(most, c.ptr[k] ? c.words[k] : 0);
+    for (int k = 0; k < ClearJob::kSlots; ++k) most = std::max(most, c.ptr[k] ? c.words[k] : 0);
     c.grid = (unsigned)std::max<size_t>(1, std::min<size_t>((most + 255) / 256, 4 * (size_t)device_sm_count()));
     clears.add(c);
   }
@@ -1637,6 +1773,7 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     DepthKeysArgs a{reqs[live[i]].proj.depth, w.rect, w.n, w.dkeys[0], w.dvals[0], w.sort_d,
+                    reqs[live[i]].plan.spans ? w.walk + 4 : nullptr,
                     (unsigned)std::min<int64_t>((w.n + 4 * kRadixThreads - 1) / (4 * kRadixThreads),
                                                 2 * device_sm_count())};
     keys.add(a);
@@ -1644,15 +1781,32 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
   }
   if ((e = launch_batch(depth_keys_kernel, keys, kRadixThreads, 0, st)) != cudaSuccess) return e;
   if ((e = radix_sort(dsort, nl, true, st, dcur)) != cudaSuccess) return e;
-  // 2. Kept tiles per warp of 32 depth-ordered Gaussians (row spans), and for span binning the
-  //    kept row spans per warp; first instance (and first span) of each warp; K.
+  // 2. Instance path: kept tiles per warp of 32 depth-ordered Gaussians (row spans); first
+  //    instance of each warp and K; the instances in depth order, with the tile-digit histograms.
+  //    Span binning: the single-pass span walk (spans in depth order, K, the row histogram).
   BatchLaunch<WalkArgs> walks;
-  ScanArgs<uint32_t, uint64_t> scans[2 * kMaxBatch];
+  BatchLaunch<SpanWalkArgs> swalks;
+  ScanArgs<uint32_t, uint64_t> scans[kMaxBatch];
   int nscan = 0;
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     const BinRequest& R = reqs[live[i]];
     w.order = w.dvals[dcur[i]];
+    if (R.plan.spans) {
+      SpanWalkArgs a{};
+      a.order = w.order; a.rect = w.rect; a.mean2d = w.m2; a.conic_opacity = w.co; a.n = w.n;
+      a.tiles_x = w.tiles_x; a.tiles_y = w.tiles_y; a.err = w.err;
+      a.pass_bit = 1u << kMaxPasses; a.spin_limit = kLookbackSpins;
+      a.cap = R.plan.capacity;
+      a.keys = w.skeys[0]; a.vals = w.svals[0];
+      a.hist = w.sort_t;
+      a.num_instances = R.out.num_instances;
+      a.counters = w.walk;
+      a.status = reinterpret_cast<uint64_t*>(w.walk + 64);
+      a.grid = (unsigned)((w.n + kWalkThreads - 1) / kWalkThreads);
+      swalks.add(a);
+      continue;
+    }
     const int64_t nwarps = (w.n + 31) / 32;
     WalkArgs a{};
     a.order = w.order; a.rect = w.rect; a.mean2d = w.m2; a.conic_opacity = w.co; a.n = w.n;
@@ -1660,45 +1814,32 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     a.wcount = w.dkeys[dcur[i] ^ 1];
     a.wfirst = w.first; a.cap = R.plan.capacity;
     a.hist = w.sort_t;
-    if (R.plan.spans) {
-      a.scount = w.dvals[dcur[i] ^ 1];
-      a.sfirst = w.sfirst;
-      a.span_n = w.span_n;
-      a.keys = w.skeys[0]; a.vals = w.svals[0];
-    } else {
-      a.keys = w.ikeys[0]; a.vals = w.ivals[0];
-      a.passes = radix_pass_count(R.plan.tile_bits); a.width = radix_digit_width(R.plan.tile_bits);
-    }
+    a.keys = w.ikeys[0]; a.vals = w.ivals[0];
+    a.passes = radix_pass_count(R.plan.tile_bits); a.width = radix_digit_width(R.plan.tile_bits);
     a.grid = (unsigned)((nwarps + kWalkWarps - 1) / kWalkWarps);
     walks.add(a);
     scans[nscan++] = ScanArgs<uint32_t, uint64_t>{a.wcount, nwarps, w.first, reinterpret_cast<uint64_t*>(w.partials),
                                                   R.out.num_instances, 0};
-    if (R.plan.spans)
-      scans[nscan++] = ScanArgs<uint32_t, uint64_t>{a.scount, nwarps, w.sfirst, w.spartials, w.span_n, 0};
   }
+  if ((e = launch_batch(span_walk_kernel, swalks, kWalkThreads, 0, st)) != cudaSuccess) return e;
   if ((e = launch_batch(walk_count_kernel, walks, kWalkThreads, 0, st)) != cudaSuccess) return e;
-  for (int s0 = 0; s0 < nscan; s0 += kMaxBatch)
-    if ((e = exclusive_scan(scans + s0, std::min(kMaxBatch, nscan - s0), st)) != cudaSuccess) return e;
-  // 3. Instances (or row spans) in depth order, with the digit histograms of the sort that follows;
-  // 4. stable sort by tile id (or by row).
-  BatchLaunch<WalkArgs> iemit, semit;
-  for (int i = 0; i < nl; ++i) (reqs[live[i]].plan.spans ? semit : iemit).add(walks.b.a[i]);
-  if ((e = launch_batch(walk_emit_kernel, iemit, kWalkThreads, 0, st)) != cudaSuccess) return e;
-  if ((e = launch_batch(span_emit_kernel, semit, kWalkThreads, 0, st)) != cudaSuccess) return e;
+  if ((e = exclusive_scan(scans, nscan, st)) != cudaSuccess) return e;
+  if ((e = launch_batch(walk_emit_kernel, walks, kWalkThreads, 0, st)) != cudaSuccess) return e;
+  // 3. Stable sort by tile id (instance path) or by row (span binning).
   SortJob tsort[kMaxBatch];
   int tcur[kMaxBatch];
   for (int i = 0; i < nl; ++i) {
     Work& w = W[live[i]];
     const BinRequest& R = reqs[live[i]];
-    if (R.plan.spans)
+    if (R.plan.spans)  // (bit kMaxPasses of the error word is the span walk's)
       tsort[i] = SortJob{{w.skeys[0], w.skeys[1]}, {w.svals[0], w.svals[1]}, w.span_n, 0,
-                         R.plan.capacity, R.plan.row_bits, w.sort_t, w.err, kMaxPasses};
+                         R.plan.capacity, R.plan.row_bits, w.sort_t, w.err, kMaxPasses + 1};
     else
       tsort[i] = SortJob{{w.ikeys[0], w.ikeys[1]}, {w.ivals[0], w.ivals[1]}, R.out.num_instances, 0,
                          R.plan.capacity, R.plan.tile_bits, w.sort_t, w.err, kMaxPasses};
   }
   if ((e = radix_sort(tsort, nl, true, st, tcur)) != cudaSuccess) return e;
-  // 5. Tile ranges (instance records), or the span expansion into the tile lists.
+  // 4. Tile ranges (instance records), or the span expansion into the tile lists.
   BatchLaunch<RangesArgs> ranges;
   BatchLaunch<SpanArgs> scnt, sexp;
   size_t sexp_smem = 0;

@@ -70,7 +70,7 @@ struct BinPlan {
   // workspace carve-up (byte offsets)
   size_t off_dkeys[2], off_dvals[2], off_first, off_ikeys[2], off_ivals, off_err, off_sort_d, off_sort_t,
       off_partials, total;
-  size_t off_svals, off_sfirst, off_span_n, off_spartials, off_ctab, off_rowtot;  // span binning only
+  size_t off_svals, off_walk, off_ctab, off_rowtot;  // span binning only
   int64_t partial_cap;  // entries available for scan partials
 };
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);
