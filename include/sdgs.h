@@ -242,6 +242,19 @@ int sdgs_lookback_selftest_workspace_size(int64_t n, size_t* bytes);
 int sdgs_bin_sort_failure_selftest(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
                                    size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                                    void* stream);
+/* Test support for the span walk's bounded wait (no counterpart in the paper): sdgs_bin_sort of
+ * an image of at most 256 tiles per side (span binning) with the span walk's block tickets
+ * starting at first_ticket instead of 0 and its look-back giving up after spin_limit polling
+ * rounds (each a short sleep).  With first_ticket > 0 the walk blocks before it never run, so the
+ * block that waits on them gives up, flags the error and carries on: the lists stay empty, the
+ * device instance count becomes -1 and, with num_instances_host, the call returns
+ * SDGS_ERR_TIMEOUT.  Every write stays inside the caller's buffers.  Other arguments as
+ * sdgs_bin_sort.  Errors: SDGS_ERR_INVALID_ARG (first_ticket > 2^20, spin_limit outside [1, 2^20],
+ * an image wider or taller than 256 tiles, or as sdgs_bin_sort), SDGS_ERR_WORKSPACE,
+ * SDGS_ERR_TIMEOUT, SDGS_ERR_CUDA. */
+int sdgs_span_walk_selftest(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                            size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                            uint32_t first_ticket, int32_t spin_limit, void* stream);
 int sdgs_lookback_selftest(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out,
                            int64_t n, uint32_t first_ticket, int32_t spin_limit, void* workspace,
                            size_t workspace_bytes, void* stream);

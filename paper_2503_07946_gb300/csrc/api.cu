@@ -184,7 +184,7 @@ extern "C" {
 
 static int bin_sort_impl(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
                          size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
-                         void* stream, uint32_t inject_err) {
+                         void* stream, uint32_t inject_err, uint32_t walk_ticket = 0, int spin_limit = 0) {
   g_error[0] = 0;
   SDGS_TRY(check_projected(proj));
   SDGS_TRY(check_view(view));
@@ -195,7 +195,12 @@ static int bin_sort_impl(const sdgs_projected* proj, const sdgs_view* view, void
     return SDGS_ERR_WORKSPACE;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st, inject_err),
+  if (walk_ticket != 0u && !plan.spans) {
+    set_error("the span walk self-test needs an image of at most 256 tiles per side (span binning)");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  SDGS_TRY(cuda_status(launch_bin_sort(*proj, *view, plan, (char*)workspace, *out, st, inject_err, walk_ticket,
+                                       spin_limit),
                        "bin_sort launch"));
   return finish_bin_sort(plan, (const char*)workspace, out, num_instances_host, st);
 }
@@ -242,6 +247,18 @@ int sdgs_bin_sort_failure_selftest(const sdgs_projected* proj, const sdgs_view* 
                                    size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
                                    void* stream) {
   return bin_sort_impl(proj, view, workspace, workspace_bytes, out, num_instances_host, stream, 1u);
+}
+
+int sdgs_span_walk_selftest(const sdgs_projected* proj, const sdgs_view* view, void* workspace,
+                            size_t workspace_bytes, const sdgs_bins* out, int64_t* num_instances_host,
+                            uint32_t first_ticket, int32_t spin_limit, void* stream) {
+  g_error[0] = 0;
+  if (first_ticket > (1u << 20) || spin_limit < 1 || spin_limit > (1 << 20)) {
+    set_error("span walk self-test: first_ticket must be <= 2^20 and spin_limit in [1, 2^20]");
+    return SDGS_ERR_INVALID_ARG;
+  }
+  return bin_sort_impl(proj, view, workspace, workspace_bytes, out, num_instances_host, stream, 0u, first_ticket,
+                       spin_limit);
 }
 
 }  // extern "C"

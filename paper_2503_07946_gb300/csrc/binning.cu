@@ -1755,11 +1755,16 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
     clears.add(c);
   }
   e = launch_batch(clear_kernel, clears, 256, 0, st);
-  for (int j = 0; j < count && e == cudaSuccess; ++j)
-    if (reqs[j].inject_err != 0u) {  // test support: as if a pass had given up waiting
+  for (int j = 0; j < count && e == cudaSuccess; ++j) {  // test support
+    if (reqs[j].inject_err != 0u) {  // as if a pass had given up waiting
       set_word_kernel<<<1, 1, 0, st>>>(W[j].err, reqs[j].inject_err);
       e = cudaGetLastError();
     }
+    if (e == cudaSuccess && reqs[j].walk_ticket != 0u && reqs[j].plan.spans && W[j].n > 0) {
+      set_word_kernel<<<1, 1, 0, st>>>(W[j].walk, reqs[j].walk_ticket);  // the span walk's first ticket
+      e = cudaGetLastError();
+    }
+  }
   if (e != cudaSuccess) return e;
   // Only the requests with Gaussians go on (the others are complete: no instances, empty ranges).
   int live[kMaxBatch], nl = 0;
@@ -1796,7 +1801,7 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
       SpanWalkArgs a{};
       a.order = w.order; a.rect = w.rect; a.mean2d = w.m2; a.conic_opacity = w.co; a.n = w.n;
       a.tiles_x = w.tiles_x; a.tiles_y = w.tiles_y; a.err = w.err;
-      a.pass_bit = 1u << kMaxPasses; a.spin_limit = kLookbackSpins;
+      a.pass_bit = 1u << kMaxPasses; a.spin_limit = R.spin_limit > 0 ? R.spin_limit : kLookbackSpins;
       a.cap = R.plan.capacity;
       a.keys = w.skeys[0]; a.vals = w.svals[0];
       a.hist = w.sort_t;
@@ -1873,8 +1878,9 @@ cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_
 }
 
 cudaError_t launch_bin_sort(const sdgs_projected& proj, const sdgs_view& v, const BinPlan& plan, char* ws,
-                            const sdgs_bins& out, cudaStream_t st, uint32_t inject_err) {
-  const BinRequest r{proj, v, plan, ws, out, inject_err};
+                            const sdgs_bins& out, cudaStream_t st, uint32_t inject_err, uint32_t walk_ticket,
+                            int spin_limit) {
+  const BinRequest r{proj, v, plan, ws, out, inject_err, walk_ticket, spin_limit};
   return launch_bin_sort_batch(&r, 1, st);
 }
 

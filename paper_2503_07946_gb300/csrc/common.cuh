@@ -76,7 +76,8 @@ struct BinPlan {
 BinPlan plan_bins(int64_t n, int64_t capacity, int width, int height);
 // inject_err != 0 (test support only) starts the sort's error word at that value.
 cudaError_t launch_bin_sort(const sdgs_projected& p, const sdgs_view& v, const BinPlan& plan,
-                            char* ws, const sdgs_bins& out, cudaStream_t st, uint32_t inject_err = 0);
+                            char* ws, const sdgs_bins& out, cudaStream_t st, uint32_t inject_err = 0,
+                            uint32_t walk_ticket = 0, int spin_limit = 0);
 
 // Binning of up to kMaxBinBatch requests with one launch per step (each kernel serves request
 // blockIdx.y); the same results as binning each request on its own.
@@ -88,6 +89,10 @@ struct BinRequest {
   char* ws;
   sdgs_bins out;
   uint32_t inject_err;
+  // test support: the span walk's block tickets start here, and its waits give up after this
+  // many polling rounds (0: the default)
+  uint32_t walk_ticket = 0;
+  int spin_limit = 0;
 };
 cudaError_t launch_bin_sort_batch(const BinRequest* reqs, int count, cudaStream_t st);
 size_t lookback_selftest_bytes(int64_t n);

@@ -106,6 +106,9 @@ SIGNATURES = {
     "sdgs_bin_sort_failure_selftest": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p,
                                         ctypes.c_size_t, ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.c_void_p], ctypes.c_int),
+    "sdgs_span_walk_selftest": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.c_void_p,
+                                 ctypes.c_size_t, ctypes.POINTER(Bins), ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
     "sdgs_bin_sort_static": ([ctypes.POINTER(Projected), ctypes.POINTER(View), ctypes.POINTER(Bins),
                               ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], ctypes.c_int),
     "sdgs_alu_peak_probe": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
@@ -317,6 +320,17 @@ def bin_sort_failure_selftest(proj: ProjectedBuffers, view: View, bins: BinBuffe
     _check(lib().sdgs_bin_sort_failure_selftest(ctypes.byref(proj.struct()), ctypes.byref(view), _ptr(bins.workspace),
                                                 bins.ws_bytes, ctypes.byref(bins.struct()),
                                                 ctypes.byref(k) if sync else None, _stream(stream)))
+    return int(k.value) if sync else None
+
+
+def span_walk_selftest(proj: ProjectedBuffers, view: View, bins: BinBuffers, first_ticket: int, spin_limit: int,
+                       sync: bool = True, stream=None):
+    """sdgs_span_walk_selftest: bin_sort with the span walk's block tickets starting at first_ticket
+    and its waits giving up after spin_limit rounds (test support for its bounded wait)."""
+    k = ctypes.c_int64(0)
+    _check(lib().sdgs_span_walk_selftest(ctypes.byref(proj.struct()), ctypes.byref(view), _ptr(bins.workspace),
+                                         bins.ws_bytes, ctypes.byref(bins.struct()), ctypes.byref(k) if sync else None,
+                                         int(first_ticket), int(spin_limit), _stream(stream)))
     return int(k.value) if sync else None
 
 

@@ -125,6 +125,11 @@ def test_failure_test_support_rejects_invalid_arguments_before_any_gpu_work(lib)
     assert rc == 1 and b"NULL" in lib.sdgs_last_error()
     rc = lib.sdgs_bin_sort_failure_selftest(None, None, None, 0, None, None, None)
     assert rc == 1 and b"projected" in lib.sdgs_last_error()
+    for ticket, spins in (((1 << 20) + 1, 100), (1, 0), (1, (1 << 20) + 1)):
+        rc = lib.sdgs_span_walk_selftest(None, None, None, 0, None, None, ticket, spins, None)
+        assert rc == 1 and b"self-test" in lib.sdgs_last_error(), (ticket, spins)
+    rc = lib.sdgs_span_walk_selftest(None, None, None, 0, None, None, 1, 100, None)
+    assert rc == 1 and b"projected" in lib.sdgs_last_error()
 
 
 def test_deferred_renderer_raises_when_the_previous_frame_failed():

@@ -80,3 +80,27 @@ def test_binning_failure_empties_the_lists_and_is_reported():
     assert int(bins.num_instances.item()) == -1
     # and the next ordinary call bins the frame again
     assert sdgs.bin_sort(proj, view, bins, sync=True) == k
+
+
+def test_span_walk_wait_gives_up_and_the_failure_is_reported():
+    """The span walk's blocks start at ticket 1, so the block that waits on block 0 (which never
+    runs) gives up after its 2000 polling rounds: the call reports SDGS_ERR_TIMEOUT, the count is
+    -1, every list is empty, nothing was written outside the buffers, and the next ordinary call
+    bins the frame again."""
+    scene, cam = synth.config_scene(0), synth.config_cameras(0)[0]
+    got, (dev, st, view, proj) = U.gpu_project(scene, cam)
+    cap = 1 << 20
+    bins = sdgs.BinBuffers(scene.n, cap + 4096, cam.width, cam.height)
+    guard = bins.point_list[cap:]
+    bins.capacity = cap  # the buffers' last 4096 entries lie past the capacity the call sees
+    guard.fill_(-7)
+    k = sdgs.bin_sort(proj, view, bins, sync=True)
+    assert k > 0 and scene.n > 512  # several walk blocks
+    with pytest.raises(sdgs.SdgsError) as e:
+        sdgs.span_walk_selftest(proj, view, bins, first_ticket=1, spin_limit=2000, sync=True)
+    assert e.value.code == 5
+    assert int(bins.num_instances.item()) == -1
+    assert int(bins.ranges.abs().sum().item()) == 0
+    assert (guard == -7).all()
+    assert sdgs.bin_sort(proj, view, bins, sync=True) == k
+
