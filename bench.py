@@ -326,34 +326,31 @@ def oracle_frames_report() -> dict:
 
 def launches_per_frame(n: int, capacity: int, width: int, height: int) -> int:
     """Kernels libsdgs launches for one render: slice_project; the binning clear kernel; the
-    depth keys (with the depth digit histograms); 4 depth radix passes; the kept-tile (and
-    row-span) count per warp of 32 Gaussians; their scans (one kernel up to 11264 warps, else
-    three); then, for images of at most 256 tiles per side, the span emit (with the row
+    depth keys (with the depth digit histograms); 4 depth radix passes; then, for images of at
+    most 256 tiles per side, the single-pass span walk (row spans in depth order, K, the row
     histogram), ceil(row bits / 8) row radix passes, the per-chunk column counts and the
-    expansion into the tile lists, else the instance emit (with the tile digit histograms),
-    ceil(tile bits / 8) tile radix passes and the tile ranges; the rasteriser."""
+    expansion into the tile lists; else the kept-tile count per warp of 32 Gaussians, its scan
+    (one kernel up to 11264 warps, else three), the instance emit (with the tile digit
+    histograms), ceil(tile bits / 8) tile radix passes and the tile ranges; the rasteriser."""
     tx, ty = (width + 15) // 16, (height + 15) // 16
-    scan = 1 if (n + 31) // 32 <= 11 * 1024 else 3
-    head = 1 + 1 + 1 + 4 + 1 + scan
-    if capacity <= 0:
-        return head + 1 + 1
+    head = 1 + 1 + 1 + 4
     if tx <= 256 and ty <= 256:
         row_passes = (max(0, (ty - 1).bit_length()) + 7) // 8
         return head + 1 + row_passes + 2 + 1
+    scan = 1 if (n + 31) // 32 <= 11 * 1024 else 3
     tile_passes = (max(0, (tx * ty - 1).bit_length()) + 7) // 8
-    return head + 1 + tile_passes + 1 + 1
+    return head + 1 + scan + 1 + tile_passes + 1 + 1
 
 
-def binning_bytes(n: int, k: int, spans: int) -> dict:
+def binning_bytes(n: int, k: int, spans: int, visible: int) -> dict:
     """Algorithmic DRAM bytes of one span-binning call: each kernel's reads and writes once.
     depth keys 20 B per Gaussian (depth 4 + rect 8 in, key + value 8 out); 4 depth passes 16 B per
-    Gaussian each (key + value in and out); the count walk and the span emit 36 B per Gaussian each
-    (order 4, rect 8, mean2d 8, conic 16); the span emit writes 8 B per span; the row pass 16 B per
-    span; the column count reads 4 B per span; the expansion reads 8 B per span and writes 4 B per
-    instance (the point list).  The scans and per-chunk tables are a few hundred kB."""
-    per_kernel = {"depth_keys": 20 * n, "depth_passes": 64 * n, "walk_count": 36 * n,
-                  "span_emit": 36 * n + 8 * spans, "row_pass": 16 * spans, "span_count": 4 * spans,
-                  "span_expand": 8 * spans + 4 * k}
+    Gaussian each (key + value in and out); the span walk 36 B per visible Gaussian (order 4,
+    rect 8, mean2d 8, conic 16) and 8 B written per span; the row pass 16 B per span; the column
+    count reads 4 B per span; the expansion reads 8 B per span and writes 4 B per instance (the
+    point list).  The per-chunk tables and block statuses are a few hundred kB."""
+    per_kernel = {"depth_keys": 20 * n, "depth_passes": 64 * n, "span_walk": 36 * visible + 8 * spans,
+                  "row_pass": 16 * spans, "span_count": 4 * spans, "span_expand": 8 * spans + 4 * k}
     return {"total": sum(per_kernel.values()), "per_kernel": per_kernel}
 
 
@@ -599,7 +596,7 @@ def run_ours(args, rank: int, world: int):
     ex2_rate = (evals / steps) / (raster_ms * 1e-3) / 1e12
     slice_gbs = (scene.n * 148 + visible * (192 + 60)) / (float(phase[:, 0].mean()) * 1e-3) / 1e9
     spans = count_spans(r.bins, k_inst, (W + 15) // 16)
-    bin_bytes = binning_bytes(scene.n, k_inst, spans)
+    bin_bytes = binning_bytes(scene.n, k_inst, spans, visible)
     bin_gbs = bin_bytes["total"] / (float(phase[:, 1].mean()) * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": steps, "warmup": warm,
