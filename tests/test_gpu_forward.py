@@ -257,9 +257,9 @@ def test_renderer_deferred_check_matches_and_grows(scene0):
 def test_bin_sort_batch_equals_binning_each_problem_alone():
     """sdgs_bin_sort_batch (one launch per step for several problems, as the render server bins
     the requests it admits together) gives every problem exactly the lists, ranges and count of
-    sdgs_bin_sort on its own: mixed sizes and tile grids, an empty problem, a single-tile image,
-    and an overflowing capacity."""
-    cases = [(5000, 256, 256, 3), (20000, 1352, 1014, 4), (0, 64, 64, 0), (1, 16, 16, 1),
+    sdgs_bin_sort on its own: mixed sizes and tile grids (span binning and, for an image 264 tiles
+    wide, instance records), an empty problem, a single-tile image, and an overflowing capacity."""
+    cases = [(4000, 4224, 64, 10), (20000, 1352, 1014, 4), (0, 64, 64, 0), (1, 16, 16, 1),
              (3000, 1920, 1080, 5), (16000, 48, 32, 9), (300, 100, 70, 2), (20000, 1352, 1014, 11)]
     projs, views, alone, batch = [], [], [], []
     for n, W, H, seed in cases:
