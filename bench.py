@@ -31,7 +31,7 @@ import synth  # noqa: E402
 
 METRIC = "Mpix/s & FPS at 800×800/300k Gaussians; fwd+bwd it/s; p50/p99 serving latency"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# FP32 work of compositing (the survey's count): 15 FLOP per evaluated (pixel, Gaussian) pair
+# FP32 work of compositing: 15 FLOP per evaluated (pixel, Gaussian) pair
 # (offsets, exponent, opacity clamp and tests, transmittance) plus one ex2, and 3 FMA = 6 FLOP per
 # blended pair (the colour update).  The counting variant of render_fwd counts both kinds of pair.
 FLOP_PER_EVAL = 15
