@@ -69,8 +69,9 @@ __device__ __forceinline__ bool span_row(const SpanRule& r, int ty, float* lo, f
   const float d2 = fminf(ey1, fmaxf(ey0, -r.dyr));
   const float s2 = __fsqrt_rn(fmaxf(__fsub_rn(r.aQ, __fmul_rn(__fmul_rn(r.det, d2), d2)), 0.f));
   const float x_min = __fsub_rn(__fdiv_rn(__fsub_rn(-__fmul_rn(r.b, d2), s2), r.a), r.padx);
-  *lo = ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(r.u, x_min), 15.5f), 16.f));
-  *hi = floorf(__fdiv_rn(__fsub_rn(__fadd_rn(r.u, x_max), 0.5f), 16.f));
+  // (x / 16 correctly rounded is x * 2^-4 correctly rounded: the same float, one multiply)
+  *lo = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(r.u, x_min), 15.5f), 0.0625f));
+  *hi = floorf(__fmul_rn(__fsub_rn(__fadd_rn(r.u, x_max), 0.5f), 0.0625f));
   return true;
 }
 
