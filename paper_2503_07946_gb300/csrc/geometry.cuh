@@ -125,9 +125,9 @@ __device__ __forceinline__ float slice_one(const float L[28], const float m[7], 
     for (int c = r + 1; c < 7; ++c) {
       if (r < 4 && c > r + 3) continue;  // structurally zero: the t, d rows of L end at column r + 3
       const float a = B[r][r], b = B[r][c];
-      const float h = sqrtf(a * a + b * b);
-      if (!(h > 0.f)) continue;
-      const float ih = 1.f / h;
+      const float h2 = a * a + b * b;
+      if (!(h2 > 0.f)) continue;
+      const float ih = rsqrtf(h2);  // (a rotation off by a few ulp: far below the path's tolerance)
       const float cs = a * ih, sn = b * ih;
 #pragma unroll
       for (int i = r; i < 7; ++i) {
