@@ -270,7 +270,7 @@ __device__ __forceinline__ void solve_upper_T(const float Lw[N][N], const float 
     float s = dX[i];
 #pragma unroll
     for (int k = i + 1; k < N; ++k) s -= Lw[k][i] * dY[k];
-    dY[i] = s / Lw[i][i];
+    dY[i] = __fdividef(s, Lw[i][i]);
   }
 }
 
@@ -330,7 +330,7 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
   // ---- SH colour ----
   {
     float w0 = s.mu[0] - cam.campos[0], w1 = s.mu[1] - cam.campos[1], w2 = s.mu[2] - cam.campos[2];
-    const float rn = 1.f / sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+    const float rn = rsqrtf(w0 * w0 + w1 * w1 + w2 * w2);
     const float x = w0 * rn, y = w1 * rn, z = w2 * rn;
     float Y[16];
     sh_basis(x, y, z, Y);
@@ -393,7 +393,7 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
 
   // ---- conic = inverse of the 2D covariance ----
   const float ca = ps.cov[0], cb = ps.cov[1], cc = ps.cov[2];
-  const float id2 = 1.f / (ps.det * ps.det);
+  const float id2 = __fdividef(1.f, ps.det * ps.det);
   const float da = (-cc * cc * dA_ + cb * cc * dB_ - cb * cb * dC_) * id2;
   const float db = (2.f * cb * cc * dA_ - (ca * cc + cb * cb) * dB_ + 2.f * ca * cb * dC_) * id2;
   const float dc = (-cb * cb * dA_ + ca * cb * dB_ - ca * ca * dC_) * id2;
@@ -423,7 +423,7 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
 
   // ---- Tm = J R and the projected mean ----
   {
-    const float z = ps.p[2], rz = 1.f / z;
+    const float z = ps.p[2], rz = __fdividef(1.f, z);
     float drz = 0.f, dtx = 0.f, dty = 0.f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {

@@ -44,7 +44,7 @@ __device__ __forceinline__ Query query_for(const Query& q, const float m[7], flo
   *rn = 0.f;
   if (q.dir_mode == 1) {
     const float w0 = m[0] - q.campos[0], w1 = m[1] - q.campos[1], w2 = m[2] - q.campos[2];
-    const float inv = 1.f / sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+    const float inv = rsqrtf(w0 * w0 + w1 * w1 + w2 * w2);
     r.d[0] = w0 * inv; r.d[1] = w1 * inv; r.d[2] = w2 * inv;
     *rn = inv;
   }
@@ -154,7 +154,7 @@ __device__ __forceinline__ float slice_one(const float L[28], const float m[7], 
     float acc = e[i];
 #pragma unroll
     for (int j = 0; j < i; ++j) acc -= s.K11[i][j] * s.v[j];
-    s.v[i] = acc / s.K11[i][i];
+    s.v[i] = __fdividef(acc, s.K11[i][i]);
   }
 #pragma unroll
   for (int r = 0; r < 3; ++r)
@@ -175,20 +175,23 @@ __device__ __forceinline__ float slice_one(const float L[28], const float m[7], 
 #pragma unroll
   for (int k = 0; k < 7; ++k) S66 += r6[k] * r6[k];
   float (&C)[3][3] = s.C;
-  C[0][0] = sqrtf(S44);
-  const float ic0 = 1.f / C[0][0];
+  // (square roots and their reciprocals from one approximate reciprocal square root each)
+  const float ic0 = rsqrtf(S44);
+  C[0][0] = S44 * ic0;
   C[1][0] = S54 * ic0;
   C[2][0] = S64 * ic0;
-  C[1][1] = sqrtf(S55 - C[1][0] * C[1][0]);
-  const float ic1 = 1.f / C[1][1];
+  const float p1 = S55 - C[1][0] * C[1][0];
+  const float ic1 = rsqrtf(p1);
+  C[1][1] = p1 * ic1;
   C[2][1] = (S65 - C[2][0] * C[1][0]) * ic1;
-  C[2][2] = sqrtf(S66 - C[2][0] * C[2][0] - C[2][1] * C[2][1]);
-  const float ic2 = 1.f / C[2][2];
+  const float p2 = S66 - C[2][0] * C[2][0] - C[2][1] * C[2][1];
+  const float ic2 = rsqrtf(p2);
+  C[2][2] = p2 * ic2;
   C[0][1] = C[0][2] = C[1][2] = 0.f;
   s.y[0] = e[1] * ic0;
   s.y[1] = (e[2] - C[1][0] * s.y[0]) * ic1;
   s.y[2] = (e[3] - C[2][0] * s.y[0] - C[2][1] * s.y[1]) * ic2;
-  s.e_t = -0.5f * q.lambda_t * e[0] * e[0] / s.St;
+  s.e_t = __fdividef(-0.5f * q.lambda_t * e[0] * e[0], s.St);
   s.e_d = -0.5f * q.lambda_d * (s.y[0] * s.y[0] + s.y[1] * s.y[1] + s.y[2] * s.y[2]);
   return alpha * expf(s.e_t) * expf(s.e_d);
 }
@@ -210,7 +213,7 @@ __device__ __forceinline__ bool project_one(const Camera& cam, const SliceState&
     ps.p[r] = cam.R[r][0] * s.mu[0] + cam.R[r][1] * s.mu[1] + cam.R[r][2] * s.mu[2] + cam.T[r];
   const float z = ps.p[2];
   if (!(z >= cam.near_plane)) return false;
-  const float rz = 1.f / z;
+  const float rz = __fdividef(1.f, z);
   const float xz = ps.p[0] * rz, yz = ps.p[1] * rz;
   ps.txz = fminf(cam.lim_x, fmaxf(-cam.lim_x, xz));
   ps.tyz = fminf(cam.lim_y, fmaxf(-cam.lim_y, yz));

@@ -66,7 +66,7 @@ __device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i)
   float u = 0.f, v = 0.f, r = 0.f;
   int rx0 = 0, ry0 = 0, rx1 = 0, ry1 = 0;
   if (keep) {
-    const float rz = 1.f / ps.p[2];
+    const float rz = __fdividef(1.f, ps.p[2]);
     u = a.cam.fx * ps.p[0] * rz + a.cam.cx;
     v = a.cam.fy * ps.p[1] * rz + a.cam.cy;
     const float mid = 0.5f * (ps.cov[0] + ps.cov[2]);
@@ -84,7 +84,7 @@ __device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i)
     a.radius[i] = 0;
     return;
   }
-  const float idet = 1.f / ps.det;
+  const float idet = __fdividef(1.f, ps.det);
   a.mean2d[i] = make_float2(u, v);
   a.conic_opacity[i] = make_float4(ps.cov[2] * idet, -ps.cov[1] * idet, ps.cov[0] * idet, alpha_c);
   a.depth[i] = ps.p[2];
@@ -94,7 +94,7 @@ __device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i)
 
   // SH colour toward the Gaussian from the camera centre.
   float dx = s.mu[0] - a.cam.campos[0], dy = s.mu[1] - a.cam.campos[1], dz = s.mu[2] - a.cam.campos[2];
-  const float rn = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+  const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
   dx *= rn; dy *= rn; dz *= rn;
   float Y[16];
   sh_basis(dx, dy, dz, Y);
