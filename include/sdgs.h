@@ -129,14 +129,18 @@ typedef struct sdgs_bins {
   int64_t capacity;
 } sdgs_bins;
 
-/* Gradients accumulated by sdgs_render_bwd (device, caller-allocated and zeroed; the call adds).
- *   dmean7 [n][7], dL28 [n][28], dopacity [n], dsh [n][16][3] */
+/* Gradients of sdgs_render_bwd (device, caller-allocated).
+ *   dmean7 [n][7], dL28 [n][28], dopacity [n], dsh [n][16][3]
+ *   overwrite  0: the call adds (+=) into the arrays, which the caller has zeroed (gradient
+ *              accumulation over several renders); nonzero: the call writes every entry (zero for
+ *              culled Gaussians) and dlambda, so the arrays need no clearing */
 typedef struct sdgs_grads {
   float* dmean7;
   float* dL28;
   float* dopacity;
   float* dsh;
-  float* dlambda; /* [2] d/d(lambda_t, lambda_d), accumulated (+=) like the others; may be NULL */
+  float* dlambda; /* [2] d/d(lambda_t, lambda_d), added to or written like the others; may be NULL */
+  int32_t overwrite;
 } sdgs_grads;
 
 /* Library version string, e.g. "sdgs 0.1.0 sm_103a". */
@@ -289,8 +293,8 @@ int sdgs_bwd_workspace_size(int64_t n, size_t* bytes);
 
 /* Adjoint of sdgs_render_fwd, sdgs_slice_project (projection, SH, conditioning, modulation and
  * Sigma = L L^T).  Inputs are the forward's scene, view, projected record, bins, final_T and
- * n_contrib, and dL_dimage [height][width][3] (device).  Gradients are ADDED to `grads`.  The
- * culling decisions, radius and tile rectangles are held fixed (they have no derivative); where
+ * n_contrib, and dL_dimage [height][width][3] (device).  Gradients are added to `grads` (or
+ * written, with grads->overwrite).  The culling decisions, radius and tile rectangles are held fixed (they have no derivative); where
  * the 0.99 opacity clamp or the colour clamp at 0 is active the corresponding derivative is 0.
  * `workspace` needs sdgs_bwd_workspace_size() bytes.
  * Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_CUDA. */

@@ -260,7 +260,17 @@ struct GeomBwdArgs {
   float* dopacity;
   float* dsh;
   float* dlambda;  // [2] or NULL
+  bool overwrite;  // write the gradients (zero for culled Gaussians) instead of adding to them
 };
+
+__device__ __forceinline__ void put_grad(const GeomBwdArgs& a, float* p, float v) {
+  if (a.overwrite) *p = v;
+  else atomicAdd(p, v);
+}
+__device__ __forceinline__ void put_grad4(const GeomBwdArgs& a, float4* p, float4 v) {
+  if (a.overwrite) *p = v;
+  else atomicAdd(p, v);
+}
 
 // For X = Lw^-1 Y with Lw lower triangular n x n (n = 3 or 4), given dX returns dY = Lw^-T dX.
 template <int N>
@@ -282,7 +292,20 @@ __global__ void __launch_bounds__(128, 3) geom_bwd_kernel(const GeomBwdArgs a) {
   float dlt = 0.f, dld = 0.f;
   if (i < a.n) {
     const ushort4 rc = a.rect[i];
-    if (rc.z > rc.x && rc.w > rc.y) geom_bwd_one(a, i, &dlt, &dld);
+    if (rc.z > rc.x && rc.w > rc.y) {
+      geom_bwd_one(a, i, &dlt, &dld);
+    } else if (a.overwrite) {  // a culled Gaussian: zero gradients
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* dLp = reinterpret_cast<float4*>(a.dL28 + 28 * i);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) dLp[q] = z;
+      float4* dshp = reinterpret_cast<float4*>(a.dsh + 48 * i);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) dshp[q] = z;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) a.dmean7[7 * i + k] = 0.f;
+      a.dopacity[i] = 0.f;
+    }
   }
   if (a.dlambda == nullptr) return;
 #pragma unroll
@@ -359,7 +382,7 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
       dY[(4 * q + 1) / 3] += v.y * dc[(4 * q + 1) % 3];
       dY[(4 * q + 2) / 3] += v.z * dc[(4 * q + 2) % 3];
       dY[(4 * q + 3) / 3] += v.w * dc[(4 * q + 3) % 3];
-      atomicAdd(dshp + q, make_float4(Y[(4 * q) / 3] * dc[(4 * q) % 3], Y[(4 * q + 1) / 3] * dc[(4 * q + 1) % 3],
+      put_grad4(a, dshp + q, make_float4(Y[(4 * q) / 3] * dc[(4 * q) % 3], Y[(4 * q + 1) / 3] * dc[(4 * q + 1) % 3],
                                       Y[(4 * q + 2) / 3] * dc[(4 * q + 2) % 3],
                                       Y[(4 * q + 3) / 3] * dc[(4 * q + 3) % 3]));
     }
@@ -501,7 +524,7 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
   // ---- alpha_cond = alpha exp(e_t) exp(e_d) ----
   {
     const float ft = expf(s.e_t), fd = expf(s.e_d);
-    atomicAdd(a.dopacity + i, dalc * ft * fd);
+    put_grad(a, a.dopacity + i, dalc * ft * fd);
     const float de_ = dalc * alpha_c;  // d alpha_c / d e_t = d alpha_c / d e_d = alpha_c
     const float e0 = q.t - m[3];
     // e_t = -1/2 lambda_t e0^2 / S_t
@@ -546,9 +569,9 @@ __device__ __forceinline__ void geom_bwd_one(const GeomBwdArgs& a, int64_t i, fl
 
   float4* dLp = reinterpret_cast<float4*>(a.dL28 + 28 * i);
 #pragma unroll
-  for (int q = 0; q < 7; ++q) atomicAdd(dLp + q, make_float4(dLg[4 * q], dLg[4 * q + 1], dLg[4 * q + 2], dLg[4 * q + 3]));
+  for (int q = 0; q < 7; ++q) put_grad4(a, dLp + q, make_float4(dLg[4 * q], dLg[4 * q + 1], dLg[4 * q + 2], dLg[4 * q + 3]));
 #pragma unroll
-  for (int k = 0; k < 7; ++k) atomicAdd(a.dmean7 + 7 * i + k, dm[k]);
+  for (int k = 0; k < 7; ++k) put_grad(a, a.dmean7 + 7 * i + k, dm[k]);
 }
 
 }  // namespace
@@ -558,7 +581,10 @@ size_t bwd_workspace_bytes(int64_t n) { return ((size_t)n * kG2 * sizeof(float) 
 cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& p,
                               const sdgs_bins& b, const float* final_T, const uint32_t* n_contrib,
                               const float* dL_dimage, char* ws, const sdgs_grads& g, cudaStream_t st) {
-  if (s.n == 0) return cudaSuccess;
+  if (s.n == 0) {
+    if (g.overwrite != 0 && g.dlambda != nullptr) return cudaMemsetAsync(g.dlambda, 0, 2 * sizeof(float), st);
+    return cudaSuccess;
+  }
   float* g2 = reinterpret_cast<float*>(ws);
   cudaError_t e = cudaMemsetAsync(g2, 0, (size_t)s.n * kG2 * sizeof(float), st);
   if (e != cudaSuccess) return e;
@@ -588,6 +614,11 @@ cudaError_t launch_render_bwd(const sdgs_scene& s, const sdgs_view& v, const sdg
   a.rect = reinterpret_cast<const ushort4*>(p.rect);
   a.g2 = g2;
   a.dmean7 = g.dmean7; a.dL28 = g.dL28; a.dopacity = g.dopacity; a.dsh = g.dsh; a.dlambda = g.dlambda;
+  a.overwrite = g.overwrite != 0;
+  if (a.overwrite && a.dlambda != nullptr) {  // (summed over the Gaussians by atomics)
+    e = cudaMemsetAsync(a.dlambda, 0, 2 * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+  }
   geom_bwd_kernel<<<(unsigned)((s.n + 127) / 128), 128, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -146,17 +146,18 @@ class Render7DGS(torch.autograd.Function):
         mean7, L28, opacity, sh = ctx.saved_tensors
         t = dict(mean7=mean7, L28=L28, opacity=opacity, sh=sh)
         scene = sdgs.scene_struct(t, *ctx.lam, ctx.dir_mode)
-        grads = {k: torch.zeros_like(v) for k, v in t.items()}
+        grads = {k: torch.empty_like(v) for k, v in t.items()}  # (written whole by the call)
         want_lam = ctx.needs_input_grad[4]
         if want_lam:  # otherwise no dlambda: the kernel skips that reduction
-            grads["lam"] = torch.zeros(2, dtype=torch.float32, device=mean7.device)
+            grads["lam"] = torch.empty(2, dtype=torch.float32, device=mean7.device)
         r = ctx.renderer
         if r.frames != ctx.frame:  # its projected records and tile lists now belong to a later frame
             raise RuntimeError("Render7DGS.backward: the Renderer has rendered %d more frame(s) since this image; "
                                "take the gradient before rendering again with it, or render each image whose "
                                "gradient is needed with its own Renderer" % (r.frames - ctx.frame))
         ws = torch.empty(max(sdgs.bwd_workspace_size(r.n), 256), dtype=torch.uint8, device=mean7.device)
-        sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, r.final_T, r.n_contrib, grad_image.contiguous(), ws, grads)
+        sdgs.render_bwd(scene, ctx.view, r.proj, r.bins, r.final_T, r.n_contrib, grad_image.contiguous(), ws, grads,
+                        overwrite=True)
         dlam = grads["lam"].to(ctx.lam_device) if want_lam else None
         return grads["mean7"], grads["L28"], grads["opacity"], grads["sh"], dlam, None, None, None
 

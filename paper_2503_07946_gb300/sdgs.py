@@ -53,7 +53,7 @@ class Bins(ctypes.Structure):
 
 class Grads(ctypes.Structure):
     _fields_ = [("dmean7", ctypes.c_void_p), ("dL28", ctypes.c_void_p), ("dopacity", ctypes.c_void_p),
-                ("dsh", ctypes.c_void_p), ("dlambda", ctypes.c_void_p)]
+                ("dsh", ctypes.c_void_p), ("dlambda", ctypes.c_void_p), ("overwrite", ctypes.c_int32)]
 
 
 class Agr(ctypes.Structure):
@@ -389,9 +389,11 @@ def bwd_workspace_size(n: int) -> int:
 
 def render_bwd(scene: Scene, view: View, proj: ProjectedBuffers, bins: BinBuffers, final_T: torch.Tensor,
                n_contrib: torch.Tensor, dL_dimage: torch.Tensor, workspace: torch.Tensor, grads: dict,
-               stream=None):
+               stream=None, overwrite: bool = False):
+    """grads: mean7, L28, opacity, sh (and optionally lam) tensors; the call adds to them, or with
+    overwrite=True writes them (they need no zeroing)."""
     g = Grads(_ptr(grads["mean7"]), _ptr(grads["L28"]), _ptr(grads["opacity"]), _ptr(grads["sh"]),
-              _ptr(grads.get("lam")))
+              _ptr(grads.get("lam")), 1 if overwrite else 0)
     _check(lib().sdgs_render_bwd(ctypes.byref(scene), ctypes.byref(view), ctypes.byref(proj.struct()),
                                  ctypes.byref(bins.struct()), _ptr(final_T), _ptr(n_contrib), _ptr(dL_dimage),
                                  _ptr(workspace), workspace.numel(), ctypes.byref(g), _stream(stream)))

@@ -169,3 +169,39 @@ def test_fp32_adjoint_matches_central_differences_of_the_fp32_render():
             checked += 1
     assert checked >= 80, (checked, jumps)
     assert worst < 0.05, worst
+
+
+def test_written_gradients_equal_added_gradients():
+    """render_bwd writing the gradients (into arrays full of NaN) gives what adding them into zeroed
+    arrays gives (the autograd Function uses the written form), and adding twice gives twice.  (The
+    per-Gaussian screen-space sums are added up by atomics across tiles, so two calls agree to
+    rounding, not bit for bit.)"""
+    scene, cam = _case("rotated")
+    dev = prender.scene_to_device(scene)
+    st = sdgs.scene_struct(dev, scene.lambda_t, scene.lambda_d, scene.dir_mode)
+    view = sdgs.view_struct(cam)
+    r = prender.Renderer(scene.n, cam.width, cam.height)
+    r.forward(st, view)
+    dL = torch.as_tensor(np.random.default_rng(5).normal(size=(cam.height, cam.width, 3)), dtype=torch.float32,
+                         device="cuda")
+    ws = torch.empty(max(sdgs.bwd_workspace_size(scene.n), 256), dtype=torch.uint8, device="cuda")
+    added = {k: torch.zeros_like(v) for k, v in dev.items()}
+    added["lam"] = torch.zeros(2, dtype=torch.float32, device="cuda")
+    written = {k: torch.full_like(v, float("nan")) for k, v in dev.items()}
+    written["lam"] = torch.full((2,), float("nan"), dtype=torch.float32, device="cuda")
+    sdgs.render_bwd(st, view, r.proj, r.bins, r.final_T, r.n_contrib, dL, ws, added)
+    sdgs.render_bwd(st, view, r.proj, r.bins, r.final_T, r.n_contrib, dL, ws, written, overwrite=True)
+    torch.cuda.synchronize()
+    culled = (r.proj.rect[:, 2] <= r.proj.rect[:, 0]) | (r.proj.rect[:, 3] <= r.proj.rect[:, 1])
+    assert 0 < int(culled.sum()) < scene.n
+    for k in ("mean7", "L28", "opacity", "sh", "lam"):
+        w, a = written[k], added[k]
+        assert not torch.isnan(w).any(), k  # every entry written
+        tol = 1e-5 * float(a.abs().max())
+        torch.testing.assert_close(w, a, rtol=1e-4, atol=tol)
+        if k != "lam":
+            assert (w.reshape(scene.n, -1)[culled] == 0).all(), k  # culled Gaussians: zero
+    sdgs.render_bwd(st, view, r.proj, r.bins, r.final_T, r.n_contrib, dL, ws, added)
+    torch.cuda.synchronize()
+    for k in ("mean7", "L28", "opacity", "sh"):
+        torch.testing.assert_close(added[k], 2 * written[k], rtol=1e-4, atol=2e-5 * float(written[k].abs().max()))
