@@ -100,15 +100,19 @@ class Renderer:
             self._k_event.record(st)
         self._k_capacity = self.bins.capacity
 
-    def forward(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
+    def forward(self, scene: sdgs.Scene, view: sdgs.View, stream=None, image: torch.Tensor | None = None
+                ) -> torch.Tensor:
+        """Renders into `image` ([height, width, 3] float32 CUDA) when given, else into the
+        renderer's own image buffer; returns the image."""
         self.frames += 1
         sdgs.slice_project(scene, view, self.proj, stream)
         if self.deferred_check:
             self._bin_deferred(view, stream)
         else:
             self.bin(view, stream)
-        sdgs.render_fwd(self.proj, self.bins, view, self.image, self.final_T, self.n_contrib, stream=stream)
-        return self.image
+        out = self.image if image is None else image
+        sdgs.render_fwd(self.proj, self.bins, view, out, self.final_T, self.n_contrib, stream=stream)
+        return out
 
     def forward_async(self, scene: sdgs.Scene, view: sdgs.View, stream=None) -> torch.Tensor:
         """Same three calls without the host read of the instance count (capacity must suffice)."""
@@ -132,7 +136,7 @@ class Render7DGS(torch.autograd.Function):
                  sh=sh.contiguous())
         lam_t, lam_d = (float(x) for x in lam.detach().cpu().tolist())  # no device round trip for a host lam
         scene = sdgs.scene_struct(t, lam_t, lam_d, dir_mode)
-        image = renderer.forward(scene, view).clone()
+        image = renderer.forward(scene, view, image=torch.empty_like(renderer.image))  # (the caller keeps it)
         ctx.renderer, ctx.view, ctx.lam, ctx.dir_mode = renderer, view, (lam_t, lam_d), dir_mode
         ctx.frame = renderer.frames
         ctx.lam_device = lam.device
