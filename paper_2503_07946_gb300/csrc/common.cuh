@@ -54,11 +54,15 @@ int device_sm_count();
 cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o,
                                  cudaStream_t st);
 
-// Batched slicing for the server: one argument block per request, uploaded by the caller.
-size_t slice_job_bytes();
-void fill_slice_job(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o, void* dst);
-cudaError_t launch_slice_project_batched(const void* jobs_device, int njobs, int64_t max_n,
-                                         cudaStream_t st);
+// Slicing of several requests (the server's): up to 8 per launch, each launch's arguments passed
+// by value; the same kernel as a single request, so the same results.
+constexpr int kMaxBinBatch = 8;
+struct SliceRequest {
+  sdgs_scene scene;
+  sdgs_view view;
+  sdgs_projected out;
+};
+cudaError_t launch_slice_project_batch(const SliceRequest* reqs, int count, cudaStream_t st);
 
 struct BinPlan {
   int64_t n;
@@ -81,7 +85,6 @@ cudaError_t launch_bin_sort(const sdgs_projected& p, const sdgs_view& v, const B
 
 // Binning of up to kMaxBinBatch requests with one launch per step (each kernel serves request
 // blockIdx.y); the same results as binning each request on its own.
-constexpr int kMaxBinBatch = 8;
 struct BinRequest {
   sdgs_projected proj;
   sdgs_view view;

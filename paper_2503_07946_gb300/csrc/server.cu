@@ -97,9 +97,6 @@ struct sdgs_server {
   // batched slicing
   cudaStream_t batch_stream = nullptr;
   cudaEvent_t batch_event = nullptr;
-  void* jobs_device = nullptr;
-  void* jobs_host = nullptr;  // pinned
-  cudaEvent_t jobs_copied = nullptr;
 };
 
 namespace sdgs {
@@ -370,20 +367,14 @@ void admit(sdgs_server* s) {
   uint64_t inflight = 0;
   for (auto& sl : s->slots) inflight += sl.req ? 1 : 0;
   s->max_inflight = std::max(s->max_inflight, inflight);
-  // one batched slicing launch for every request admitted in this pass
-  const size_t jb = slice_job_bytes();
-  cudaEventSynchronize(s->jobs_copied);  // the previous batch's arguments have been copied
-  int64_t max_n = 0;
+  // batched slicing of every request admitted in this pass (8 per launch, arguments by value)
+  std::vector<SliceRequest> slices;
   for (size_t j = 0; j < started.size(); ++j) {
     Slot& sl = s->slots[started[j]];
     const sdgs_scene& sc = s->scenes[sl.req->scene];
-    fill_slice_job(sc, sl.req->view, slot_projected(sl, sc.n), (char*)s->jobs_host + j * jb);
-    max_n = std::max(max_n, sc.n);
+    slices.push_back(SliceRequest{sc, sl.req->view, slot_projected(sl, sc.n)});
   }
-  cudaError_t e = cudaMemcpyAsync(s->jobs_device, s->jobs_host, started.size() * jb,
-                                  cudaMemcpyHostToDevice, s->batch_stream);
-  if (e == cudaSuccess) e = cudaEventRecord(s->jobs_copied, s->batch_stream);
-  if (e == cudaSuccess) e = launch_slice_project_batched(s->jobs_device, (int)started.size(), max_n, s->batch_stream);
+  cudaError_t e = launch_slice_project_batch(slices.data(), (int)slices.size(), s->batch_stream);
   // binning of the same requests, kMaxBinBatch per launch sequence, on the batch stream
   for (size_t j0 = 0; j0 < started.size() && e == cudaSuccess; j0 += kMaxBinBatch) {
     BinRequest reqs[kMaxBinBatch];
@@ -478,10 +469,6 @@ int sdgs_server_create(const sdgs_server_cfg* cfg, sdgs_server** out) {
   }
   cudaError_t e = cudaStreamCreateWithFlags(&s->batch_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->batch_event, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->jobs_copied, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc(&s->jobs_device, slice_job_bytes() * cfg->max_slots);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->jobs_host, slice_job_bytes() * cfg->max_slots);
-  if (e == cudaSuccess) e = cudaEventRecord(s->jobs_copied, s->batch_stream);
   for (auto& sl : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.pinned_k), sizeof(int64_t));
@@ -610,9 +597,6 @@ void sdgs_server_destroy(sdgs_server* s) {
     cudaStreamDestroy(s->batch_stream);
   }
   if (s->batch_event) cudaEventDestroy(s->batch_event);
-  if (s->jobs_copied) cudaEventDestroy(s->jobs_copied);
-  if (s->jobs_device) cudaFree(s->jobs_device);
-  if (s->jobs_host) cudaFreeHost(s->jobs_host);
   for (auto& kv : s->requests) delete kv.second;
   delete s;
 }

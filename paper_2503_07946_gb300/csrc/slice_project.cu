@@ -2,6 +2,8 @@
 // colour, fused into one pass over the scene (one thread per Gaussian).
 #include <string.h>
 
+#include <algorithm>
+
 #include "geometry.cuh"
 
 namespace sdgs {
@@ -26,19 +28,19 @@ struct SliceArgs {
 
 constexpr int kThreads = 128;
 
+// One launch slices up to kMaxSliceBatch problems (blockIdx.y selects one), their arguments by
+// value in kernel parameter space; a single problem is a batch of one, so a request sliced in a
+// batch gives the same bits as the request sliced alone.
+constexpr int kMaxSliceBatch = kMaxBinBatch;
+struct SliceBatch {
+  SliceArgs a[kMaxSliceBatch];
+};
+
 __device__ __forceinline__ void slice_project_one(const SliceArgs& a, int64_t i);
 
-__global__ void __launch_bounds__(kThreads) slice_project_kernel(const SliceArgs a) {
+__global__ void __launch_bounds__(kThreads) slice_project_kernel(const SliceBatch b) {
   griddep_wait();
-  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= a.n) return;
-  slice_project_one(a, i);
-}
-
-// Several requests in one launch: blockIdx.y selects the request's argument block.
-__global__ void __launch_bounds__(kThreads) slice_project_batched_kernel(const SliceArgs* __restrict__ jobs) {
-  griddep_wait();
-  const SliceArgs& a = jobs[blockIdx.y];
+  const SliceArgs& a = b.a[blockIdx.y];
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= a.n) return;
   slice_project_one(a, i);
@@ -152,25 +154,26 @@ static SliceArgs make_args(const sdgs_scene& s, const sdgs_view& v, const sdgs_p
 
 cudaError_t launch_slice_project(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o,
                                  cudaStream_t st) {
-  if (s.n == 0) return cudaSuccess;
-  const SliceArgs a = make_args(s, v, o);
-  const int64_t blocks = (s.n + kThreads - 1) / kThreads;
-  return launch_pdl(slice_project_kernel, dim3((unsigned)blocks), dim3(kThreads), 0, st, a);
+  const SliceRequest r{s, v, o};
+  return launch_slice_project_batch(&r, 1, st);
 }
 
-size_t slice_job_bytes() { return sizeof(SliceArgs); }
-
-void fill_slice_job(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o, void* dst) {
-  const SliceArgs a = make_args(s, v, o);
-  memcpy(dst, &a, sizeof(SliceArgs));
-}
-
-cudaError_t launch_slice_project_batched(const void* jobs_device, int njobs, int64_t max_n, cudaStream_t st) {
-  if (njobs == 0 || max_n == 0) return cudaSuccess;
-  const int64_t blocks = (max_n + kThreads - 1) / kThreads;
-  slice_project_batched_kernel<<<dim3((unsigned)blocks, (unsigned)njobs), kThreads, 0, st>>>(
-      reinterpret_cast<const SliceArgs*>(jobs_device));
-  return cudaGetLastError();
+cudaError_t launch_slice_project_batch(const SliceRequest* reqs, int count, cudaStream_t st) {
+  for (int j0 = 0; j0 < count; j0 += kMaxSliceBatch) {
+    SliceBatch b;
+    int m = 0;
+    int64_t max_n = 0;
+    for (int j = j0; j < count && m < kMaxSliceBatch; ++j, ++m) {
+      b.a[m] = make_args(reqs[j].scene, reqs[j].view, reqs[j].out);
+      max_n = std::max<int64_t>(max_n, reqs[j].scene.n);
+    }
+    for (int k = m; k < kMaxSliceBatch; ++k) b.a[k] = b.a[0];  // (never read: grid.y = m)
+    if (max_n == 0) continue;
+    const int64_t blocks = (max_n + kThreads - 1) / kThreads;
+    const cudaError_t e = launch_pdl(slice_project_kernel, dim3((unsigned)blocks, (unsigned)m), dim3(kThreads), 0, st, b);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 static SliceArgs make_args(const sdgs_scene& s, const sdgs_view& v, const sdgs_projected& o) {
