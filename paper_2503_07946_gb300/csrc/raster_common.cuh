@@ -19,12 +19,13 @@ __device__ __forceinline__ float4 scaled_conic(float4 co) {
                      __fmul_rn(kNegHalfLog2e, co.z), co.w);
 }
 
-// A record whose conic is not positive definite (only caller-made records can be) is staged with
-// opacity 0, so that every pixel skips it; the rasterisers then need no per-pixel sign test of
-// the exponent.
+// A record whose conic is not positive definite (only caller-made records can be) is staged as
+// conic 0 and opacity 0, so that every pixel skips it (exponent 0, alpha 0; with its own conic the
+// exponent could overflow to +inf and 0 * inf make alpha NaN); the rasterisers then need no
+// per-pixel sign test of the exponent.
 __device__ __forceinline__ float4 pd_or_transparent(float4 co) {
   const bool pd = co.x > 0.f && __fsub_rn(__fmul_rn(co.x, co.z), __fmul_rn(co.y, co.y)) > 0.f;
-  return pd ? co : make_float4(co.x, co.y, co.z, 0.f);
+  return pd ? co : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __device__ __forceinline__ float splat_power2(const float4& q, float dx, float dy) {

@@ -4,7 +4,10 @@
 // r + 8, so every Gaussian fetched from shared memory is evaluated twice.  The tile's sorted
 // instances (only Gaussians that may reach the tile, see tile_reach.cuh) are staged 128 at a time
 // in shared memory; each pixel walks them front to back.  The block leaves once every pixel has
-// stopped.
+// stopped.  A batch in which no staged Gaussian can reach the 0.99 clamp of alpha at any pixel of
+// the tile (clamp_free) is blended without the clamp.
+#include <type_traits>
+
 #include "raster_common.cuh"
 
 namespace sdgs {
@@ -43,7 +46,9 @@ struct PixelPair {
 // (without blending).  The exponent is qa dx^2 + dy (qc dy + qb dx), as in splat_power2; staged
 // conics are positive definite (others get opacity 0), so it is <= 0 but for FP32 rounding at a
 // pixel on the centre, where alpha is then alpha_cond (the FP64 oracle takes the Gaussian there).
-template <bool kCount>
+// kClamp = false: the caller knows that alpha_cond * exp2(exponent) <= 0.99 for this Gaussian at
+// both pixels (see clamp_free), so the 0.99 clamp would return its argument and is left out.
+template <bool kCount, bool kClamp = true>
 __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const float4& c, float dx, float2 dy,
                                        uint32_t pos1) {
   const float a = __fmul_rn(__fmul_rn(q.x, dx), dx);
@@ -52,7 +57,7 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
   const float2 p2 = __ffma2_rn(dy, t, make_float2(a, a));
   const float2 e = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
   const float2 m = __fmul2_rn(make_float2(q.w, q.w), e);
-  const float2 al = make_float2(fminf(kAlphaMax, m.x), fminf(kAlphaMax, m.y));
+  const float2 al = kClamp ? make_float2(fminf(kAlphaMax, m.x), fminf(kAlphaMax, m.y)) : m;
   const float2 aT = __fmul2_rn(al, px.T);
   const float2 Tn = __fadd2_rn(px.T, make_float2(-aT.x, -aT.y));  // T (1 - alpha) as T - alpha T
   const bool hit0 = !px.done0 && al.x >= kAlphaMin;
@@ -72,6 +77,22 @@ __device__ __forceinline__ void blend2(PixelPair& px, const float4& q, const flo
   px.last1 = take1 ? pos1 : px.last1;
   px.done0 = px.done0 || stop0;
   px.done1 = px.done1 || stop1;
+}
+
+// Whether the 0.99 clamp of alpha cannot act for staged Gaussian (m, q) at any pixel centre of the
+// tile whose first pixel centre is (x0, y0).  The exponent is evaluated as in blend2 from the
+// rounded offsets dx, dy; for a positive-definite conic its exact value at those offsets is <= 0,
+// and the three roundings of a, bx, t and the final sum add at most
+// gamma_3 * S, S = |qa| Dx^2 + |qb| Dx Dy + |qc| Dy^2 with Dx, Dy bounds of |dx|, |dy| over the
+// tile (gamma_3 = 3u / (1 - 3u), u = 2^-24).  With S <= 6e4 that is below 0.0108, so exp2 of the
+// computed exponent is below 2^0.0108 = 1.0075, ex2.approx adds a relative error far below 1e-6,
+// and alpha_cond <= 0.98 keeps alpha_cond * exp2 <= 0.9874 < 0.99.  (S is formed in FP32 from
+// values that bound the true ones; NaN or infinite inputs fail the test.)
+__device__ __forceinline__ bool clamp_free(float2 m, float4 q, float x0, float y0) {
+  const float Dx = fmaxf(fabsf(x0 - m.x), fabsf(x0 + 15.f - m.x)) * 1.0001f;
+  const float Dy = fmaxf(fabsf(y0 - m.y), fabsf(y0 + 15.f - m.y)) * 1.0001f;
+  const float S = (fabsf(q.x) * Dx * Dx + fabsf(q.y) * Dx * Dy + fabsf(q.z) * Dy * Dy) * 1.0001f;
+  return q.w <= 0.98f && S <= 6e4f;
 }
 
 template <bool kCount>
@@ -99,12 +120,16 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
     if (__syncthreads_count(pp.done0 && pp.done1) == kThreads) break;
     // stage the next 128 instances of the tile's list
     const int j = base + threadIdx.x;
+    bool no_clamp = true;  // the 0.99 clamp cannot act for this thread's staged Gaussian
     if (j < n) {
       const uint32_t g = a.point_list[range.x + j];
       if (g < a.n) {
-        s_xy[threadIdx.x] = a.mean2d[g];
-        s_q[threadIdx.x] = scaled_conic(pd_or_transparent(a.conic_opacity[g]));
+        const float2 m = a.mean2d[g];
+        const float4 q = scaled_conic(pd_or_transparent(a.conic_opacity[g]));
+        s_xy[threadIdx.x] = m;
+        s_q[threadIdx.x] = q;
         s_rgb[threadIdx.x] = make_float4(a.rgb[3 * g + 0], a.rgb[3 * g + 1], a.rgb[3 * g + 2], 0.f);
+        no_clamp = clamp_free(m, q, (float)(tx * kTile) + 0.5f, (float)(ty * kTile) + 0.5f);
       } else {  // opacity 0: every pixel skips it
         s_xy[threadIdx.x] = make_float2(0.f, 0.f);
         s_q[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -112,34 +137,40 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(const FwdArgs a) {
       }
     }
     const int cnt = min(kThreads, n - base);
-    __syncthreads();
+    // whether the whole batch can run without the clamp (uniform over the block)
+    const bool batch_no_clamp = __syncthreads_and(no_clamp) != 0;
     if (!(pp.done0 && pp.done1)) {
       // A full batch runs as straight-line groups of 8 Gaussians with the stop test after each
       // group; the tile's last, partial batch in groups of 4 with bound checks (entries past cnt
       // are never read).  A stopped pixel ignores the rest (blend2 is a no-op for it).
-      auto one = [&](int k) {
-        const float2 m = s_xy[k];
-        const float4 q = s_q[k];
-        const float4 c = s_rgb[k];
-        const uint32_t pos1 = (uint32_t)(base + k) + 1u;
-        // offsets exactly as the backward forms them, so both passes take the same decisions
-        const float dx = fx - m.x;
-        blend2<kCount>(pp, q, c, dx, __fadd2_rn(fy, make_float2(-m.y, -m.y)), pos1);
+      auto run = [&](auto clamp) {
+        constexpr bool kClamp = decltype(clamp)::value;
+        auto one = [&](int k) {
+          const float2 m = s_xy[k];
+          const float4 q = s_q[k];
+          const float4 c = s_rgb[k];
+          const uint32_t pos1 = (uint32_t)(base + k) + 1u;
+          // offsets exactly as the backward forms them, so both passes take the same decisions
+          const float dx = fx - m.x;
+          blend2<kCount, kClamp>(pp, q, c, dx, __fadd2_rn(fy, make_float2(-m.y, -m.y)), pos1);
+        };
+        if (cnt == kThreads) {  // a full batch: no bound checks
+          for (int k0 = 0; k0 < kThreads; k0 += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) one(k0 + u);
+            if (pp.done0 && pp.done1) break;
+          }
+        } else {
+          for (int k0 = 0; k0 < cnt; k0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (k0 + u < cnt) one(k0 + u);
+            if (pp.done0 && pp.done1) break;
+          }
+        }
       };
-      if (cnt == kThreads) {  // a full batch: no bound checks
-        for (int k0 = 0; k0 < kThreads; k0 += 8) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) one(k0 + u);
-          if (pp.done0 && pp.done1) break;
-        }
-      } else {
-        for (int k0 = 0; k0 < cnt; k0 += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (k0 + u < cnt) one(k0 + u);
-          if (pp.done0 && pp.done1) break;
-        }
-      }
+      if (!kCount && batch_no_clamp) run(std::false_type{});
+      else run(std::true_type{});
     }
   }
   if (kCount) {

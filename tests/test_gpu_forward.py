@@ -310,3 +310,44 @@ def test_renderer_on_a_side_stream_matches_the_default_stream(scene0):
             img = r.forward(st, view, side)
     side.synchronize()
     assert torch.equal(img, ref)
+
+
+def test_clamped_opacities_and_non_positive_definite_records(scene0):
+    """Caller-made records.  (1) A tenth of the Gaussians at opacity 0.999, so that the 0.99 clamp
+    of alpha acts near their centres and their tiles' batches take the clamped blend: the image
+    matches the oracle's.  (2) Records whose conic is not positive definite, in front of
+    everything and listed on every tile of the image: every pixel skips them (their exponent could
+    otherwise overflow), so the image and transmittance equal those without them, bit for bit."""
+    cam = _cams()[0]
+    g = render.gaussians(render.params_from_scene(scene0), cam, scene0.lambda_t, scene0.lambda_d)
+    rec = U.oracle_records_f32(g)
+    rng = np.random.default_rng(7)
+    hi = rng.random(len(rec["opacity"])) < 0.1
+    rec["opacity"] = np.where(hi, np.float32(0.999), rec["opacity"]).astype(np.float32)
+    view = U.sdgs.view_struct(cam)
+    proj = U.sdgs.ProjectedBuffers.from_host(rec)
+    k, keys, vals, ranges, bins = U.gpu_bin(proj, view)
+    img, T, nc = U.gpu_render(proj, bins, view)
+    ref = render.render_projected(rec, cam.width, cam.height, cam.bg)
+    ok = U.pixel_ok(ref["margin_alpha"].numpy(), ref["margin_T"].numpy())
+    assert ok.mean() > 0.99
+    assert np.abs(img - ref["image"].numpy()).max(-1)[ok].max() <= COLOUR_TOL
+    clamped = (hi[:, None] & (rec["rect"][:, 2] > rec["rect"][:, 0])[:, None]).any()
+    assert clamped
+
+    m = 16
+    extra = dict(
+        mean2d=rng.uniform(0, [cam.width, cam.height], size=(m, 2)).astype(np.float32),
+        conic=np.tile(np.array([[-0.01, 0.0, 0.02], [0.01, 0.05, 0.01], [0.0, 0.0, 0.0], [0.3, 0.0, -0.2]],
+                               np.float32), (m // 4, 1)),
+        opacity=np.full(m, 0.5, np.float32),
+        rgb=np.full((m, 3), 0.3, np.float32),
+        depth=np.full(m, 0.5 * float(rec["depth"].min()), np.float32),
+        rect=np.tile(np.array([[0, 0, cam.tiles_x, cam.tiles_y]], np.int64), (m, 1)))
+    rec2 = {key: np.concatenate([rec[key], extra[key]], 0) for key in extra}
+    proj2 = U.sdgs.ProjectedBuffers.from_host(rec2)
+    k2, _, _, _, bins2 = U.gpu_bin(proj2, view)
+    assert k2 >= k + m * cam.tiles_x * cam.tiles_y  # listed on every tile
+    img2, T2, _ = U.gpu_render(proj2, bins2, view)
+    np.testing.assert_array_equal(img2, img)
+    np.testing.assert_array_equal(T2, T)
