@@ -556,19 +556,20 @@ def run_ours(args, rank: int, world: int):
     re_.check_deferred()
     assert re_.overflowed_frames == overflowed, "a timed end-to-end frame exceeded the bins' capacity"
     del re_
-    # the same with two frames in flight, as a streaming client runs: two renderers on two
-    # streams; every frame's image is copied to pinned host memory and waited for (by the host)
-    # before its renderer takes the frame after next
-    rs = [prender.Renderer(scene.n, W, H, capacity=r.bins.capacity, deferred_check=True) for _ in range(2)]
-    sts = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    hosts = [torch.empty(H, W, 3, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    # the same with K frames in flight, as a streaming client runs: K renderers on K streams;
+    # every frame's image is copied to pinned host memory and waited for (by the host) before its
+    # renderer takes the frame K later.  K = 2, 3 and 4 are timed; the line reports the fastest.
+    kmax_fif = 4
+    rs = [prender.Renderer(scene.n, W, H, capacity=r.bins.capacity, deferred_check=True) for _ in range(kmax_fif)]
+    sts = [torch.cuda.Stream(dev) for _ in range(kmax_fif)]
+    hosts = [torch.empty(H, W, 3, dtype=torch.float32, pin_memory=True) for _ in range(kmax_fif)]
 
-    def stream_frames(count, first):
-        done = [None, None]
+    def stream_frames(count, first, k):
+        done = [None] * k
         for i in range(count):
-            j = i % 2
+            j = i % k
             if done[j] is not None:
-                done[j].synchronize()  # frame i - 2's image is on the host
+                done[j].synchronize()  # frame i - k's image is on the host
             with torch.cuda.stream(sts[j]):
                 rs[j].forward(st, views[first + i], sts[j])
                 hosts[j].copy_(rs[j].image, non_blocking=True)
@@ -578,16 +579,20 @@ def run_ours(args, rank: int, world: int):
             if ev is not None:
                 ev.synchronize()
 
-    stream_frames(warm, 0)
-    for q in rs:
-        q.check_deferred()
-    overflowed = [q.overflowed_frames for q in rs]
-    t0 = time.perf_counter()
-    stream_frames(steps, warm)
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
-    for q, o in zip(rs, overflowed):
-        q.check_deferred()
-        assert q.overflowed_frames == o, "a timed end-to-end frame exceeded the bins' capacity"
+    e2e_by_k = {}
+    for k in range(2, kmax_fif + 1):
+        stream_frames(warm, 0, k)
+        for q in rs:
+            q.check_deferred()
+        overflowed = [q.overflowed_frames for q in rs]
+        t0 = time.perf_counter()
+        stream_frames(steps, warm, k)
+        e2e_by_k[k] = max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
+        for q, o in zip(rs, overflowed):
+            q.check_deferred()
+            assert q.overflowed_frames == o, "a timed end-to-end frame exceeded the bins' capacity"
+    fif = min(e2e_by_k, key=e2e_by_k.get)
+    e2e_s = e2e_by_k[fif]
     del rs
 
     # ---- fwd + bwd (L2 loss against a target from perturbed parameters, camera 0) ----
@@ -596,9 +601,11 @@ def run_ours(args, rank: int, world: int):
     large["workload"] = ("config 2: 1.5M 7D Gaussians in 64 clusters, 1352x1014, forward-facing arc cameras, "
                          "black background, lambda_t = lambda_d = 0.1")
     del big_scene
-    pipe = pipelined_frames(scene, t_scene, views, min(steps, 1000), warm, dev)
-    fb = fwd_bwd_its(scene, cams[0], steps, warm, dev)
-    fb_agr = fwd_bwd_its(scene, cams[0], min(steps, 200), warm, dev, agr=True)
+    pipe = {str(k): pipelined_frames(scene, t_scene, views, min(steps, 1000), warm, dev, k) for k in (2, 3, 4)}
+    # (the training iterations are timed over at least 200 of them: 20 take 17 ms, short enough
+    # for the host's launch queue to show)
+    fb = fwd_bwd_its(scene, cams[0], max(steps, 200), warm, dev)
+    fb_agr = fwd_bwd_its(scene, cams[0], max(min(steps, 200), 100), warm, dev, agr=True)
     agr = agr_frames(scene, t_scene, views, flush, min(steps, 300), warm, dev)
     dens = densify_ms(t_scene, scene, views[0], flush, 20, dev)
     serving = None if args.no_serving else serving_bench(dev, count=args.serve_requests)
@@ -638,7 +645,8 @@ def run_ours(args, rank: int, world: int):
         "densify_stats": dens,
         "serving": serving,
         "e2e": {"value": job_mpix_s(world, pix, e2e_s * 1e3), "unit": "Mpix/s", "h2d_bytes_per_step": view_bytes,
-                "d2h_bytes_per_step": pix * 3 * 4 + 8, "frames_in_flight": 2,
+                "d2h_bytes_per_step": pix * 3 * 4 + 8, "frames_in_flight": fif,
+                "by_frames_in_flight": {str(k): job_mpix_s(world, pix, v * 1e3) for k, v in e2e_by_k.items()},
                 "one_frame_in_flight": job_mpix_s(world, pix, e2e_one_s * 1e3)},
         "gpu_launches": steps * launches_per_frame(scene.n, r.bins.capacity, W, H),
         "roofline": {"kernel": "render_fwd_kernel", "bound": "alu", "achieved": achieved_tflops,
@@ -853,10 +861,10 @@ def frames_on(scene, cams, steps: int, warm: int, dev, flush) -> dict:
             "instances": int(r.bins.num_instances.item()), "steps": steps}
 
 
-def pipelined_frames(scene, t_scene, views, steps: int, warm: int, dev) -> dict:
-    """Throughput with two frames in flight: independent views alternate between two streams with
-    their own buffers, so one frame's latency-bound binning overlaps the other's compositing.  No
-    L2 flush between frames (scene, records and lists together exceed the 129 MB L2)."""
+def pipelined_frames(scene, t_scene, views, steps: int, warm: int, dev, k: int = 2) -> dict:
+    """Throughput with k frames in flight: independent views rotate over k streams with their own
+    buffers, so one frame's latency-bound binning overlaps another's compositing.  No L2 flush
+    between frames (scene, records and lists together exceed the 129 MB L2)."""
     from paper_2503_07946_gb300 import render as prender
     from paper_2503_07946_gb300 import sdgs
     st = sdgs.scene_struct(t_scene, scene.lambda_t, scene.lambda_d)
@@ -867,12 +875,12 @@ def pipelined_frames(scene, t_scene, views, steps: int, warm: int, dev) -> dict:
         sdgs.slice_project(st, v, sizing.proj)
         kmax = max(kmax, sizing.bin(v))
     del sizing
-    rs = [prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096) for _ in range(2)]
-    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    rs = [prender.Renderer(scene.n, W, H, capacity=int(kmax * 1.02) + 4096) for _ in range(k)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(k)]
 
     def run(lo, hi):
         for i in range(lo, hi):
-            r, s = rs[i % 2], streams[i % 2]
+            r, s = rs[i % k], streams[i % k]
             sdgs.slice_project(st, views[i], r.proj, s)
             sdgs.bin_sort(r.proj, views[i], r.bins, sync=False, stream=s)
             sdgs.render_fwd(r.proj, r.bins, views[i], r.image, r.final_T, r.n_contrib, None, s)
@@ -893,7 +901,7 @@ def pipelined_frames(scene, t_scene, views, steps: int, warm: int, dev) -> dict:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     return {"value": W * H / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "ms_per_frame": ms, "fps": 1000.0 / ms,
-            "frames_in_flight": 2, "steps": steps}
+            "frames_in_flight": k, "steps": steps}
 
 
 def agr_weights_dev(dev) -> dict:
