@@ -30,6 +30,8 @@ import torch  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "Mpix/s & FPS at 800×800/300k Gaussians; fwd+bwd it/s; p50/p99 serving latency"
+WORKLOAD = ("config 1: 300k 7D Gaussians, 800x800, 100 orbit cameras (random frame each), white background, "
+            "lambda_t = lambda_d = 0.05")
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
@@ -293,8 +295,7 @@ def run_reference(args, rank: int, world: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "config 1: 300k 7D Gaussians, 800x800, 100 orbit cameras",
-                       "n_gaussians": 300000, "width": 800, "height": 800},
+            "config": {"workload": WORKLOAD, "n_gaussians": 300000, "width": 800, "height": 800},
             "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample,
                              "cpu_model": cpu_model(), "frame_s_estimate": est,
                              "frame_mpix_s_estimate": 800 * 800 / est / 1e6},
@@ -629,9 +630,7 @@ def run_ours(args, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": steps, "warmup": warm,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "fps": world * 1000.0 / ms,
-        "config": {"workload": "config 1: 300k 7D Gaussians, 800x800, 100 orbit cameras (random frame each), "
-                               "white background, lambda_t = lambda_d = 0.05",
-                   "n_gaussians": scene.n, "width": W, "height": H, "parallelism": f"replicas x{world}",
+        "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "width": W, "height": H, "parallelism": f"replicas x{world}",
                    "l2": L2Flush.DESCRIPTION},
         "phases_ms": {"slice_project": float(phase[:, 0].mean()), "bin_sort": float(phase[:, 1].mean()),
                       "render_fwd": raster_ms},
