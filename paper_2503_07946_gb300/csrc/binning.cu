@@ -27,7 +27,6 @@ namespace sdgs {
 namespace {
 
 constexpr int kRadixThreads = 256;
-constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kBins = 256;
 
 constexpr int kScanThreads = 256;
@@ -418,8 +417,10 @@ struct PassArgs {
   unsigned grid;
 };
 
-template <int ITEMS>
-__global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_kernel(const Batch<PassArgs> batch) {
+// THREADS threads with ITEMS keys each; threads past the kBins digits sit out the digit phases.
+template <int ITEMS, int THREADS = kRadixThreads>
+__global__ void __launch_bounds__(THREADS, THREADS > kRadixThreads ? 2 : (ITEMS >= 12 ? 4 : 5))
+    onesweep_kernel(const Batch<PassArgs> batch) {
   const PassArgs& pa = batch.a[blockIdx.y];
   if (blockIdx.x >= pa.grid) return;
   const uint32_t* __restrict__ keys_in = pa.keys_in;
@@ -436,15 +437,17 @@ __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_k
   const uint32_t pass_bit = pa.pass_bit;
   const int spin_limit = pa.spin_limit;
   griddep_wait();
-  constexpr int TILE = kRadixThreads * ITEMS;
+  constexpr int TILE = THREADS * ITEMS;
+  constexpr int WARPS = THREADS / 32;
+  static_assert(THREADS >= kBins, "one thread per digit");
   __shared__ uint32_t s_keys[TILE];
   __shared__ uint32_t s_vals[TILE];
-  __shared__ uint32_t s_whist[kRadixWarps][kBins];
+  __shared__ uint32_t s_whist[WARPS][kBins];
   __shared__ uint32_t s_dstart[kBins];
   __shared__ uint32_t s_gbase[kBins];
   __shared__ uint32_t s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-  for (int i = threadIdx.x; i < kRadixWarps * kBins; i += kRadixThreads) (&s_whist[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < WARPS * kBins; i += THREADS) (&s_whist[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t n = element_count(nptr, n_static, cap);
@@ -460,6 +463,7 @@ __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_k
   const int64_t wbase = base + (int64_t)warp * 32 * ITEMS;
   const bool full = base + TILE <= n;  // uniform over the block
   const int dg = threadIdx.x;
+  const bool digit = dg < kBins;       // this thread owns bin dg
   const bool used = dg <= (int)dmask;  // digits of `width` bits: the other bins stay empty
   uint32_t* mine = status + tile * kBins + dg;
   uint32_t run = 0;  // this tile's keys with digit dg
@@ -468,17 +472,19 @@ __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_k
     if (full) load_and_rank<ITEMS, true>(keys_in, vals_in, wbase, n, shift, width, s_whist[warp], key, val, rank);
     else load_and_rank<ITEMS, false>(keys_in, vals_in, wbase, n, shift, width, s_whist[warp], key, val, rank);
     __syncthreads();
+    if (digit) {
 #pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) {
-      const uint32_t c = s_whist[w][dg];
-      s_whist[w][dg] = run;
-      run += c;
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_whist[w][dg];
+        s_whist[w][dg] = run;
+        run += c;
+      }
     }
     // publish this tile's count at once, so later tiles can pass over it while it waits
     if (used) store_status(mine, (tile == 0 ? kStatusInclusive : kStatusAggregate) | run);
     uint32_t tot;
-    const uint32_t incl = block_inclusive_scan<uint32_t, kRadixThreads>(run, &tot);
-    s_dstart[dg] = incl - run;
+    const uint32_t incl = block_inclusive_scan<uint32_t, THREADS>(run, &tot);
+    if (digit) s_dstart[dg] = incl - run;
     __syncthreads();
     // the tile's keys in digit order, in shared memory (stable: warps, then ranks)
 #pragma unroll
@@ -496,15 +502,15 @@ __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_k
   if (used && tile > 0) store_status(mine, kStatusInclusive | (before + run));
   {
     uint32_t tot;
-    const uint32_t all = digit_hist[dg];
-    const uint32_t gincl = block_inclusive_scan<uint32_t, kRadixThreads>(all, &tot);
-    s_gbase[dg] = gincl - all + before;
+    const uint32_t all = digit ? digit_hist[dg] : 0u;
+    const uint32_t gincl = block_inclusive_scan<uint32_t, THREADS>(all, &tot);
+    if (digit) s_gbase[dg] = gincl - all + before;
   }
   __syncthreads();
   if (full) {
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
-      const int i = r * kRadixThreads + threadIdx.x;
+      const int i = r * THREADS + threadIdx.x;
       const uint32_t k = s_keys[i];
       const uint32_t d = (k >> shift) & dmask;
       const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
@@ -515,7 +521,7 @@ __global__ void __launch_bounds__(kRadixThreads, ITEMS >= 12 ? 4 : 5) onesweep_k
     }
   } else {
     const int cnt = (int)(n - base);
-    for (int i = threadIdx.x; i < cnt; i += kRadixThreads) {
+    for (int i = threadIdx.x; i < cnt; i += THREADS) {
       const uint32_t k = s_keys[i];
       const uint32_t d = (k >> shift) & dmask;
       const uint32_t g = s_gbase[d] + (uint32_t)i - s_dstart[d];
@@ -662,8 +668,10 @@ cudaError_t radix_sort(const SortJob* jobs, int count, bool hist_ready, cudaStre
       (sort_items(J.cap) == 12 ? l12 : l8).add(a);
       cur[j] ^= 1;
     }
+    // (the 2048-key tiles run as 512 threads with 4 keys each: twice the warps of 256 x 8 to hide
+    // the latency of the pass's dependent phases, the same tiles and look-back chain)
     e = launch_batch(onesweep_kernel<12>, l12, kRadixThreads, 0, st);
-    if (e == cudaSuccess) e = launch_batch(onesweep_kernel<8>, l8, kRadixThreads, 0, st);
+    if (e == cudaSuccess) e = launch_batch(onesweep_kernel<4, 2 * kRadixThreads>, l8, 2 * kRadixThreads, 0, st);
   }
   return e;
 }
