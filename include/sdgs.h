@@ -372,6 +372,8 @@ int sdgs_agr_bwd_workspace_size(int64_t n, size_t* bytes);
 /* Adjoint of sdgs_agr_refine: given dmean7_hat [n][7] and dL28_hat [n][28] (gradients w.r.t. the
  * refined parameters, e.g. from sdgs_render_bwd on the refined scene), accumulates
  * dmean7 += dmean7_hat + (d phi / d mu)^T (...), dL28 += dL28_hat, and the weight gradients.
+ * The refinement adds its residual to L without reading L, so the gradient of L28 is dL28_hat
+ * itself: dL28 may be NULL, and then the call leaves it to the caller (no copy is made).
  * The weight gradients are summed per block and then across blocks in a fixed order, so repeated
  * calls give identical results.  Errors: SDGS_ERR_INVALID_ARG, SDGS_ERR_WORKSPACE, SDGS_ERR_CUDA. */
 int sdgs_agr_refine_bwd(const sdgs_scene* scene, const sdgs_agr* agr, float t, const float* dmean7_hat,

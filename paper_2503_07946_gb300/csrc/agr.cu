@@ -294,8 +294,10 @@ __global__ void __launch_bounds__(kAgrThreads) agr_bwd_kernel(
     if (live) {
 #pragma unroll
       for (int c = 0; c < kX; ++c) dmean7[kX * i + c] += dmean7_hat[kX * i + c] + dx[c];
+      if (dL28 != nullptr) {  // (NULL: the caller takes dL28_hat as the gradient of L28 itself)
 #pragma unroll
-      for (int k = 0; k < 28; ++k) dL28[28 * i + k] += dL28_hat[28 * i + k];
+        for (int k = 0; k < 28; ++k) dL28[28 * i + k] += dL28_hat[28 * i + k];
+      }
     }
     __syncthreads();  // s_x / s_dout are rewritten by the next tile
   }

@@ -447,7 +447,7 @@ int sdgs_agr_refine_bwd(const sdgs_scene* scene, const sdgs_agr* agr, float t, c
     set_error("AGR gradient pointers are NULL");
     return SDGS_ERR_INVALID_ARG;
   }
-  if (scene->n > 0 && (!dmean7_hat || !dL28_hat || !dmean7 || !dL28)) {
+  if (scene->n > 0 && (!dmean7_hat || !dL28_hat || !dmean7)) {
     set_error("AGR backward input / output pointer is NULL");
     return SDGS_ERR_INVALID_ARG;
   }

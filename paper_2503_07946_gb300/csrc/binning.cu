@@ -419,7 +419,7 @@ struct PassArgs {
 
 // THREADS threads with ITEMS keys each; threads past the kBins digits sit out the digit phases.
 template <int ITEMS, int THREADS = kRadixThreads>
-__global__ void __launch_bounds__(THREADS, THREADS > kRadixThreads ? 2 : (ITEMS >= 12 ? 4 : 5))
+__global__ void __launch_bounds__(THREADS, THREADS > kRadixThreads ? 1024 / THREADS : (ITEMS >= 12 ? 4 : 5))
     onesweep_kernel(const Batch<PassArgs> batch) {
   const PassArgs& pa = batch.a[blockIdx.y];
   if (blockIdx.x >= pa.grid) return;

@@ -220,11 +220,12 @@ class AGRRefine(torch.autograd.Function):
         scene = sdgs.scene_struct(dict(mean7=m7, L28=l28, opacity=opacity, sh=sh), 0.0, 0.0)
         d_m = torch.zeros_like(m7) if d_m is None else d_m.contiguous()
         d_l = torch.zeros_like(l28) if d_l is None else d_l.contiguous()
-        gm, gl = torch.zeros_like(m7), torch.zeros_like(l28)
+        gm = torch.zeros_like(m7)
         dw = {k: torch.zeros_like(v) for k, v in w.items()}
         ws = torch.empty(max(sdgs.agr_bwd_workspace_size(n), 256), dtype=torch.uint8, device=m7.device)
-        sdgs.agr_refine_bwd(scene, w, ctx.t, d_m, d_l, gm, gl, dw, ws)
-        return gm, gl, dw["w1"], dw["b1"], dw["w2"], dw["b2"], None
+        # the residual of L does not depend on L: its gradient passes through unchanged (dL28 = NULL)
+        sdgs.agr_refine_bwd(scene, w, ctx.t, d_m, d_l, gm, None, dw, ws)
+        return gm, d_l, dw["w1"], dw["b1"], dw["w2"], dw["b2"], None
 
 
 def agr_refine(mean7, L28, weights: dict, t: float):

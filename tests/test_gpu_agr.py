@@ -58,15 +58,21 @@ def test_refinement_adjoint_matches_oracle_and_is_deterministic():
     wd = _weights_dev(w)
     ws = torch.empty(sdgs.agr_bwd_workspace_size(n), dtype=torch.uint8, device="cuda")
     runs = []
-    for _ in range(2):
+    for with_dl28 in (True, True, False):
         gm, gl = torch.zeros(n, 7, device="cuda"), torch.zeros(n, 28, device="cuda")
         dw = {k: torch.zeros_like(v) for k, v in wd.items()}
         sdgs.agr_refine_bwd(st, wd, t, torch.tensor(dm_hat, device="cuda"), torch.tensor(dl_hat, device="cuda"),
-                            gm, gl, dw, ws)
+                            gm, gl if with_dl28 else None, dw, ws)
         torch.cuda.synchronize()
         runs.append(dict(mean7=gm.cpu().numpy(), L28=gl.cpu().numpy(), **{k: v.cpu().numpy() for k, v in dw.items()}))
     for k in runs[0]:
         np.testing.assert_array_equal(runs[0][k], runs[1][k])  # fixed reduction order
+    # dL28 = NULL: the same mean and weight gradients, and dL28 left alone (the caller's to take)
+    for k in runs[0]:
+        if k != "L28":
+            np.testing.assert_array_equal(runs[2][k], runs[0][k])
+    np.testing.assert_array_equal(runs[2]["L28"], 0.0)
+    np.testing.assert_array_equal(runs[0]["L28"], dl_hat)
     got = runs[0]
     m7 = torch.tensor(scene.mean7, dtype=torch.float64, requires_grad=True)
     l28 = torch.tensor(scene.L28, dtype=torch.float64, requires_grad=True)
