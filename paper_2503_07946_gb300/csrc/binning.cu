@@ -1065,7 +1065,7 @@ __device__ __forceinline__ int span_len(uint32_t k) { return (int)(k >> 16) + 1;
 // rows again while writing.  The last block to finish sets the kept span count.  Every wait is
 // bounded: a block that gives up sets pass_bit in *err (the row sort then skips and the lists
 // stay empty).
-constexpr int kWalkKeep = 160;                          // spans per warp kept between walk and write
+constexpr int kWalkKeep = 224;                          // spans per warp kept between walk and write
 constexpr uint64_t kWalkAggregate = 1ull << 62;         // the block's own totals
 constexpr uint64_t kWalkInclusive = 2ull << 62;         // totals of blocks 0 .. this one
 constexpr uint64_t kWalkField = (1ull << 31) - 1;       // 31-bit fields: instances << 31 | spans
