@@ -544,9 +544,10 @@ int radix_pass_count(int bits) {
   return k;
 }
 
-// Keys per sort block for `cap` slots: 12 per thread when that still gives two blocks per SM, else
-// 8.  Fewer, larger blocks shorten the look-back chains of small sorts (a 300k-key depth pass:
-// 147 blocks of 2048 keys run faster than 293 of 1024).
+// Tile size of a sort of `cap` slots, in keys per kRadixThreads threads: 12 (3072-key tiles, run
+// as 256 threads x 12) when that still gives two blocks per SM, else 8 (2048-key tiles, run as
+// 512 threads x 4).  Fewer, larger tiles shorten the look-back chains of small sorts (a 300k-key
+// depth pass: 147 tiles of 2048 keys run faster than 293 of 1024).
 int sort_items(int64_t cap) {
   const int64_t want = 2 * (int64_t)device_sm_count();
   if ((cap + 12 * kRadixThreads - 1) / (12 * kRadixThreads) >= want) return 12;
